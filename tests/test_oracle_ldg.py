@@ -1,0 +1,155 @@
+"""Pins for the oracle's basis and LDG operator (Sec. 2.1).
+
+Each check compares the oracle with something other than itself: a closed
+form, a brute-force point evaluation, an invariant stated in the paper, or
+the convergence order the paper states (order p+1, Sec. 2.1 last bullet).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import ldg
+from paper_2412_12506_gb300.inputs import circle_mu
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5])
+def test_basis_closed_forms(p):
+    bas = ldg.Basis1D(p)
+    # orthonormality of sqrt((2k+1)/2) P_k
+    assert np.allclose(bas.mass, np.eye(p + 1), atol=1e-14)
+    # int phi_i phi_j' = sqrt((2i+1)(2j+1)) when j > i and j - i odd, else 0
+    K = np.zeros((p + 1, p + 1))
+    for i in range(p + 1):
+        for j in range(p + 1):
+            if j > i and (j - i) % 2 == 1:
+                K[i, j] = np.sqrt((2 * i + 1) * (2 * j + 1))
+    assert np.allclose(bas.K, K, atol=1e-13)
+    k = np.arange(p + 1)
+    assert np.allclose(bas.hi, np.sqrt((2 * k + 1) / 2.0), atol=1e-14)
+    assert np.allclose(bas.lo, (-1.0) ** k * np.sqrt((2 * k + 1) / 2.0), atol=1e-14)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_child_injection_pointwise(p):
+    """(I u)|_child reproduces the coarse polynomial at arbitrary points."""
+    bas = ldg.Basis1D(p)
+    rng = np.random.default_rng(1)
+    xi = rng.uniform(-1, 1, 17)
+    c = rng.standard_normal(p + 1)
+    for s in (0, 1):
+        eta = (xi + 2 * s - 1) / 2.0
+        coarse_val = sum(c[j] * ldg.phi(j, eta) for j in range(p + 1))
+        fine_c = bas.P[s] @ c
+        fine_val = sum(fine_c[i] * ldg.phi(i, xi) for i in range(p + 1))
+        assert np.allclose(fine_val, coarse_val, atol=1e-13)
+    # norm preservation: sum_s P_s^T P_s = 2 I
+    assert np.allclose(bas.P[0].T @ bas.P[0] + bas.P[1].T @ bas.P[1], 2 * np.eye(p + 1), atol=1e-13)
+
+
+def _check_spsd_kernel(op, d, p):
+    A = op.A.dense()
+    scale = np.abs(A).max()
+    assert np.abs(A - A.T).max() <= 1e-14 * scale
+    lam = np.linalg.eigvalsh(A)
+    assert lam[0] >= -1e-12 * lam[-1]
+    # kernel is exactly span{constant}: A c = 0 and the second eigenvalue is positive
+    c = ldg.constant_vector(d, p, op.A.nblocks)
+    assert np.abs(A @ c).max() <= 1e-12 * scale
+    assert lam[1] > 1e-8 * lam[-1]
+
+
+@pytest.mark.parametrize("d,n,p", [(2, 4, 1), (2, 4, 2), (2, 3, 3), (2, 2, 2), (2, 1, 2),
+                                   (3, 3, 1), (3, 2, 2)])
+def test_poisson_symmetric_psd_kernel(d, n, p):
+    _check_spsd_kernel(ldg.assemble(d, n, p), d, p)
+
+
+@pytest.mark.parametrize("d,n,p,contrast", [(2, 8, 2, 1e4), (2, 8, 1, 1e-4), (3, 4, 1, 1e4)])
+def test_interface_symmetric_psd_kernel(d, n, p, contrast):
+    mu = circle_mu(d, n, seed=3, mu_in=contrast)
+    assert len(np.unique(mu)) == 2
+    _check_spsd_kernel(ldg.assemble(d, n, p, mu), d, p)
+
+
+@pytest.mark.parametrize("d,n", [(2, 5), (2, 8), (3, 4)])
+def test_stencil_is_5_or_7_point(d, n):
+    """One-sided fluxes on a Cartesian grid give the 5/7-point block stencil (Sec. 2.3.2)."""
+    op = ldg.assemble(d, n, 1)
+    counts = np.diff(op.A.pat.indptr)
+    assert np.all(counts == 2 * d + 1)
+
+
+def test_flux_direction_follows_viscosity():
+    """u_hat comes from the more viscous side; on ties from the lower element (Sec. 2.1)."""
+    d, n = 2, 8
+    mu = circle_mu(d, n, seed=5, mu_in=1e4)
+    op = ldg.assemble(d, n, 1, mu)
+    mesh = ldg.Mesh(d, n)
+    for a in range(d):
+        Gp = op.G[a].pat
+        for L, U in mesh.faces(a):
+            src = L if mu[L] >= mu[U] else U
+            other = U if src == L else L
+            # the element that does not own u_hat is coupled to the one that does
+            assert Gp[other, src] == 1
+            # and the owner does not see the other element through this face
+            if n > 2:
+                assert Gp[src, other] == 0 or (mu[other] > mu[src])
+
+
+def _l2_error(d, n, p, uh, u_exact):
+    import numpy.polynomial.legendre as npleg
+    q = p + 3
+    xg, wg = npleg.leggauss(q)
+    vals = ldg.evaluate(uh, d, n, p, xg)                    # (N, q^d)
+    mesh = ldg.Mesh(d, n)
+    h = mesh.h
+    W = wg
+    for _ in range(d - 1):
+        W = np.multiply.outer(W, wg)
+    W = W.reshape(-1) * (h / 2.0) ** d
+    err2 = 0.0
+    mean_h = 0.0
+    for e in range(mesh.N):
+        c = mesh.coords(e)
+        pts = [(c[a] + 0.5) * h + (h / 2.0) * xg for a in range(d)]
+        grids = np.meshgrid(*pts, indexing="ij")
+        ue = u_exact(*grids).reshape(-1)
+        err2 += np.sum(W * (vals[e] - ue) ** 2)
+        mean_h += np.sum(W * vals[e])
+    return np.sqrt(err2), mean_h
+
+
+def _solve_manufactured(d, n, p):
+    k2 = 2 * np.pi
+    if d == 2:
+        u = lambda x, y: np.sin(k2 * x) * np.sin(k2 * y)
+        f = lambda x, y: d * k2 ** 2 * np.sin(k2 * x) * np.sin(k2 * y)
+    else:
+        u = lambda x, y, z: np.sin(k2 * x) * np.sin(k2 * y) * np.sin(k2 * z)
+        f = lambda x, y, z: d * k2 ** 2 * np.sin(k2 * x) * np.sin(k2 * y) * np.sin(k2 * z)
+    op = ldg.assemble(d, n, p)
+    b = ldg.project_out_constant(ldg.l2_project(f, d, n, p), d, p, op.A.nblocks)
+    c = ldg.constant_vector(d, p, op.A.nblocks)
+    chat = c / np.linalg.norm(c)
+    # (A + chat chat^T) is nonsingular; with b orthogonal to c its solution is A^+ b
+    Areg = sp.csr_matrix(op.A.mat) + sp.csr_matrix(np.outer(chat, chat)) if op.A.mat.shape[0] < 2000 \
+        else None
+    if Areg is None:
+        x, info = spla.cg(op.A.mat, b, rtol=1e-13, maxiter=20000)
+        assert info == 0
+        x = x - (chat @ x) * chat
+    else:
+        x = np.linalg.solve(Areg.toarray(), b)
+    err, _ = _l2_error(d, n, p, x, u)
+    return err
+
+
+@pytest.mark.parametrize("d,p,ns", [(2, 1, (8, 16, 32)), (2, 2, (8, 16, 32)), (2, 3, (4, 8, 16)),
+                                    (3, 1, (4, 8, 16))])
+def test_manufactured_order_p_plus_1(d, p, ns):
+    """Optimal order p+1 (Sec. 2.1, last bullet) in the L2 norm on smooth data."""
+    errs = [_solve_manufactured(d, n, p) for n in ns]
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert rates[-1] >= p + 1 - 0.2, (errs, rates)
