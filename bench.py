@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark: 1e-10 solves/s of multigrid-preconditioned CG on one GB300.
+
+Workload (default): 3D periodic Poisson, uniform 48^3 mesh, LDG degree p = 3
+(64 dofs per element, 7.08M dofs), balanced SAI1 smoother with B1 pre / BT
+post sweeps (3 + 3), V-cycle down to 3^3 with a dense pseudo-inverse bottom,
+CG to a 1e-10 relative residual, seeded N(0,1) right-hand sides projected to
+zero mean.  One step = one complete solve (every row of the hot path: FP64
+operator apply + CG vector work, and per V-cycle the smoother sweeps,
+residuals, restrictions, prolongations and the bottom solve).
+
+`value` is the mixed-precision path (V-cycle in --precision, FP64 outer
+flexible CG); the plain FP64 GPU solver is timed beside it.  `e2e` repeats
+the mixed solves through the C-ABI with pinned host buffers (host<->device
+copies inside the timed region).  `roofline` covers the dominant kernel, the
+block-row apply (ldgmg bsr_kernel) on the finest level's SAI matrix.
+`cpu_baseline` / `--impl reference` time the CPU oracle on a bounded sample.
+
+Multi-GPU (torchrun): every rank runs an independent replica (the solves do
+not shard across GPUs); value = all ranks' solves / max elapsed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "1e-10 solves/s (mixed-precision V-cycle + FP64 CG)"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ldgmg", choices=["ldgmg", "reference"])
+    ap.add_argument("--n", type=int, default=48)
+    ap.add_argument("--p", type=int, default=3)
+    ap.add_argument("--dim", type=int, default=3)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-n", type=int, default=8)
+    ap.add_argument("--oracle-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (runs in a fresh single-threaded process)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(args):
+    import numpy as np
+
+    from oracle import krylov, ldg
+    from oracle import multigrid as mg
+    from paper_2412_12506_gb300.inputs import random_rhs
+    d, n, p = args.dim, args.oracle_n, args.p
+    N, b = n ** d, (p + 1) ** d
+    levels = mg.build_levels(d, n, p)
+    V = mg.VCycle(levels, "sai", 3, 3)
+    A = levels[0].A.mat
+    times, iters = [], []
+    t_end = time.perf_counter() + args.oracle_seconds
+    seed = 0
+    while time.perf_counter() < t_end or not times:
+        rhs = ldg.project_out_constant(random_rhs(N, b, seed=seed), d, p, N)
+        t0 = time.perf_counter()
+        _, k, _ = krylov.pcg(A, V, rhs, tol=args.tol)
+        times.append(time.perf_counter() - t0)
+        iters.append(k)
+        seed += 1
+    t = float(np.median(times))
+    scale = (args.n / n) ** d          # work per solve grows with the element count
+    return {"solve_s": t, "solves": len(times), "iters": iters, "n": n, "scale": scale,
+            "value": 1.0 / (t * scale)}
+
+
+def run_oracle_subprocess(args):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--oracle-n", str(args.oracle_n),
+           "--oracle-seconds", str(args.oracle_seconds), "--n", str(args.n), "--p", str(args.p),
+           "--dim", str(args.dim), "--tol", str(args.tol)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(s, args):
+    return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"CPU oracle (numpy/scipy, FP64, 1 thread): PCG+SAI1 V-cycle solves of the same problem "
+                       f"on a {s['n']}^{args.dim} mesh (p={args.p}), {s['solves']} solves, median "
+                       f"{s['solve_s']:.3f} s/solve, iterations {sorted(set(s['iters']))}; scaled by the element "
+                       f"ratio {s['scale']:.0f} to {args.n}^{args.dim} (iteration counts are mesh independent)")}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": float(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args)))
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        s = oracle_sample(args) if os.environ.get("OMP_NUM_THREADS") == "1" else run_oracle_subprocess(args)
+        cb = cpu_baseline_obj(s, args)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": s["value"], "unit": UNIT, "n_gpus": 0,
+            "steps": s["solves"], "warmup": 0, "ms_per_step": s["solve_s"] * s["scale"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"poisson{args.dim}d_n{args.n}_p{args.p}_sai1",
+                                             "inputs": "larger than L2"},
+            "cpu_baseline": cb,
+            "e2e": {"value": s["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    # the CPU oracle sample runs first, in a separate process, before any GPU work
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_obj(run_oracle_subprocess(args), args)
+
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    from paper_2412_12506_gb300 import ldgmg
+
+    d, n, p = args.dim, args.n, args.p
+    t0 = time.time()
+    op = ldgmg.Operator(d, n, p)
+    N, b = op.N, op.b
+    size = op.size
+    H = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision=args.precision)
+    H64 = H
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        H64 = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp64")
+    setup_s = time.time() - t0
+
+    gen = torch.Generator(device=dev).manual_seed(1234 + rank)
+    nrhs = args.steps + args.warmup
+    rhs = [op.project_kernel(torch.randn(size, dtype=torch.float64, device=dev, generator=gen))
+           for _ in range(min(nrhs, 8))]
+    xs = torch.empty(size, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(hier, count, warm, rhs_list, x_out):
+        iters = []
+        for i in range(warm):
+            hier.solve(rhs_list[i % len(rhs_list)], args.tol, x=x_out)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(count)]
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ldgmg.kernel_launches()
+        g0.record(stream)
+        for i in range(count):
+            ev[i][0].record(stream)
+            _, k, rr, st = hier.solve(rhs_list[(warm + i) % len(rhs_list)], args.tol, x=x_out)
+            ev[i][1].record(stream)
+            iters.append((k, rr))
+        g1.record(stream)
+        torch.cuda.synchronize()
+        launches = ldgmg.kernel_launches() - l0
+        barrier()
+        torch.cuda.synchronize()
+        lat = [a.elapsed_time(bq) for a, bq in ev]
+        return g0.elapsed_time(g1), lat, iters, launches
+
+    clocks = ldgmg_clock = None
+    if rank == 0:
+        ldgmg_clock = Clocks(local_rank)
+    total_ms, lat, iters, launches = timed(H, args.steps, args.warmup, rhs, xs)
+    if ldgmg_clock is not None:
+        clocks = ldgmg_clock.stop()
+    x_mixed = xs.clone()
+
+    # max over ranks
+    t_all = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    total_ms = float(t_all.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # plain FP64 GPU solver beside it
+    fp64 = None
+    if args.fp64_steps > 0:
+        x64 = torch.empty_like(xs)
+        ms64, lat64, it64, _ = timed(H64, args.fp64_steps, 1, rhs, x64)
+        # same rhs as the last mixed step for the error comparison
+        H64.solve(rhs[(args.warmup + args.steps - 1) % len(rhs)], args.tol, x=x64)
+        op.project_kernel(x64)
+        xm = op.project_kernel(x_mixed.clone())
+        err = float(torch.linalg.norm(xm - x64) / torch.linalg.norm(x64))
+        fp64 = {"solves_per_s": args.fp64_steps / (ms64 / 1e3), "p50_ms": float(np.median(lat64)),
+                "iterations": [k for k, _ in it64], "mixed_rel_err_vs_fp64": err}
+
+    # e2e: the same solves through the C-ABI with pinned host buffers
+    hrhs = [r.cpu().pin_memory() for r in rhs[:2]]
+    hx = torch.empty(size, dtype=torch.float64).pin_memory()
+    H.solve(hrhs[0], args.tol, x=hx)
+    torch.cuda.synchronize()
+    e_steps = max(2, args.steps // 2)
+    te = time.perf_counter()
+    for i in range(e_steps):
+        H.solve(hrhs[i % 2], args.tol, x=hx)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - te
+    e2e = {"value": world * e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": size * 8,
+           "d2h_bytes_per_step": size * 8}
+
+    # dominant kernel: block-row apply of the finest SAI matrix, in the V-cycle precision
+    inf = H.info(0)
+    es = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
+    vs = 8 if args.precision == "fp64" else 4
+    xv = torch.randn(size, device=dev, dtype=H.vdtype)
+    yv = torch.empty_like(xv)
+    reps = 20
+    for _ in range(3):
+        H.level_apply(0, ldgmg.MAT_B, xv, yv)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        H.level_apply(0, ldgmg.MAT_B, xv, yv)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kern_ms = k0.elapsed_time(k1) / reps
+    alg_bytes = inf["nnzb_S"] * b * b * es + 2 * size * vs   # matrix once, x and y once
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = alg_bytes / (kern_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": f"bsr_kernel<64,{args.precision}> finest-level B apply",
+                "bytes_per_launch": alg_bytes, "ms_per_launch": kern_ms,
+                "peak_source": "measured" if peaks else "fallback"}
+
+    # FP64 operator apply (the outer CG SpMV)
+    y64 = torch.empty_like(xs)
+    for _ in range(2):
+        op.apply(rhs[0], y64)
+    k0.record(stream)
+    for _ in range(10):
+        op.apply(rhs[0], y64)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    spmv_ms = k0.elapsed_time(k1) / 10
+    spmv_bytes = op.nnzb * b * b * 8 + 2 * size * 8
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    dtype = {"fp32": "f32 V-cycle + f64 CG", "bf16": "bf16-stored/f32 V-cycle + f64 CG", "fp64": "f64"}[args.precision]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": {"workload": f"poisson{d}d_n{n}_p{p}_sai1_cg1e-10", "dofs": size, "levels": H.nlevels,
+                   "smoother": "balanced SAI1, B1 pre / BT post, nu1 = nu2 = 3", "vcycle_precision": args.precision,
+                   "inputs": "larger than L2 (matrices ~ tens of GB)", "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "iterations": [k for k, _ in iters], "final_relres": max(rr for _, rr in iters),
+        "fp64_path": fp64,
+        "spmv_fp64": {"ms": spmv_ms, "GB_per_s": spmv_bytes / (spmv_ms / 1e3) / 1e9,
+                      "frac_of_hbm": spmv_bytes / (spmv_ms / 1e3) / 1e9 / peak},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches, "setup_s": setup_s,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

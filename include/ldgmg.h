@@ -1,0 +1,187 @@
+/*
+ * ldgmg — GB300-native multigrid for high-order LDG discretisations.
+ *
+ * C ABI of the hot path of the multigrid solvers in arXiv 2412.12506 (Saye,
+ * "A comparative study of efficient multigrid solvers for high-order local
+ * discontinuous Galerkin methods"): the element-block-sparse LDG operator,
+ * block-Jacobi and balanced block-SAI smoothers, the per-level residual,
+ * restriction and prolongation of the V-cycle (Algorithm 1), the bottom
+ * pseudo-inverse, and multigrid-preconditioned CG.
+ *
+ * Conventions shared by every call
+ *   - Mesh: uniform periodic Cartesian n^dim mesh of the unit square/cube
+ *     (dim = 2 or 3), h = 1/n.  Elements are numbered lexicographically with x
+ *     fastest: e = ix + n*iy (+ n*n*iz).
+ *   - Basis: tensor-product orthonormal Legendre modes (Sec. 2.1), b = (p+1)^dim
+ *     coefficients per element, mode m = kx + (p+1)*ky (+ (p+1)^2*kz).
+ *   - Vector layout: [element][mode][rhs]; with nrhs == 1 a vector is N*b
+ *     contiguous values.  FP64 vectors are double, V-cycle level vectors are
+ *     double (FP64 hierarchy) or float (FP32/BF16 hierarchy).
+ *   - Pointers named *_dev are device pointers owned by the caller; *_host are
+ *     host pointers owned by the caller.  Handles (ldgmg_op, ldgmg_hier) are
+ *     opaque; the library owns every allocation made behind them and releases
+ *     it in the matching *_free.
+ *   - Every call takes a cudaStream_t passed as void* (NULL = legacy default
+ *     stream) and enqueues its work on it; calls that return host results
+ *     synchronise that stream.
+ *   - Errors: every call returns an ldgmg_status and never aborts, traps or
+ *     exits.  On failure ldgmg_last_error() returns a thread-local message.
+ *   - Threading: a handle must not be used from two host threads at once.
+ */
+#ifndef LDGMG_H
+#define LDGMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LDGMG_OK = 0,
+  LDGMG_EINVAL = 1,        /* bad argument (null pointer, size, NaN/Inf input) */
+  LDGMG_ENOMEM = 2,        /* device or host allocation failed */
+  LDGMG_ECUDA = 3,         /* a CUDA runtime / library call failed */
+  LDGMG_ENOTCONV = 4,      /* Krylov solve hit max_iter; the iterate is still written */
+  LDGMG_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  LDGMG_EUNSUPPORTED = 6   /* valid request outside what this build implements */
+} ldgmg_status;
+
+enum { LDGMG_JACOBI = 0, LDGMG_SAI = 1 };                  /* smoother kind */
+enum { LDGMG_FORM_B1 = 0, LDGMG_FORM_BT = 1 };            /* SAI smoother form, Eqs. B1 / BT */
+enum { LDGMG_FP64 = 0, LDGMG_FP32 = 1, LDGMG_BF16 = 2 };   /* V-cycle precision */
+enum { LDGMG_MAT_A = 0, LDGMG_MAT_B = 1, LDGMG_MAT_BT = 2, LDGMG_MAT_D = 3 }; /* level matrices */
+
+typedef struct {
+  int dim;          /* 2 or 3 */
+  int n;            /* elements per axis, >= 1 */
+  int periodic;     /* must be 1 (periodic boundaries); 0 -> LDGMG_EUNSUPPORTED */
+} ldgmg_mesh;
+
+typedef struct {
+  int smoother;          /* LDGMG_JACOBI (Sec. 2.3.1) or LDGMG_SAI (Sec. 2.3.3) */
+  int sai_level;         /* ell: B has the block pattern of A^ell (Sec. 2.3.3); 0..2 */
+  int balance;           /* 1: balanced SAI, alpha_i = ||A_ii||_F^{-1/2} (Sec. 2.3.3) */
+  int nu1, nu2;          /* pre / post sweeps of Algorithm 1 (paper: 3 / 3, Sec. 2.2) */
+  double omega;          /* Jacobi damping (paper: 0.8, Eq. Jsmooth) */
+  int pre_form;          /* SAI form of the pre-sweeps  (B1 = Eq. B1) */
+  int post_form;         /* SAI form of the post-sweeps (BT = Eq. BT); B1/BT is symmetric */
+  int vcycle_precision;  /* LDGMG_FP64, LDGMG_FP32 or LDGMG_BF16 (matrix storage; FP32 accumulate) */
+  int max_iter;          /* Krylov iteration cap for ldgmg_solve */
+} ldgmg_setup_opts;
+
+typedef struct ldgmg_op ldgmg_op;
+typedef struct ldgmg_hier ldgmg_hier;
+
+/* Fill *o with the paper's defaults: SAI, ell = 1, balanced, nu1 = nu2 = 3,
+ * omega = 0.8, B1 pre / BT post, FP64, max_iter = 200. */
+void ldgmg_default_opts(ldgmg_setup_opts* o);
+
+/* Assemble the LDG Laplacian A = sum_a G_a^T M_mu G_a + E of Sec. 2.1 (display
+ * after Eq. scalar3) on the device, FP64.
+ *   mesh         uniform periodic mesh (see conventions).
+ *   p            polynomial degree, 1 <= p <= 5 (b = (p+1)^dim must be one of
+ *                4, 8, 9, 16, 25, 27, 36, 64).
+ *   mu_host      host array of N = n^dim per-element coefficients (> 0, finite),
+ *                or NULL for mu == 1.  Copied; the caller keeps ownership.
+ *   tau0         penalty constant: tau_f = tau0 * min(mu_L, mu_U) / h (> 0).
+ *   out          receives the handle; free with ldgmg_op_free.
+ * Fluxes are viscosity-upwinded one-sided (Sec. 2.1): u_hat from the element with
+ * the larger mu, from the lower element on ties.  Errors: EINVAL, EUNSUPPORTED,
+ * ENOMEM, ECUDA. */
+ldgmg_status ldgmg_assemble(const ldgmg_mesh* mesh, int p, const double* mu_host, double tau0,
+                            ldgmg_op** out);
+
+/* Sizes of an assembled operator: N elements, b dofs per element, nnzb stored blocks. */
+ldgmg_status ldgmg_op_info(const ldgmg_op* op, int64_t* N, int* b, int64_t* nnzb);
+
+/* y = A x in FP64 (Sec. 2.3: y_i = sum_j A_ij x_j).  x_dev, y_dev: device arrays
+ * of N*b*nrhs doubles, must not overlap.  nrhs must be 1 in this build. */
+ldgmg_status ldgmg_apply(ldgmg_op* op, const double* x_dev, double* y_dev, int nrhs, void* stream);
+
+/* Remove the kernel component (constant functions, Sec. 2.2 "Bottom solver"):
+ * v <- v - (c^T v / c^T c) c with c the coefficients of u == 1.  In place. */
+ldgmg_status ldgmg_project_kernel(ldgmg_op* op, double* v_dev, int nrhs, void* stream);
+
+/* Build the multigrid hierarchy (Sec. 2.2): levels n, n/2, ... while n is even
+ * and > 1, coarse operators by operator coarsening, the smoother of every
+ * level but the last (block-Jacobi inverse blocks or balanced SAI by
+ * Householder-QR least squares), and the bottom pseudo-inverse from a
+ * symmetric eigendecomposition.  Everything stays resident on the device.
+ * The op must outlive the hierarchy.  Errors: EINVAL, EUNSUPPORTED (e.g. a
+ * rank-deficient SAI least-squares column), ENOMEM, ECUDA. */
+ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* opts, void* stream,
+                         ldgmg_hier** out);
+
+/* Number of levels and, for level l, n, N, b and stored blocks of A_l and of the
+ * smoother matrix (B_l for SAI, D_l for Jacobi; 0 on the bottom level). */
+ldgmg_status ldgmg_hier_info(const ldgmg_hier* h, int level, int* nlevels, int* n, int64_t* N,
+                             int* b, int64_t* nnzb_A, int64_t* nnzb_S);
+
+/* x = V b: one V-cycle of Algorithm 1 with zero initial guess (the
+ * preconditioner V of Sec. 2.2), FP64 in and out; internally in the
+ * hierarchy's precision.  b_dev, x_dev: N*b doubles, may not overlap. */
+ldgmg_status ldgmg_vcycle(ldgmg_hier* h, const double* b_dev, double* x_dev, int nrhs,
+                          void* stream);
+
+/* Solve A x = rhs by V-preconditioned CG from x0 = 0 (Sec. 2.2, last paragraph)
+ * until ||rhs - A x||_2 <= tol ||rhs||_2.  rhs and x may be device pointers or
+ * host pointers (pinned or pageable); host buffers are staged through device
+ * memory owned by the hierarchy.  rhs must be consistent (orthogonal to the
+ * constants, see ldgmg_project_kernel).  iters[r] and relres[r] (host arrays of
+ * nrhs entries, may be NULL) receive the iteration count and the true final
+ * relative residual.  Returns ENOTCONV (with x written) if max_iter is hit,
+ * EINVAL for non-finite rhs. */
+ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x, int nrhs,
+                         int* iters, double* relres, void* stream);
+
+/* ---- per-level entry points (one step of the hot path each) --------------
+ * Level vectors are in the hierarchy's working type: double for an FP64
+ * hierarchy, float for FP32/BF16.  All pointers are device pointers. */
+
+/* y = M x for M in {A_l, B_l, B_l^T, D_l} (LDGMG_MAT_*). */
+ldgmg_status ldgmg_level_apply(ldgmg_hier* h, int level, int which, const void* x_dev,
+                               void* y_dev, void* stream);
+
+/* One smoother sweep on level l (Eq. Jsmooth, Eq. B1 or Eq. BT by `form`;
+ * Jacobi ignores form).  x_out may equal x_in.  x_is_zero != 0 treats x_in as
+ * zero without reading it (first pre-sweep of a coarse level). */
+ldgmg_status ldgmg_level_smooth(ldgmg_hier* h, int level, int form, const void* rhs_dev,
+                                const void* x_in_dev, void* x_out_dev, int x_is_zero,
+                                void* stream);
+
+/* Restricted residual of Algorithm 1: rc = I_l^T (rhs - A_l x) onto level l+1. */
+ldgmg_status ldgmg_level_restrict(ldgmg_hier* h, int level, const void* rhs_dev,
+                                  const void* x_dev, void* rc_dev, void* stream);
+
+/* Interpolate and correct (Algorithm 1): x += I_l xc, xc on level l+1. */
+ldgmg_status ldgmg_level_prolong(ldgmg_hier* h, int level, const void* xc_dev, void* x_dev,
+                                 void* stream);
+
+/* Bottom solve: x = A_bottom^+ rhs (FP64 pseudo-inverse, Sec. 2.2 "Bottom solver"). */
+ldgmg_status ldgmg_bottom_solve(ldgmg_hier* h, const void* rhs_dev, void* x_dev, void* stream);
+
+/* Copy a level matrix to host memory as FP64 block-CSR (values as stored on the
+ * device, converted to double).  row_ptr: N+1 int64, col: nnzb int32, vals:
+ * nnzb*b*b doubles, block (r, c) at vals[nz*b*b + r*b + c].  Any of the three
+ * may be NULL to skip it.  Test/inspection entry point. */
+ldgmg_status ldgmg_export_level(ldgmg_hier* h, int level, int which, int64_t* row_ptr,
+                                int32_t* col, double* vals);
+
+void ldgmg_op_free(ldgmg_op* op);
+void ldgmg_hier_free(ldgmg_hier* h);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded (all
+ * handles, streams and devices; setup-only kernels included).  For counting
+ * the launches of a timed region: read before and after it. */
+unsigned long long ldgmg_kernel_launches(void);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* ldgmg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDGMG_H */

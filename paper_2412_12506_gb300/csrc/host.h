@@ -1,0 +1,89 @@
+// Host-side setup of the LDG multigrid hierarchy (assembly, operator
+// coarsening, smoother construction).  Pure C++17; no CUDA.
+//
+// Every block-sparse operator is stored "pooled": a block-CSR pattern whose
+// nonzero blocks are ids into a pool of distinct dense blocks.  Pools
+// deduplicate by exact bytes, and every derived block is computed once per
+// distinct combination of input block ids (memoised).  On a uniform periodic
+// mesh each level therefore holds only a handful of distinct blocks and setup
+// cost is independent of N; near an interface the number of distinct blocks
+// grows with the interface length.  This generalises the SAI column cache of
+// the paper (a hash table plus a one-to-one stencil mapping, Sec. 4 item (i))
+// to every setup product.  Results are identical to computing every block
+// separately, because a block is reused only when its inputs are bitwise equal.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+namespace ldgmg {
+
+struct Basis1D {
+  int p = 0, q = 0;                // degree, q = p + 1 modes
+  std::vector<double> K;           // q*q, K[i*q+j] = int phi_i phi_j'
+  std::vector<double> lo, hi;      // phi_k(-1), phi_k(+1)
+  std::vector<double> P[2];        // q*q, P[s][i*q+j] = int phi_i(xi) phi_j((xi+2s-1)/2)
+};
+Basis1D make_basis(int p);
+
+struct Pool {
+  int b = 0;
+  std::vector<double> data;        // block id -> b*b values, row-major (r, c)
+  std::unordered_map<uint64_t, std::vector<uint32_t>> index;
+  uint32_t intern(const double* blk);
+  const double* get(uint32_t id) const { return data.data() + size_t(id) * b * b; }
+  uint32_t size() const { return b ? uint32_t(data.size() / (size_t(b) * b)) : 0; }
+};
+
+struct PBSR {
+  int64_t nrows = 0;
+  std::vector<int64_t> row_ptr;    // nrows + 1
+  std::vector<int32_t> col;        // sorted within each row
+  std::vector<uint32_t> id;        // pool id per stored block
+  Pool pool;
+  int64_t nnzb() const { return int64_t(col.size()); }
+  // pool id of block (r, c), or UINT32_MAX if structurally absent
+  uint32_t find(int64_t r, int32_t c) const;
+};
+
+struct HostLevel {
+  int dim = 0, n = 0, p = 0, b = 0;
+  int64_t N = 0;
+  double h = 0.0;
+  PBSR G[3];                       // discrete gradient per axis
+  std::vector<uint32_t> mmu;       // mu-weighted mass, one block per element
+  Pool mmu_pool;
+  PBSR E;                          // penalty
+  PBSR A;                          // sum_a G_a^T M_mu G_a + E
+  // smoother
+  PBSR B, BT;                      // SAI (BT holds the transposed blocks of B, row-wise)
+  std::vector<uint32_t> dinv;      // Jacobi: pseudo-inverse of A_ii per element
+  Pool dinv_pool;
+};
+
+struct SetupParams {
+  int smoother = 1;                // 0 Jacobi, 1 SAI
+  int sai_level = 1;
+  int balance = 1;
+};
+
+// Fine-level assembly (Sec. 2.1).  mu: N values or nullptr for mu == 1.
+// Returns an empty string on success, else an error message.
+std::string assemble_fine(HostLevel& L, int dim, int n, int p, const double* mu, double tau0);
+
+// Operator coarsening of `fine` onto n/2 (Sec. 2.2).
+std::string coarsen(const HostLevel& fine, HostLevel& coarse);
+
+// Coarse levels of `fine` (n/2, n/4, ... while n is even and > 1), appended
+// to `out` (which must not alias `fine`).
+std::string build_coarse_levels(const HostLevel& fine, std::vector<HostLevel>& out);
+
+// Smoother setup on one level (Jacobi blocks or balanced SAI, Sec. 2.3).
+std::string setup_smoother(HostLevel& L, const SetupParams& sp, int nthreads);
+
+// Dense copy of A (row-major, (N*b)^2) for the bottom solver.
+void dense_A(const HostLevel& L, std::vector<double>& out);
+
+}  // namespace ldgmg

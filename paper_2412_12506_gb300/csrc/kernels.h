@@ -1,0 +1,82 @@
+// Device kernels of the LDG multigrid hot path (launchers callable from host code).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace ldgmg {
+
+enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2 };
+
+// Block-CSR matrix resident on the device.  Block nz of row i is the dense
+// b x b block M_{i, col[nz]}, stored column-major: element (r, c) at
+// vals[nz*b*b + c*b + r], in the storage precision `prec`.
+struct DevMat {
+  int64_t nrows = 0, nnzb = 0;
+  int b = 0, prec = P_FP64;
+  int* row_ptr = nullptr;   // nrows + 1
+  int* col = nullptr;       // nnzb
+  void* vals = nullptr;     // nnzb * b * b elements
+};
+
+// Epilogue of a block-row apply, acc_i = sum_j M_ij x_j:
+enum BsrMode {
+  M_Y = 0,      // y_i = acc_i
+  M_RES = 1,    // y_i = rhs_i - acc_i
+  M_AXPY = 2,   // y_i = xin_i + s * acc_i   (xin may alias y)
+  M_SCALE = 3   // y_i = s * acc_i
+};
+
+bool block_size_supported(int b);
+
+// kernels enqueued by this library so far
+unsigned long long launches();
+
+// vector type: double when prec == P_FP64, float otherwise
+cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
+                      void* y, double s, cudaStream_t st);
+
+// vals[nz] = transpose(pool[ids[nz]]) converted to `prec` (pool blocks row-major FP64)
+cudaError_t expand_blocks(int64_t nnzb, int b, const uint32_t* ids, const double* pool, void* vals,
+                          int prec, cudaStream_t st);
+
+// P: device array of the 1D child-injection matrices P[s][i][j] (2*q*q doubles,
+// q = p + 1 <= 8).  Level vectors are double (vprec 0) or float (vprec 1).
+// rc_C = sum_children P_c^T rf_c
+cudaError_t restrict_apply(int d, int q, int n_fine, const double* P, const void* rf, void* rc,
+                           int vprec, cudaStream_t st);
+// xf_c += P_c xc_C
+cudaError_t prolong_apply(int d, int q, int n_fine, const double* P, const void* xc, void* xf,
+                          int vprec, cudaStream_t st);
+
+// y = Pinv v, Pinv dense n x n FP64 row-major; v, y of type vprec
+cudaError_t dense_gemv(int64_t n, const double* Pinv, const void* v, void* y, int vprec,
+                       cudaStream_t st);
+
+// conversions and BLAS-1 (FP64 unless stated)
+cudaError_t cast_d2f(int64_t n, const double* a, float* b, cudaStream_t st);
+cudaError_t cast_f2d(int64_t n, const float* a, double* b, cudaStream_t st);
+
+// deterministic dot: out[0] = sum_i a_i b_i (two-stage, fixed order).  partials
+// holds at least kDotBlocks doubles.
+constexpr int kDotBlocks = 1024;
+cudaError_t dot(int64_t n, const double* a, const double* b, double* partials, double* out,
+                cudaStream_t st);
+// out[0] = sum_e v[e*stride]  (sum of mode-0 coefficients)
+cudaError_t strided_sum(int64_t count, int64_t stride, const double* v, double* partials,
+                        double* out, cudaStream_t st);
+// v[e*stride] -= (*sum) / count
+cudaError_t strided_sub_mean(int64_t count, int64_t stride, double* v, const double* sum,
+                             cudaStream_t st);
+
+// CG scalar slots
+enum CgSlot { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZNEW = 3, S_RZOLD = 4, S_ALPHA = 5, S_BETA = 6,
+              S_BB = 7, S_TMP = 8, kCgSlots = 16 };
+cudaError_t cg_alpha(double* scal, cudaStream_t st);                    // alpha = rz / pq
+cudaError_t cg_update_xr(int64_t n, double* x, double* r, const double* p, const double* q,
+                         const double* scal, cudaStream_t st);          // x += a p ; r -= a q
+cudaError_t cg_beta(double* scal, int flexible, cudaStream_t st);       // beta, rz <- rz_new
+cudaError_t cg_update_p(int64_t n, double* p, const double* z, const double* scal,
+                        cudaStream_t st);                              // p = z + beta p
+
+}  // namespace ldgmg

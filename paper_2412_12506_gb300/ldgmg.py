@@ -1,0 +1,311 @@
+"""Python binding of libldgmg (include/ldgmg.h, include/ldgmg_host.h).
+
+Argument marshalling only: every computation runs in the C-ABI library
+(CUDA kernels for sm_103a, host C++ for setup).  PyTorch supplies device
+memory and streams.  Importing this module raises ImportError when the
+library has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libldgmg.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libldgmg.so not found at {LIB_PATH}; build it with "
+                      "`python -m paper_2412_12506_gb300.build` (or __graft_entry__.build())")
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, EUNSUPPORTED = range(7)
+JACOBI, SAI = 0, 1
+FORM_B1, FORM_BT = 0, 1
+FP64, FP32, BF16 = 0, 1, 2
+MAT_A, MAT_B, MAT_BT, MAT_D = 0, 1, 2, 3
+_PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+_FORM = {"B1": FORM_B1, "BT": FORM_BT}
+_SMOOTHER = {"jacobi": JACOBI, "sai": SAI}
+
+
+class LdgmgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ldgmg status {status}: {msg}")
+        self.status = status
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("periodic", ctypes.c_int)]
+
+
+class SetupOpts(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("sai_level", ctypes.c_int), ("balance", ctypes.c_int),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
+                ("pre_form", ctypes.c_int), ("post_form", ctypes.c_int),
+                ("vcycle_precision", ctypes.c_int), ("max_iter", ctypes.c_int)]
+
+
+_vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+_P = ctypes.POINTER
+_SIGS = {
+    "ldgmg_default_opts": (None, [_P(SetupOpts)]),
+    "ldgmg_assemble": (_i, [_P(Mesh), _i, _vp, _d, _P(_vp)]),
+    "ldgmg_op_info": (_i, [_vp, _P(_i64), _P(_i), _P(_i64)]),
+    "ldgmg_apply": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "ldgmg_project_kernel": (_i, [_vp, _vp, _i, _vp]),
+    "ldgmg_setup": (_i, [_vp, _P(SetupOpts), _vp, _P(_vp)]),
+    "ldgmg_hier_info": (_i, [_vp, _i, _P(_i), _P(_i), _P(_i64), _P(_i), _P(_i64), _P(_i64)]),
+    "ldgmg_vcycle": (_i, [_vp, _vp, _vp, _i, _vp]),
+    "ldgmg_solve": (_i, [_vp, _vp, _d, _vp, _i, _P(_i), _P(_d), _vp]),
+    "ldgmg_level_apply": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "ldgmg_level_smooth": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _vp]),
+    "ldgmg_level_restrict": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
+    "ldgmg_level_prolong": (_i, [_vp, _i, _vp, _vp, _vp]),
+    "ldgmg_bottom_solve": (_i, [_vp, _vp, _vp, _vp]),
+    "ldgmg_export_level": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "ldgmg_op_free": (None, [_vp]),
+    "ldgmg_hier_free": (None, [_vp]),
+    "ldgmg_last_error": (ctypes.c_char_p, []),
+    "ldgmg_kernel_launches": (ctypes.c_ulonglong, []),
+    "ldgmg_host_build": (_i, [_P(Mesh), _i, _vp, _d, _P(SetupOpts), _P(_vp)]),
+    "ldgmg_host_level_info": (_i, [_vp, _i, _P(_i), _P(_i), _P(_i64), _P(_i), _P(_i64), _P(_i64),
+                                   _P(_i64)]),
+    "ldgmg_host_export": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "ldgmg_host_free": (None, [_vp]),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def _check(status: int):
+    if status != OK:
+        raise LdgmgError(status, _lib.ldgmg_last_error().decode())
+
+
+def kernel_launches() -> int:
+    """Kernels enqueued by the library so far (ldgmg_kernel_launches)."""
+    return int(_lib.ldgmg_kernel_launches())
+
+
+def make_opts(smoother="sai", sai_level=1, balance=True, nu1=3, nu2=3, omega=0.8, pre="B1", post="BT",
+              precision="fp64", max_iter=200) -> SetupOpts:
+    o = SetupOpts()
+    _lib.ldgmg_default_opts(ctypes.byref(o))
+    o.smoother = _SMOOTHER[smoother]
+    o.sai_level = sai_level
+    o.balance = int(bool(balance))
+    o.nu1, o.nu2, o.omega = nu1, nu2, omega
+    o.pre_form, o.post_form = _FORM[pre], _FORM[post]
+    o.vcycle_precision = _PREC[precision]
+    o.max_iter = max_iter
+    return o
+
+
+def _mu_ptr(mu):
+    if mu is None:
+        return None, None
+    arr = np.ascontiguousarray(mu, dtype=np.float64)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# host-side setup inspection (no GPU)
+# ---------------------------------------------------------------------------
+
+class HostHierarchy:
+    """Host setup of ldgmg_setup without the device upload (include/ldgmg_host.h)."""
+
+    def __init__(self, dim, n, p, mu=None, tau0=1.0, **opts):
+        keep, mp = _mu_ptr(mu)
+        h = ctypes.c_void_p()
+        o = make_opts(**opts)
+        _check(_lib.ldgmg_host_build(ctypes.byref(Mesh(dim, n, 1)), p, mp, tau0, ctypes.byref(o),
+                                     ctypes.byref(h)))
+        self._h = h
+        self.nlevels = self.info(0)["nlevels"]
+
+    def info(self, level):
+        nl, n, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        N, nA, nS, dA = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.ldgmg_host_level_info(self._h, level, ctypes.byref(nl), ctypes.byref(n), ctypes.byref(N),
+                                          ctypes.byref(b), ctypes.byref(nA), ctypes.byref(nS),
+                                          ctypes.byref(dA)))
+        return dict(nlevels=nl.value, n=n.value, N=N.value, b=b.value, nnzb_A=nA.value, nnzb_S=nS.value,
+                    distinct_A=dA.value)
+
+    def export(self, level, which=MAT_A):
+        inf = self.info(level)
+        nnz = inf["nnzb_A"] if which == MAT_A else inf["nnzb_S"]
+        N, b = inf["N"], inf["b"]
+        rp = np.zeros(N + 1, np.int64)
+        col = np.zeros(nnz, np.int32)
+        vals = np.zeros((nnz, b, b), np.float64)
+        _check(_lib.ldgmg_host_export(self._h, level, which, rp.ctypes.data_as(_vp), col.ctypes.data_as(_vp),
+                                      vals.ctypes.data_as(_vp)))
+        return rp, col, vals
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.ldgmg_host_free(self._h)
+            self._h = None
+
+
+# ---------------------------------------------------------------------------
+# device API
+# ---------------------------------------------------------------------------
+
+class Operator:
+    """LDG operator A on the device (ldgmg_assemble)."""
+
+    def __init__(self, dim, n, p, mu=None, tau0=1.0):
+        keep, mp = _mu_ptr(mu)
+        h = ctypes.c_void_p()
+        _check(_lib.ldgmg_assemble(ctypes.byref(Mesh(dim, n, 1)), p, mp, tau0, ctypes.byref(h)))
+        self._h = h
+        N, b, nnz = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+        _check(_lib.ldgmg_op_info(h, ctypes.byref(N), ctypes.byref(b), ctypes.byref(nnz)))
+        self.dim, self.n, self.p = dim, n, p
+        self.N, self.b, self.nnzb = N.value, b.value, nnz.value
+        self.size = self.N * self.b
+
+    def apply(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(_lib.ldgmg_apply(self._h, _ptr(x), _ptr(y), 1, _stream(stream)))
+        return y
+
+    def project_kernel(self, v, stream=None):
+        _check(_lib.ldgmg_project_kernel(self._h, _ptr(v), 1, _stream(stream)))
+        return v
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.ldgmg_op_free(self._h)
+            self._h = None
+
+
+class Hierarchy:
+    """Multigrid hierarchy + smoothers + bottom solver (ldgmg_setup)."""
+
+    def __init__(self, op: Operator, stream=None, **opts):
+        self.op = op
+        self.opts = opts
+        o = make_opts(**opts)
+        h = ctypes.c_void_p()
+        _check(_lib.ldgmg_setup(op._h, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.precision = opts.get("precision", "fp64")
+        self.nlevels = self.info(0)["nlevels"]
+
+    @property
+    def vdtype(self):
+        import torch
+        return torch.float64 if self.precision == "fp64" else torch.float32
+
+    def info(self, level):
+        nl, n, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        N, nA, nS = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.ldgmg_hier_info(self._h, level, ctypes.byref(nl), ctypes.byref(n), ctypes.byref(N),
+                                    ctypes.byref(b), ctypes.byref(nA), ctypes.byref(nS)))
+        return dict(nlevels=nl.value, n=n.value, N=N.value, b=b.value, nnzb_A=nA.value, nnzb_S=nS.value)
+
+    def vcycle(self, b, x=None, stream=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        _check(_lib.ldgmg_vcycle(self._h, _ptr(b), _ptr(x), 1, _stream(stream)))
+        return x
+
+    def solve(self, rhs, tol=1e-10, x=None, stream=None, check=True):
+        """Returns (x, iterations, true relative residual, status).  rhs/x may be
+        CUDA or CPU tensors (host buffers are staged by the library)."""
+        import torch
+        if x is None:
+            x = torch.empty_like(rhs)
+        it, rr = ctypes.c_int(), ctypes.c_double()
+        st = _lib.ldgmg_solve(self._h, _ptr(rhs), tol, _ptr(x), 1, ctypes.byref(it), ctypes.byref(rr),
+                              _stream(stream))
+        if check and st not in (OK,):
+            _check(st)
+        return x, it.value, rr.value, st
+
+    # per-level entry points (vectors in the hierarchy's working dtype)
+    def level_apply(self, level, which, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(_lib.ldgmg_level_apply(self._h, level, which, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
+    def level_smooth(self, level, form, rhs, x_in=None, x_out=None, stream=None):
+        import torch
+        if x_out is None:
+            x_out = torch.empty_like(rhs)
+        xin = _ptr(x_in) if x_in is not None else None
+        _check(_lib.ldgmg_level_smooth(self._h, level, _FORM[form], _ptr(rhs), xin, _ptr(x_out),
+                                       int(x_in is None), _stream(stream)))
+        return x_out
+
+    def level_restrict(self, level, rhs, x, rc=None, stream=None):
+        import torch
+        if rc is None:
+            inf = self.info(level + 1)
+            rc = torch.empty(inf["N"] * inf["b"], dtype=rhs.dtype, device=rhs.device)
+        _check(_lib.ldgmg_level_restrict(self._h, level, _ptr(rhs), _ptr(x), _ptr(rc), _stream(stream)))
+        return rc
+
+    def level_prolong(self, level, xc, x, stream=None):
+        _check(_lib.ldgmg_level_prolong(self._h, level, _ptr(xc), _ptr(x), _stream(stream)))
+        return x
+
+    def bottom_solve(self, rhs, x=None, stream=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(rhs)
+        _check(_lib.ldgmg_bottom_solve(self._h, _ptr(rhs), _ptr(x), _stream(stream)))
+        return x
+
+    def export_level(self, level, which=MAT_A):
+        inf = self.info(level)
+        nnz = inf["nnzb_A"] if which == MAT_A else inf["nnzb_S"]
+        N, b = inf["N"], inf["b"]
+        rp = np.zeros(N + 1, np.int64)
+        col = np.zeros(nnz, np.int32)
+        vals = np.zeros((nnz, b, b), np.float64)
+        _check(_lib.ldgmg_export_level(self._h, level, which, rp.ctypes.data_as(_vp), col.ctypes.data_as(_vp),
+                                       vals.ctypes.data_as(_vp)))
+        return rp, col, vals
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.ldgmg_hier_free(self._h)
+            self._h = None
+
+
+def bsr_to_dense(rp, col, vals):
+    """Dense matrix from an exported block-CSR (tests/inspection)."""
+    N = len(rp) - 1
+    b = vals.shape[1] if vals.ndim == 3 else 0
+    D = np.zeros((N * b, N * b))
+    for i in range(N):
+        for z in range(rp[i], rp[i + 1]):
+            j = col[z]
+            D[i * b:(i + 1) * b, j * b:(j + 1) * b] += vals[z]
+    return D

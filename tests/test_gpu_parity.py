@@ -1,0 +1,297 @@
+"""GPU parity: every step of the hot path through the C-ABI, against the oracle.
+
+Tolerances (relative, max-abs error over max-abs value unless stated):
+  * FP64 kernels: 1e-12 for a single block-row apply / smoother sweep /
+    transfer (rounding of a k*b-term dot product, with k*b <= 448, plus the
+    1e-12 agreement of the independently assembled operators);
+    1e-10 for a whole V-cycle (about 10^2 chained kernels).
+  * FP32 / BF16 storage: the exported device matrix is compared with the
+    oracle's FP64 matrix rounded to the storage type (2^-23 / 2^-8 relative per
+    entry), and the apply is compared with the FP64 product of those stored
+    values (FP32 accumulation: 1e-5).
+  * Solves (Sec. 2.2 / 2.4): iteration counts equal to the oracle's within one;
+    FP64 solutions within 1e-9 relative L2 of the oracle's after removing the
+    constant mode; mixed-precision solves reach the 1e-10 relative residual
+    and their error against the FP64 oracle solution is reported and bounded.
+"""
+import numpy as np
+import pytest
+
+from oracle import krylov, ldg
+from oracle import multigrid as mg
+from paper_2412_12506_gb300.inputs import circle_mu, random_rhs, random_vector, square_mu
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2412_12506_gb300 import ldgmg   # raises if libldgmg.so is missing
+    return ldgmg
+
+
+DEV = "cuda"
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def mu_for(kind, d, n):
+    """None: mu == 1; "circle": seeded circle, contrast 1e4; "circle100": contrast
+    1e2; "square": the paper's (1/4, 3/4)^d inclusion, contrast 1e4 (Sec. 2.4.3)."""
+    if kind is None:
+        return None
+    if kind == "circle":
+        return circle_mu(d, n, seed=3, mu_in=1e4)
+    if kind == "circle100":
+        return circle_mu(d, n, seed=3, mu_in=1e2)
+    return square_mu(d, n, mu_in=1e4)
+
+
+_ORACLE = {}
+
+
+def oracle_solver(d, n, p, mu_kind, smoother, nu):
+    """Oracle hierarchy + V-cycle, cached across tests (the SAI setup is slow)."""
+    key = (d, n, p, mu_kind, smoother, nu)
+    if key not in _ORACLE:
+        levels = mg.build_levels(d, n, p, mu_for(mu_kind, d, n))
+        _ORACLE[key] = (levels, mg.VCycle(levels, smoother, nu, nu))
+    return _ORACLE[key]
+
+
+def cuda(v, dtype=torch.float64):
+    return torch.tensor(np.asarray(v), dtype=dtype, device=DEV)
+
+
+# every block size instantiated by the kernels, ragged row counts (N % 8 != 0)
+APPLY_CASES = [(2, 5, 1, None), (3, 3, 1, None), (2, 13, 2, None), (2, 11, 3, "circle"), (2, 7, 4, None),
+               (3, 5, 2, None), (2, 5, 5, None), (3, 5, 3, None), (2, 1, 2, None), (2, 2, 3, None)]
+
+
+@pytest.mark.parametrize("d,n,p,mu_kind", APPLY_CASES)
+def test_operator_apply_fp64(lib, d, n, p, mu_kind):
+    mu = mu_for(mu_kind, d, n)
+    op = lib.Operator(d, n, p, mu)
+    A = ldg.assemble(d, n, p, mu).A
+    x = random_vector(op.size, seed=n + p)
+    y = op.apply(cuda(x)).cpu().numpy()
+    assert rel(y, A.mat @ x) < 1e-12
+
+
+def test_project_kernel(lib):
+    d, n, p = 2, 6, 2
+    op = lib.Operator(d, n, p)
+    v = random_vector(op.size, 5)
+    got = op.project_kernel(cuda(v)).cpu().numpy()
+    assert rel(got, ldg.project_out_constant(v, d, p, n * n)) < 1e-14
+
+
+def _round(vals, prec):
+    if prec == "fp64":
+        return vals
+    t = torch.tensor(vals)
+    return (t.to(torch.float32) if prec == "fp32" else t.to(torch.float32).to(torch.bfloat16)).to(
+        torch.float64).numpy()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("d,n,p,smoother", [(2, 10, 3, "sai"), (3, 6, 3, "sai"), (2, 8, 2, "jacobi"),
+                                            (3, 4, 2, "jacobi")])
+def test_level_matrices_and_applies(lib, d, n, p, smoother, prec):
+    """Stored level matrices equal the oracle's (rounded to the storage type)
+    and every block-row apply (A, B, B^T, D) matches the FP64 product of the
+    stored values."""
+    mu = None
+    op = lib.Operator(d, n, p, mu)
+    H = lib.Hierarchy(op, smoother=smoother, nu1=2, nu2=2, precision=prec)
+    levels = mg.build_levels(d, n, p, mu)
+    ent = {"fp64": 1e-12, "fp32": 2.0 ** -23 * 1.01, "bf16": 2.0 ** -8 * 1.01}[prec]
+    acc_tol = 1e-12 if prec == "fp64" else 1e-5
+    vdt = H.vdtype
+    for l, lv in enumerate(levels[:-1]):
+        mats = [(lib.MAT_A, lv.A.dense())]
+        if smoother == "sai":
+            B = mg.SAI(lv.A, 1).B.dense()
+            mats += [(lib.MAT_B, B), (lib.MAT_BT, B.T)]
+        else:
+            jac = mg.Jacobi(lv.A)
+            Dd = np.zeros_like(lv.A.dense())
+            b = lv.b
+            for i in range(lv.N):
+                Dd[i * b:(i + 1) * b, i * b:(i + 1) * b] = jac.Dinv[i]
+            mats += [(lib.MAT_D, Dd)]
+        x = random_vector(lv.N * lv.b, seed=l)
+        for which, Mo in mats:
+            rp, col, vals = H.export_level(l, which)
+            Md = lib.bsr_to_dense(rp, col, vals)
+            ref_round = lib.bsr_to_dense(rp, col, _round(
+                np.stack([Mo[i * lv.b:(i + 1) * lv.b, j * lv.b:(j + 1) * lv.b]
+                          for i in range(lv.N) for j in col[rp[i]:rp[i + 1]]]), prec))
+            # entries: stored value vs oracle value rounded to the storage type
+            scale = np.abs(Mo).max()
+            assert np.abs(Md - Mo).max() <= ent * scale + 1e-12 * scale, (l, which)
+            # one storage ulp: torch rounds double -> float -> bf16, the device double -> bf16
+            assert np.abs(Md - ref_round).max() <= max(2 * ent, 1e-12) * scale, (l, which)
+            xin = x.astype(np.float32).astype(np.float64) if prec != "fp64" else x
+            y = H.level_apply(l, which, cuda(xin, vdt)).cpu().double().numpy()
+            assert rel(y, Md @ xin) < acc_tol, (l, which)
+
+
+@pytest.mark.parametrize("d,n,p,smoother,mu_kind", [(2, 8, 2, "jacobi", None), (2, 8, 3, "sai", "circle"),
+                                                    (3, 4, 3, "sai", None), (2, 12, 1, "sai", "square")])
+def test_smoother_restrict_prolong_bottom_fp64(lib, d, n, p, smoother, mu_kind):
+    mu = mu_for(mu_kind, d, n)
+    op = lib.Operator(d, n, p, mu)
+    H = lib.Hierarchy(op, smoother=smoother, nu1=2, nu2=2)
+    levels = mg.build_levels(d, n, p, mu)
+    V = mg.VCycle(levels, smoother, 2, 2)
+    # With a 1e4 contrast the balanced SAI least-squares problems are less well
+    # conditioned (condition ~1e3-1e4), so the oracle's LAPACK QR and the
+    # library's Householder QR give B entries that agree to ~1e-12 relative,
+    # not to rounding; the sweep inherits that.  The kernel itself is pinned at
+    # 1e-12 against the stored values in test_level_matrices_and_applies.
+    tol = 1e-12 if mu_kind is None else 1e-10
+    for l, lv in enumerate(levels[:-1]):
+        size = lv.N * lv.b
+        rhs, x = random_vector(size, 10 + l), random_vector(size, 20 + l)
+        for form in ("B1", "BT"):
+            got = H.level_smooth(l, form, cuda(rhs), cuda(x)).cpu().numpy()
+            assert rel(got, lv.smoother.sweep(x, rhs, form)) < tol, (l, form)
+            got0 = H.level_smooth(l, form, cuda(rhs)).cpu().numpy()         # x = 0
+            assert rel(got0, lv.smoother.sweep(np.zeros(size), rhs, form)) < tol
+        # in place
+        xt = cuda(x)
+        H.level_smooth(l, "B1", cuda(rhs), xt, xt)
+        assert rel(xt.cpu().numpy(), lv.smoother.sweep(x, rhs, "B1")) < tol
+        rc = H.level_restrict(l, cuda(rhs), cuda(x)).cpu().numpy()
+        assert rel(rc, lv.I.mat.T @ (rhs - lv.A.mat @ x)) < 1e-12
+        xc = random_vector(levels[l + 1].N * lv.b, 30 + l)
+        got = H.level_prolong(l, cuda(xc), cuda(x)).cpu().numpy()
+        assert rel(got, x + lv.I.mat @ xc) < 1e-13
+    bot = levels[-1]
+    rb = ldg.project_out_constant(random_vector(bot.N * bot.b, 40), d, p, bot.N)
+    assert rel(H.bottom_solve(cuda(rb)).cpu().numpy(), V.bottom_pinv @ rb) < 1e-10
+    # one whole V-cycle (Algorithm 1, zero initial guess)
+    r0 = ldg.project_out_constant(random_vector(levels[0].N * levels[0].b, 41), d, p, levels[0].N)
+    assert rel(H.vcycle(cuda(r0)).cpu().numpy(), V(r0)) < 1e-10
+
+
+SOLVE_CASES = [
+    # (d, n, p, smoother, nu, mu)   -- includes the 16^2 p=2 Jacobi 2/2 workload at full size
+    (2, 16, 2, "jacobi", 2, None),
+    (2, 32, 3, "sai", 3, "square"),
+    (2, 32, 3, "jacobi", 3, "circle"),
+    (2, 32, 2, "sai", 3, "circle100"),
+    (2, 16, 1, "sai", 3, "square"),
+    (3, 6, 3, "sai", 3, None),
+    (3, 8, 2, "jacobi", 3, None),
+]
+
+
+@pytest.mark.parametrize("d,n,p,smoother,nu,mu_kind", SOLVE_CASES)
+def test_solve_fp64_matches_oracle(lib, d, n, p, smoother, nu, mu_kind):
+    mu = mu_for(mu_kind, d, n)
+    N, b = n ** d, (p + 1) ** d
+    rhs = ldg.project_out_constant(random_rhs(N, b, seed=7), d, p, N)
+    levels, V = oracle_solver(d, n, p, mu_kind, smoother, nu)
+    xo, ko, _ = krylov.pcg(levels[0].A.mat, V, rhs, tol=1e-10)
+    op = lib.Operator(d, n, p, mu)
+    H = lib.Hierarchy(op, smoother=smoother, nu1=nu, nu2=nu)
+    x, k, rr, st = H.solve(cuda(rhs), tol=1e-10)
+    assert st == lib.OK
+    assert abs(k - ko) <= 1, (k, ko)
+    assert rr <= 1.05e-10
+    xg = ldg.project_out_constant(x.cpu().numpy(), d, p, N)
+    xo = ldg.project_out_constant(xo, d, p, N)
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("d,n,p,smoother,nu,mu_kind", [(2, 32, 3, "sai", 3, "square"), (3, 6, 3, "sai", 3, None),
+                                                       (2, 16, 2, "jacobi", 2, None)])
+def test_solve_mixed_precision_reaches_fp64_accuracy(lib, d, n, p, smoother, nu, mu_kind, prec):
+    """FP32/BF16 V-cycle + FP64 flexible CG reaches the same 1e-10 residual; the
+    error against the FP64 oracle solution is bounded (and printed)."""
+    mu = mu_for(mu_kind, d, n)
+    N, b = n ** d, (p + 1) ** d
+    rhs = ldg.project_out_constant(random_rhs(N, b, seed=8), d, p, N)
+    levels, V = oracle_solver(d, n, p, mu_kind, smoother, nu)
+    xo, ko, _ = krylov.pcg(levels[0].A.mat, V, rhs, tol=1e-12)
+    op = lib.Operator(d, n, p, mu)
+    H = lib.Hierarchy(op, smoother=smoother, nu1=nu, nu2=nu, precision=prec)
+    x, k, rr, st = H.solve(cuda(rhs), tol=1e-10)
+    assert st == lib.OK
+    assert rr <= 1.05e-10
+    xg = ldg.project_out_constant(x.cpu().numpy(), d, p, N)
+    xo = ldg.project_out_constant(xo, d, p, N)
+    err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
+    print(f"\n{prec} d={d} n={n} p={p} {smoother}: iters {k} (fp64 oracle {ko}), rel err vs FP64 oracle {err:.2e}")
+    assert err < 1e-7
+    assert k <= ko + (3 if prec == "fp32" else 8)
+
+
+def test_solve_host_buffers_and_errors(lib):
+    d, n, p = 2, 8, 2
+    op = lib.Operator(d, n, p)
+    H = lib.Hierarchy(op, smoother="sai")
+    rhs = ldg.project_out_constant(random_rhs(n * n, 9, seed=3), d, p, n * n)
+    xd, kd, _, _ = H.solve(cuda(rhs))
+    xh = torch.zeros(op.size, dtype=torch.float64).pin_memory()
+    xh2, kh, rr, st = H.solve(torch.tensor(rhs).pin_memory(), x=xh)
+    assert st == lib.OK and kh == kd
+    assert np.array_equal(xh2.numpy(), xd.cpu().numpy())
+    xp, kp, _, _ = H.solve(torch.tensor(rhs))          # pageable host memory
+    assert np.array_equal(xp.numpy(), xd.cpu().numpy())
+    bad = rhs.copy()
+    bad[3] = np.nan
+    with pytest.raises(lib.LdgmgError) as e:
+        H.solve(cuda(bad))
+    assert e.value.status == lib.EINVAL
+    Hc = lib.Hierarchy(op, smoother="sai", max_iter=1)
+    x1, k1, rr1, st1 = Hc.solve(cuda(rhs), check=False)
+    assert st1 == lib.ENOTCONV and k1 == 1 and np.isfinite(rr1)
+    zero = torch.zeros(op.size, dtype=torch.float64, device=DEV)
+    xz, kz, rz, sz = H.solve(zero)
+    assert sz == lib.OK and kz == 0 and float(xz.abs().max()) == 0.0
+
+
+def test_repeat_solves_are_bitwise_deterministic(lib):
+    d, n, p = 3, 6, 3
+    op = lib.Operator(d, n, p)
+    H = lib.Hierarchy(op, smoother="sai", precision="fp32")
+    rhs = cuda(ldg.project_out_constant(random_rhs(n ** 3, 64, seed=4), d, p, n ** 3))
+    x1 = H.solve(rhs)[0].clone()
+    x2 = H.solve(rhs)[0]
+    assert torch.equal(x1, x2)
+
+
+def test_full_size_poisson3d_apply_sampled_rows(lib):
+    """48^3, p = 3 (7.08M dofs): sampled rows of y = A x against the oracle's
+    translation-invariant stencil.  With mu == 1 every block row of A is the
+    same set of 7 blocks; A at h scales as h^{d-2} (the 8^3 oracle operator
+    times 8/48 in 3D)."""
+    d, n, p, nref = 3, 48, 3, 8
+    op = lib.Operator(d, n, p)
+    b = op.b
+    x = torch.randn(op.size, dtype=torch.float64, device=DEV, generator=torch.Generator(DEV).manual_seed(0))
+    y = op.apply(x).cpu().numpy()
+    xs = x.cpu().numpy()
+    Aref = ldg.assemble(d, nref, p).A
+    mref, mfull = ldg.Mesh(d, nref), ldg.Mesh(d, n)
+    scale = nref / n
+    rng = np.random.default_rng(1)
+    for i in rng.integers(0, op.N, 64):
+        ci = mfull.coords(int(i))
+        acc = np.zeros(b)
+        for jr in Aref.row_pattern(0):            # stencil of the reference row 0
+            off = mref.coords(int(jr))
+            off = [o if o <= nref // 2 else o - nref for o in off]
+            j = mfull.index(tuple(ci[a] + off[a] for a in range(d)))
+            acc += scale * Aref.block(0, int(jr)) @ xs[j * b:(j + 1) * b]
+        assert rel(y[i * b:(i + 1) * b], acc) < 1e-12
