@@ -34,6 +34,18 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "1e-10 solves/s (mixed-precision V-cycle + FP64 CG)"
+
+# DRAM bytes (read + write) per block row of the finest-level B apply, from one
+# ncu capture on the 16^3 case (profiles/bsr_kernel_fp32_poisson3d_n16_p3.md),
+# scaled by rows to the launch timed here; valid only for the kernel source it
+# was taken on (sha256 prefix of kernels.cu), else reported as null.
+TRAFFIC_PER_ROW = {"fp32": (476.5e6 / 4096, "3cb9903e9aba4e64")}
+
+
+def kernel_source_hash():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2412_12506_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 UNIT = "solves/s"
 
 
@@ -303,12 +315,15 @@ def main():
     torch.cuda.synchronize()
     kern_ms = k0.elapsed_time(k1) / reps
     alg_bytes = inf["nnzb_S"] * b * b * es + 2 * size * vs   # matrix once, x and y once
+    traffic = None
+    if args.precision in TRAFFIC_PER_ROW and kernel_source_hash() == TRAFFIC_PER_ROW[args.precision][1]:
+        traffic = TRAFFIC_PER_ROW[args.precision][0] * inf["N"]
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = alg_bytes / (kern_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"bsr_kernel<64,{args.precision}> finest-level B apply",
+                "traffic": traffic, "kernel": f"bsr_kernel<64,{args.precision}> finest-level B apply",
                 "bytes_per_launch": alg_bytes, "ms_per_launch": kern_ms,
                 "peak_source": "measured" if peaks else "fallback"}
 

