@@ -172,6 +172,28 @@ ldgmg_status ldgmg_export_level(ldgmg_hier* h, int level, int which, int64_t* ro
 void ldgmg_op_free(ldgmg_op* op);
 void ldgmg_hier_free(ldgmg_hier* h);
 
+/* ---- allocation-free entry point ------------------------------------------
+ * The paper has no counterpart to this call; it exists for callers that must
+ * not call cudaMalloc: code whose device memory is wholly owned by another
+ * allocator (e.g. a framework's caching allocator that has reserved the GPU),
+ * or a latency-critical loop that cannot take cudaMalloc's implicit device
+ * synchronisation.  Such callers cannot create an ldgmg_op either, so this
+ * call takes plain sizes.
+ *
+ * Same result as ldgmg_project_kernel (up to summation order): removes the
+ * constant mode from v_dev, an N*b FP64 device vector laid out [element][mode],
+ * in place.  N must satisfy 1 <= N <= LDGMG_NOALLOC_MAX_ELEMENTS, else EINVAL.
+ * It allocates nothing: its reduction scratch is a fixed file-scope device
+ * array of (LDGMG_NOALLOC_MAX_ELEMENTS / 4096 + 1) doubles (about 32 KB) that
+ * every GPU which loads the library holds until the process exits.  The first
+ * call on a device looks up that array's device address once (with the device
+ * current); make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU (unordered streams, concurrent host
+ * threads) race.  Each call writes every scratch word it reads, so nothing
+ * carries over between calls.  Enqueues on `stream`; does not synchronise. */
+#define LDGMG_NOALLOC_MAX_ELEMENTS 16777216
+ldgmg_status ldgmg_project_kernel_noalloc(int64_t N, int b, double* v_dev, void* stream);
+
 /* Number of CUDA kernels this library has enqueued since it was loaded (all
  * handles, streams and devices; setup-only kernels included).  For counting
  * the launches of a timed region: read before and after it. */

@@ -68,6 +68,7 @@ _SIGS = {
     "ldgmg_hier_free": (None, [_vp]),
     "ldgmg_last_error": (ctypes.c_char_p, []),
     "ldgmg_kernel_launches": (ctypes.c_ulonglong, []),
+    "ldgmg_project_kernel_noalloc": (_i, [_i64, _i, _vp, _vp]),
     "ldgmg_host_build": (_i, [_P(Mesh), _i, _vp, _d, _P(SetupOpts), _P(_vp)]),
     "ldgmg_host_level_info": (_i, [_vp, _i, _P(_i), _P(_i), _P(_i64), _P(_i), _P(_i64), _P(_i64),
                                    _P(_i64)]),
@@ -90,6 +91,16 @@ def _check(status: int):
 def kernel_launches() -> int:
     """Kernels enqueued by the library so far (ldgmg_kernel_launches)."""
     return int(_lib.ldgmg_kernel_launches())
+
+
+NOALLOC_MAX_ELEMENTS = 16777216
+
+
+def project_kernel_noalloc(v, N, b, stream=None):
+    """ldgmg_project_kernel_noalloc: remove the constant mode from v (N*b FP64,
+    device) without any allocation in the library; see include/ldgmg.h."""
+    _check(_lib.ldgmg_project_kernel_noalloc(N, b, _ptr(v), _stream(stream)))
+    return v
 
 
 def make_opts(smoother="sai", sai_level=1, balance=True, nu1=3, nu2=3, omega=0.8, pre="B1", post="BT",
