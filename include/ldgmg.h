@@ -14,9 +14,11 @@
  *     fastest: e = ix + n*iy (+ n*n*iz).
  *   - Basis: tensor-product orthonormal Legendre modes (Sec. 2.1), b = (p+1)^dim
  *     coefficients per element, mode m = kx + (p+1)*ky (+ (p+1)^2*kz).
- *   - Vector layout: [element][mode][rhs]; with nrhs == 1 a vector is N*b
- *     contiguous values.  FP64 vectors are double, V-cycle level vectors are
- *     double (FP64 hierarchy) or float (FP32/BF16 hierarchy).
+ *   - Vector layout: a vector is N*b contiguous values [element][mode]; calls
+ *     taking nrhs > 1 right-hand sides take nrhs such vectors one after another
+ *     ([rhs][element][mode]).  FP64 vectors are double; V-cycle level vectors
+ *     are double (FP64 hierarchy) or float (FP32/BF16 hierarchy); batched level
+ *     vectors (ldgmg_level_apply_batched) are float [element][rhs][mode].
  *   - Pointers named *_dev are device pointers owned by the caller; *_host are
  *     host pointers owned by the caller.  Handles (ldgmg_op, ldgmg_hier) are
  *     opaque; the library owns every allocation made behind them and releases
@@ -69,13 +71,16 @@ typedef struct {
   int post_form;         /* SAI form of the post-sweeps (BT = Eq. BT); B1/BT is symmetric */
   int vcycle_precision;  /* LDGMG_FP64, LDGMG_FP32 or LDGMG_BF16 (matrix storage; FP32 accumulate) */
   int max_iter;          /* Krylov iteration cap for ldgmg_solve */
+  int max_rhs;           /* right-hand sides per call, 1..128.  > 1 builds the batched
+                            hierarchy: BF16 storage (vcycle_precision must be LDGMG_BF16),
+                            b = 16 or 64, V-cycle block applies on tensor cores */
 } ldgmg_setup_opts;
 
 typedef struct ldgmg_op ldgmg_op;
 typedef struct ldgmg_hier ldgmg_hier;
 
 /* Fill *o with the paper's defaults: SAI, ell = 1, balanced, nu1 = nu2 = 3,
- * omega = 0.8, B1 pre / BT post, FP64, max_iter = 200. */
+ * omega = 0.8, B1 pre / BT post, FP64, max_iter = 200, max_rhs = 1. */
 void ldgmg_default_opts(ldgmg_setup_opts* o);
 
 /* Assemble the LDG Laplacian A = sum_a G_a^T M_mu G_a + E of Sec. 2.1 (display
@@ -96,12 +101,13 @@ ldgmg_status ldgmg_assemble(const ldgmg_mesh* mesh, int p, const double* mu_host
 /* Sizes of an assembled operator: N elements, b dofs per element, nnzb stored blocks. */
 ldgmg_status ldgmg_op_info(const ldgmg_op* op, int64_t* N, int* b, int64_t* nnzb);
 
-/* y = A x in FP64 (Sec. 2.3: y_i = sum_j A_ij x_j).  x_dev, y_dev: device arrays
- * of N*b*nrhs doubles, must not overlap.  nrhs must be 1 in this build. */
+/* y = A x in FP64 (Sec. 2.3: y_i = sum_j A_ij x_j) for nrhs >= 1 stacked
+ * vectors.  x_dev, y_dev: device arrays of N*b*nrhs doubles, must not overlap. */
 ldgmg_status ldgmg_apply(ldgmg_op* op, const double* x_dev, double* y_dev, int nrhs, void* stream);
 
 /* Remove the kernel component (constant functions, Sec. 2.2 "Bottom solver"):
- * v <- v - (c^T v / c^T c) c with c the coefficients of u == 1.  In place. */
+ * v <- v - (c^T v / c^T c) c with c the coefficients of u == 1, for each of the
+ * nrhs stacked vectors.  In place. */
 ldgmg_status ldgmg_project_kernel(ldgmg_op* op, double* v_dev, int nrhs, void* stream);
 
 /* Build the multigrid hierarchy (Sec. 2.2): levels n, n/2, ... while n is even
@@ -121,18 +127,23 @@ ldgmg_status ldgmg_hier_info(const ldgmg_hier* h, int level, int* nlevels, int* 
 
 /* x = V b: one V-cycle of Algorithm 1 with zero initial guess (the
  * preconditioner V of Sec. 2.2), FP64 in and out; internally in the
- * hierarchy's precision.  b_dev, x_dev: N*b doubles, may not overlap. */
+ * hierarchy's precision.  b_dev, x_dev: nrhs stacked vectors (nrhs <=
+ * max_rhs of the setup), may not overlap. */
 ldgmg_status ldgmg_vcycle(ldgmg_hier* h, const double* b_dev, double* x_dev, int nrhs,
                           void* stream);
 
 /* Solve A x = rhs by V-preconditioned CG from x0 = 0 (Sec. 2.2, last paragraph)
- * until ||rhs - A x||_2 <= tol ||rhs||_2.  rhs and x may be device pointers or
- * host pointers (pinned or pageable); host buffers are staged through device
- * memory owned by the hierarchy.  rhs must be consistent (orthogonal to the
- * constants, see ldgmg_project_kernel).  iters[r] and relres[r] (host arrays of
- * nrhs entries, may be NULL) receive the iteration count and the true final
- * relative residual.  Returns ENOTCONV (with x written) if max_iter is hit,
- * EINVAL for non-finite rhs. */
+ * until ||rhs - A x||_2 <= tol ||rhs||_2, for nrhs <= max_rhs stacked right-hand
+ * sides at once (batched hierarchy when nrhs > 1).  Every right-hand side keeps
+ * its own CG scalars and stops updating once it has converged, so its result
+ * is the same whether it is solved alone or in a batch.  rhs and x may be
+ * device pointers or host pointers (pinned or pageable); host buffers are
+ * staged through device memory owned by the hierarchy.  rhs must be
+ * consistent (orthogonal to the constants, see ldgmg_project_kernel).
+ * iters[r] and relres[r] (host arrays of nrhs entries, may be NULL) receive
+ * the iteration count and the true final relative residual of right-hand side
+ * r.  Returns ENOTCONV (with x written) if max_iter is hit, EINVAL for
+ * non-finite rhs, ETIMEOUT if a bounded device wait gave up. */
 ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x, int nrhs,
                          int* iters, double* relres, void* stream);
 
@@ -143,6 +154,13 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
 /* y = M x for M in {A_l, B_l, B_l^T, D_l} (LDGMG_MAT_*). */
 ldgmg_status ldgmg_level_apply(ldgmg_hier* h, int level, int which, const void* x_dev,
                                void* y_dev, void* stream);
+
+/* Batched block-row apply on level l: y = M x for nrhs right-hand sides, float
+ * vectors laid out [element][rhs][mode] (N*b*nrhs floats).  On a batched
+ * hierarchy (max_rhs > 1) this is the tensor-core kernel; otherwise the
+ * CUDA-core kernel (FP32/BF16 hierarchies only).  nrhs <= 128. */
+ldgmg_status ldgmg_level_apply_batched(ldgmg_hier* h, int level, int which, int nrhs, const float* x_dev,
+                                       float* y_dev, void* stream);
 
 /* One smoother sweep on level l (Eq. Jsmooth, Eq. B1 or Eq. BT by `form`;
  * Jacobi ignores form).  x_out may equal x_in.  x_is_zero != 0 treats x_in as

@@ -2,11 +2,13 @@
 //
 // Setup (assembly, operator coarsening, smoother construction) runs in host
 // C++ on pooled block storage (host.cpp), then every level matrix is
-// expanded on the device into explicit block-CSR in the requested precision.
-// The bottom pseudo-inverse comes from a cuSOLVER FP64 eigendecomposition on
-// the device.  Everything the V-cycle and CG touch afterwards is device
-// resident; the host only enqueues kernels and reads one scalar per CG
-// iteration for the stopping test.
+// expanded on the device into explicit block-CSR in the requested precision
+// (column-major blocks for the CUDA-core kernel, row-major BF16 blocks for
+// the tensor-core batched kernel).  The bottom pseudo-inverse comes from a
+// cuSOLVER FP64 eigendecomposition on the device.  Everything the V-cycle and
+// CG touch afterwards is device resident; the host only enqueues kernels and
+// reads the per-right-hand-side residual norms once per CG iteration for the
+// stopping test.
 #include "ldgmg.h"
 
 #include <cublas_v2.h>
@@ -69,13 +71,14 @@ static void free_mat(DevMat& M) {
   M = DevMat();
 }
 
-// Expand a pooled host matrix into an explicit device block-CSR of precision prec.
-static ldgmg_status upload(const PBSR& H, int b, int prec, DevMat& M, cudaStream_t st) {
+// Expand a pooled host matrix into an explicit device block-CSR.
+static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat& M, cudaStream_t st) {
   if (H.nnzb() >= (int64_t(1) << 31)) return fail(LDGMG_EUNSUPPORTED, "more than 2^31 blocks");
   M.nrows = H.nrows;
   M.nnzb = H.nnzb();
   M.b = b;
   M.prec = prec;
+  M.row_major = row_major;
   std::vector<int> rp(H.row_ptr.begin(), H.row_ptr.end());
   CKS(dalloc(&M.row_ptr, rp.size() * sizeof(int)));
   CKS(dalloc(&M.col, H.col.size() * sizeof(int)));
@@ -90,7 +93,7 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, DevMat& M, cudaStream
     CK(cudaMemcpyAsync(d_ids, H.id.data(), H.id.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_pool, H.pool.data.data(), H.pool.data.size() * sizeof(double),
                        cudaMemcpyHostToDevice, st));
-    CK(expand_blocks(M.nnzb, b, d_ids, d_pool, M.vals, prec, st));
+    CK(expand_blocks(M.nnzb, b, d_ids, d_pool, M.vals, prec, row_major, st));
   }
   CK(cudaStreamSynchronize(st));
   cudaFree(d_ids);
@@ -104,7 +107,7 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, DevMat& M, cudaStream
 
 struct ldgmg_op {
   HostLevel host;
-  DevMat A;              // FP64 finest-level operator
+  DevMat A;              // FP64 finest-level operator (column-major blocks)
   double tau0 = 1.0;
   double* partials = nullptr;
   double* scal = nullptr;
@@ -116,7 +119,7 @@ struct DevLevel {
   int b = 0;
   DevMat A, S, ST;       // A_l; smoother matrix (B_l or D_l); B_l^T (SAI only)
   bool own_A = true;
-  void* rhs = nullptr;
+  void* rhs = nullptr;   // level vectors, room for max_rhs right-hand sides
   void* x = nullptr;
   void* r = nullptr;
 };
@@ -127,20 +130,52 @@ struct ldgmg_hier {
   int prec = P_FP64;
   int vprec = 0;         // 0: double level vectors, 1: float
   size_t vsz = 8;
+  int Rmax = 1;          // right-hand sides per call
+  bool batched = false;  // tensor-core hierarchy (row-major BF16 blocks)
   std::vector<HostLevel> host;   // host[0] is unused (the op holds the finest level)
   std::vector<DevLevel> lv;
   double* P1d = nullptr;         // 2 * q * q injection matrices
   double* pinv = nullptr;        // bottom pseudo-inverse, nbot x nbot
   int64_t nbot = 0;
-  // CG work space (FP64)
-  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *xk = nullptr;
+  // CG work space (FP64, Rmax right-hand sides, [element][rhs][mode])
+  double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *bvec = nullptr, *xvec = nullptr;
   double *scal = nullptr, *partials = nullptr;
   double *stage_rhs = nullptr, *stage_x = nullptr;
-  double* hscal = nullptr;       // pinned host mirror of the CG scalars
+  int* active = nullptr;         // device per-RHS flags
+  int* err = nullptr;            // device flag set by bounded waits
+  double* hscal = nullptr;       // pinned host mirror of per-RHS scalars
+  int* hactive = nullptr;        // pinned host mirror of the flags
 };
 
 static const HostLevel& host_level(const ldgmg_hier* h, int l) {
   return l == 0 ? h->op->host : h->host[l];
+}
+
+// y = M x (+ epilogue) on R right-hand sides in the [element][rhs][mode] layout
+static ldgmg_status apply_mat(ldgmg_hier* h, const DevMat& M, int mode, const void* x, const void* rhs,
+                              const void* xin, void* y, double s, int R, cudaStream_t st) {
+  const int64_t b = M.b;
+  if (M.row_major) {
+    BatchArgs a;
+    a.nrows = M.nrows;
+    a.row_ptr = M.row_ptr;
+    a.col = M.col;
+    a.vals = M.vals;
+    a.x = static_cast<const float*>(x);
+    a.rhs = static_cast<const float*>(rhs);
+    a.xin = static_cast<const float*>(xin);
+    a.y = static_cast<float*>(y);
+    a.s = s;
+    a.mode = mode;
+    a.R = R;
+    a.es = R * b;
+    a.rs = b;
+    a.err = h ? h->err : nullptr;
+    CK(bsr_apply_tc(a, M.b, st));
+    return LDGMG_OK;
+  }
+  CK(bsr_apply_strided(M, mode, x, rhs, xin, y, s, R, R * b, b, st));
+  return LDGMG_OK;
 }
 
 extern "C" {
@@ -161,6 +196,7 @@ void ldgmg_default_opts(ldgmg_setup_opts* o) {
   o->post_form = LDGMG_FORM_BT;
   o->vcycle_precision = LDGMG_FP64;
   o->max_iter = 200;
+  o->max_rhs = 1;
 }
 
 void ldgmg_op_free(ldgmg_op* op) {
@@ -190,7 +226,7 @@ ldgmg_status ldgmg_assemble(const ldgmg_mesh* mesh, int p, const double* mu_host
     return fail(LDGMG_EINVAL, err);
   }
   op->tau0 = tau0;
-  ldgmg_status s = upload(op->host.A, b, P_FP64, op->A, 0);
+  ldgmg_status s = upload(op->host.A, b, P_FP64, 0, op->A, 0);
   if (s == LDGMG_OK) s = dalloc(&op->partials, kDotBlocks * sizeof(double));
   if (s == LDGMG_OK) s = dalloc(&op->scal, kCgSlots * sizeof(double));
   if (s != LDGMG_OK) {
@@ -211,19 +247,24 @@ ldgmg_status ldgmg_op_info(const ldgmg_op* op, int64_t* N, int* b, int64_t* nnzb
 
 ldgmg_status ldgmg_apply(ldgmg_op* op, const double* x, double* y, int nrhs, void* stream) {
   if (!op || !x || !y) return fail(LDGMG_EINVAL, "null argument");
-  if (nrhs != 1) return fail(LDGMG_EUNSUPPORTED, "nrhs must be 1");
-  CK(bsr_apply(op->A, M_Y, x, nullptr, nullptr, y, 1.0, (cudaStream_t)stream));
+  if (nrhs < 1 || nrhs > 65535) return fail(LDGMG_EINVAL, "nrhs out of range");
+  const int64_t b = op->host.b, N = op->host.N;
+  // stacked vectors: element e of right-hand side r at (r*N + e)*b
+  CK(bsr_apply_strided(op->A, M_Y, x, nullptr, nullptr, y, 1.0, nrhs, b, N * b, (cudaStream_t)stream));
   return LDGMG_OK;
 }
 
 ldgmg_status ldgmg_project_kernel(ldgmg_op* op, double* v, int nrhs, void* stream) {
   if (!op || !v) return fail(LDGMG_EINVAL, "null argument");
-  if (nrhs != 1) return fail(LDGMG_EUNSUPPORTED, "nrhs must be 1");
+  if (nrhs < 1) return fail(LDGMG_EINVAL, "nrhs must be >= 1");
   cudaStream_t st = (cudaStream_t)stream;
   // c has equal mode-0 entries and zeros elsewhere, so the projection
   // subtracts the mean of the mode-0 coefficients from each of them.
-  CK(strided_sum(op->host.N, op->host.b, v, op->partials, op->scal, st));
-  CK(strided_sub_mean(op->host.N, op->host.b, v, op->scal, st));
+  const int64_t N = op->host.N, b = op->host.b;
+  for (int r = 0; r < nrhs; ++r) {
+    CK(strided_sum(N, b, v + r * N * b, op->partials, op->scal, st));
+    CK(strided_sub_mean(N, b, v + r * N * b, op->scal, st));
+  }
   return LDGMG_OK;
 }
 
@@ -239,8 +280,12 @@ void ldgmg_hier_free(ldgmg_hier* h) {
   }
   cudaFree(h->P1d);
   cudaFree(h->pinv);
-  for (double* v : {h->r, h->z, h->p, h->q, h->xk, h->scal, h->partials, h->stage_rhs, h->stage_x}) cudaFree(v);
+  for (double* v : {h->r, h->z, h->p, h->q, h->bvec, h->xvec, h->scal, h->partials, h->stage_rhs, h->stage_x})
+    cudaFree(v);
+  cudaFree(h->active);
+  cudaFree(h->err);
   if (h->hscal) cudaFreeHost(h->hscal);
+  if (h->hactive) cudaFreeHost(h->hactive);
   delete h;
 }
 
@@ -255,7 +300,6 @@ static ldgmg_status bottom_pinv(ldgmg_hier* h, const HostLevel& L, cudaStream_t 
   dense_A(L, dense);
   const int64_t n = L.N * L.b;
   if (n > 20000) return fail(LDGMG_EUNSUPPORTED, "bottom level too large for a dense solve");
-  // symmetrise against rounding
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = i + 1; j < n; ++j) {
       const double m = 0.5 * (dense[i * n + j] + dense[j * n + i]);
@@ -350,7 +394,13 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 > 64 || o->nu2 > 64) return fail(LDGMG_EINVAL, "nu1/nu2");
   if (o->vcycle_precision < 0 || o->vcycle_precision > 2) return fail(LDGMG_EINVAL, "precision");
   if (o->max_iter < 1) return fail(LDGMG_EINVAL, "max_iter");
+  if (o->max_rhs < 1 || o->max_rhs > 128) return fail(LDGMG_EINVAL, "max_rhs must be in 1..128");
   if (o->smoother == LDGMG_JACOBI && !(o->omega > 0.0 && o->omega < 2.0)) return fail(LDGMG_EINVAL, "omega");
+  const bool batched = o->max_rhs > 1;
+  if (batched && o->vcycle_precision != LDGMG_BF16)
+    return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 needs vcycle_precision = LDGMG_BF16 (tensor-core path)");
+  if (batched && !tc_block_size_supported(op->host.b))
+    return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 needs b = 16 or 64 (p = 3)");
   cudaStream_t st = (cudaStream_t)stream;
   ldgmg_hier* h = new (std::nothrow) ldgmg_hier();
   if (!h) return fail(LDGMG_ENOMEM, "host allocation");
@@ -359,6 +409,8 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   h->prec = o->vcycle_precision;
   h->vprec = h->prec == P_FP64 ? 0 : 1;
   h->vsz = h->vprec ? 4 : 8;
+  h->Rmax = o->max_rhs;
+  h->batched = batched;
   auto bail = [&](ldgmg_status s) {
     ldgmg_hier_free(h);
     return s;
@@ -392,6 +444,7 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
     if (cudaMemcpyAsync(h->P1d, P.data(), P.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess)
       return bail(fail(LDGMG_ECUDA, "P1d copy"));
   }
+  const int rm = batched ? 1 : 0;
   h->lv.resize(nl);
   for (int l = 0; l < nl; ++l) {
     const HostLevel& L = host_level(h, l);
@@ -404,17 +457,17 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
       D.A = op->A;
       D.own_A = false;
     } else {
-      s = upload(L.A, L.b, h->prec, D.A, st);
+      s = upload(L.A, L.b, h->prec, rm, D.A, st);
     }
     if (s == LDGMG_OK && l + 1 < nl) {
       if (o->smoother == LDGMG_SAI) {
-        s = upload(L.B, L.b, h->prec, D.S, st);
-        if (s == LDGMG_OK) s = upload(L.BT, L.b, h->prec, D.ST, st);
+        s = upload(L.B, L.b, h->prec, rm, D.S, st);
+        if (s == LDGMG_OK) s = upload(L.BT, L.b, h->prec, rm, D.ST, st);
       } else {
-        s = upload(jacobi_pbsr(L), L.b, h->prec, D.S, st);
+        s = upload(jacobi_pbsr(L), L.b, h->prec, rm, D.S, st);
       }
     }
-    const size_t vb = size_t(L.N) * L.b * h->vsz;
+    const size_t vb = size_t(L.N) * L.b * h->vsz * h->Rmax;
     if (s == LDGMG_OK) s = dalloc((char**)&D.rhs, vb);
     if (s == LDGMG_OK) s = dalloc((char**)&D.x, vb);
     if (s == LDGMG_OK) s = dalloc((char**)&D.r, vb);
@@ -424,16 +477,19 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
     ldgmg_status s = bottom_pinv(h, host_level(h, nl - 1), st);
     if (s != LDGMG_OK) return bail(s);
   }
-  const size_t n0 = size_t(L0.N) * L0.b * sizeof(double);
-  for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->xk, &h->stage_rhs, &h->stage_x}) {
+  const size_t n0 = size_t(L0.N) * L0.b * sizeof(double) * h->Rmax;
+  for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->bvec, &h->xvec, &h->stage_rhs, &h->stage_x}) {
     ldgmg_status s = dalloc(v, n0);
     if (s != LDGMG_OK) return bail(s);
   }
-  if (dalloc(&h->scal, kCgSlots * sizeof(double)) != LDGMG_OK ||
-      dalloc(&h->partials, kDotBlocks * sizeof(double)) != LDGMG_OK)
+  if (dalloc(&h->scal, size_t(kCgSlots) * h->Rmax * sizeof(double)) != LDGMG_OK ||
+      dalloc(&h->partials, size_t(std::max(kDotBlocks, kBatchDotBlocks)) * h->Rmax * sizeof(double)) != LDGMG_OK ||
+      dalloc(&h->active, size_t(h->Rmax) * sizeof(int)) != LDGMG_OK || dalloc(&h->err, sizeof(int)) != LDGMG_OK)
     return bail(LDGMG_ENOMEM);
-  if (cudaMallocHost((void**)&h->hscal, kCgSlots * sizeof(double)) != cudaSuccess)
+  if (cudaMallocHost((void**)&h->hscal, size_t(kCgSlots) * h->Rmax * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost((void**)&h->hactive, size_t(h->Rmax) * sizeof(int)) != cudaSuccess)
     return bail(fail(LDGMG_ENOMEM, "cudaMallocHost"));
+  if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "memset"));
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "setup sync"));
   *out = h;
   return LDGMG_OK;
@@ -454,82 +510,100 @@ ldgmg_status ldgmg_hier_info(const ldgmg_hier* h, int level, int* nlevels, int* 
 }
 
 // ---------------------------------------------------------------------------
-// V-cycle steps
+// V-cycle steps on R right-hand sides (level vectors [element][rhs][mode])
 // ---------------------------------------------------------------------------
 
 static ldgmg_status smooth(ldgmg_hier* h, int l, int form, const void* rhs, const void* xin, void* xout,
-                           bool x_zero, cudaStream_t st) {
+                           bool x_zero, int R, cudaStream_t st) {
   DevLevel& D = h->lv[l];
   if (h->o.smoother == LDGMG_JACOBI) {
     // Eq. Jsmooth written as x + omega D^{-1} (b - A x)
     if (x_zero) {
-      CK(bsr_apply(D.S, M_SCALE, rhs, nullptr, nullptr, xout, h->o.omega, st));
+      CKS(apply_mat(h, D.S, M_SCALE, rhs, nullptr, nullptr, xout, h->o.omega, R, st));
     } else {
-      CK(bsr_apply(D.A, M_RES, xin, rhs, nullptr, D.r, 1.0, st));
-      CK(bsr_apply(D.S, M_AXPY, D.r, nullptr, xin, xout, h->o.omega, st));
+      CKS(apply_mat(h, D.A, M_RES, xin, rhs, nullptr, D.r, 1.0, R, st));
+      CKS(apply_mat(h, D.S, M_AXPY, D.r, nullptr, xin, xout, h->o.omega, R, st));
     }
     return LDGMG_OK;
   }
   // Eq. B1: x - B (A x - b) = x + B (b - A x); Eq. BT with B^T
   const DevMat& M = form == LDGMG_FORM_BT ? D.ST : D.S;
   if (x_zero) {
-    CK(bsr_apply(M, M_Y, rhs, nullptr, nullptr, xout, 1.0, st));
+    CKS(apply_mat(h, M, M_Y, rhs, nullptr, nullptr, xout, 1.0, R, st));
   } else {
-    CK(bsr_apply(D.A, M_RES, xin, rhs, nullptr, D.r, 1.0, st));
-    CK(bsr_apply(M, M_AXPY, D.r, nullptr, xin, xout, 1.0, st));
+    CKS(apply_mat(h, D.A, M_RES, xin, rhs, nullptr, D.r, 1.0, R, st));
+    CKS(apply_mat(h, M, M_AXPY, D.r, nullptr, xin, xout, 1.0, R, st));
   }
   return LDGMG_OK;
 }
 
 static ldgmg_status restrict_residual(ldgmg_hier* h, int l, const void* rhs, const void* x, bool x_zero,
-                                      void* rc, cudaStream_t st) {
+                                      void* rc, int R, cudaStream_t st) {
   DevLevel& D = h->lv[l];
   const void* r = rhs;
   if (!x_zero) {
-    CK(bsr_apply(D.A, M_RES, x, rhs, nullptr, D.r, 1.0, st));
+    CKS(apply_mat(h, D.A, M_RES, x, rhs, nullptr, D.r, 1.0, R, st));
     r = D.r;
   }
-  CK(restrict_apply(h->op->host.dim, h->op->host.p + 1, D.n, h->P1d, r, rc, h->vprec, st));
+  CK(restrict_apply(h->op->host.dim, h->op->host.p + 1, D.n, h->P1d, r, rc, h->vprec, R, st));
   return LDGMG_OK;
 }
 
 // Algorithm 1 on level l with x_l = 0 initially; rhs in lv[l].rhs, result in lv[l].x
-static ldgmg_status vcycle_level(ldgmg_hier* h, int l, cudaStream_t st) {
+static ldgmg_status vcycle_level(ldgmg_hier* h, int l, int R, cudaStream_t st) {
   DevLevel& D = h->lv[l];
   const int nl = int(h->lv.size());
   if (l == nl - 1) {
-    CK(dense_gemv(h->nbot, h->pinv, D.rhs, D.x, h->vprec, st));
+    CK(dense_gemv(h->nbot, D.b, h->pinv, D.rhs, D.x, h->vprec, R, st));
     return LDGMG_OK;
   }
   bool xz = true;
   for (int s = 0; s < h->o.nu1; ++s) {
-    CKS(smooth(h, l, h->o.pre_form, D.rhs, D.x, D.x, xz, st));
+    CKS(smooth(h, l, h->o.pre_form, D.rhs, D.x, D.x, xz, R, st));
     xz = false;
   }
-  CKS(restrict_residual(h, l, D.rhs, D.x, xz, h->lv[l + 1].rhs, st));
-  CKS(vcycle_level(h, l + 1, st));
-  if (xz) CK(cudaMemsetAsync(D.x, 0, size_t(D.N) * D.b * h->vsz, st));
-  CK(prolong_apply(h->op->host.dim, h->op->host.p + 1, D.n, h->P1d, h->lv[l + 1].x, D.x, h->vprec, st));
-  for (int s = 0; s < h->o.nu2; ++s) CKS(smooth(h, l, h->o.post_form, D.rhs, D.x, D.x, false, st));
+  CKS(restrict_residual(h, l, D.rhs, D.x, xz, h->lv[l + 1].rhs, R, st));
+  CKS(vcycle_level(h, l + 1, R, st));
+  if (xz) CK(cudaMemsetAsync(D.x, 0, size_t(D.N) * D.b * h->vsz * R, st));
+  CK(prolong_apply(h->op->host.dim, h->op->host.p + 1, D.n, h->P1d, h->lv[l + 1].x, D.x, h->vprec, R, st));
+  for (int s = 0; s < h->o.nu2; ++s) CKS(smooth(h, l, h->o.post_form, D.rhs, D.x, D.x, false, R, st));
   return LDGMG_OK;
 }
 
-// x = V b, FP64 device vectors
-static ldgmg_status apply_V(ldgmg_hier* h, const double* b, double* x, cudaStream_t st) {
+// x = V b on R right-hand sides, FP64 device vectors [element][rhs][mode]
+static ldgmg_status apply_V(ldgmg_hier* h, const double* b, double* x, int R, cudaStream_t st) {
   DevLevel& D = h->lv[0];
-  const int64_t n = D.N * D.b;
+  const int64_t n = D.N * D.b * R;
   if (h->vprec == 0) CK(cudaMemcpyAsync(D.rhs, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   else CK(cast_d2f(n, b, (float*)D.rhs, st));
-  CKS(vcycle_level(h, 0, st));
+  CKS(vcycle_level(h, 0, R, st));
   if (h->vprec == 0) CK(cudaMemcpyAsync(x, D.x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   else CK(cast_f2d(n, (const float*)D.x, x, st));
   return LDGMG_OK;
 }
 
+static ldgmg_status check_err_flag(ldgmg_hier* h, cudaStream_t st) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (e) return fail(LDGMG_ETIMEOUT, "a bounded device wait in the tensor-core apply gave up");
+  return LDGMG_OK;
+}
+
 ldgmg_status ldgmg_vcycle(ldgmg_hier* h, const double* b, double* x, int nrhs, void* stream) {
   if (!h || !b || !x) return fail(LDGMG_EINVAL, "null argument");
-  if (nrhs != 1) return fail(LDGMG_EUNSUPPORTED, "nrhs must be 1");
-  return apply_V(h, b, x, (cudaStream_t)stream);
+  if (nrhs < 1 || nrhs > h->Rmax) return fail(LDGMG_EINVAL, "nrhs must be in 1..max_rhs");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = h->op->host.N, bsz = h->op->host.b;
+  if (nrhs == 1) {
+    CKS(apply_V(h, b, x, 1, st));
+  } else {
+    CK(stack_to_batch(N, nrhs, int(bsz), b, h->bvec, st));
+    CKS(apply_V(h, h->bvec, h->xvec, nrhs, st));
+    CK(batch_to_stack(N, nrhs, int(bsz), h->xvec, x, st));
+  }
+  if (h->batched) return check_err_flag(h, st);
+  return LDGMG_OK;
 }
 
 static bool is_host_ptr(const void* p) {
@@ -541,10 +615,11 @@ static bool is_host_ptr(const void* p) {
   return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
 }
 
-static ldgmg_status read_scalar(ldgmg_hier* h, int slot, double* v, cudaStream_t st) {
-  CK(cudaMemcpyAsync(h->hscal + slot, h->scal + slot, sizeof(double), cudaMemcpyDeviceToHost, st));
+// copy slot `slot` (R doubles) of the device scalars to the pinned host mirror
+static ldgmg_status read_slot(ldgmg_hier* h, int slot, int R, cudaStream_t st) {
+  CK(cudaMemcpyAsync(h->hscal + size_t(slot) * R, h->scal + size_t(slot) * R, R * sizeof(double),
+                     cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  *v = h->hscal[slot];
   return LDGMG_OK;
 }
 
@@ -552,71 +627,112 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
                          double* relres, void* stream) {
   g_err.clear();
   if (!h || !rhs || !x) return fail(LDGMG_EINVAL, "null argument");
-  if (nrhs != 1) return fail(LDGMG_EUNSUPPORTED, "nrhs must be 1");
+  if (nrhs < 1 || nrhs > h->Rmax) return fail(LDGMG_EINVAL, "nrhs must be in 1..max_rhs of the setup");
   if (!(tol > 0.0)) return fail(LDGMG_EINVAL, "tol must be positive");
   cudaStream_t st = (cudaStream_t)stream;
   const HostLevel& L0 = h->op->host;
-  const int64_t n = L0.N * L0.b;
+  const int R = nrhs;
+  const int64_t N = L0.N, bsz = L0.b;
+  const int64_t n = N * bsz * R;
   const size_t nb = size_t(n) * sizeof(double);
   const bool host_rhs = is_host_ptr(rhs), host_x = is_host_ptr(x);
-  const double* b = rhs;
+  // right-hand sides in the [element][rhs][mode] layout (the stacked layout when R = 1)
+  const double* src = rhs;
   if (host_rhs) {
     CK(cudaMemcpyAsync(h->stage_rhs, rhs, nb, cudaMemcpyHostToDevice, st));
-    b = h->stage_rhs;
+    src = h->stage_rhs;
   }
-  double* xd = host_x ? h->stage_x : x;
+  const double* b = src;
+  if (R > 1) {
+    CK(stack_to_batch(N, R, int(bsz), src, h->bvec, st));
+    b = h->bvec;
+  }
+  double* xd = (R > 1) ? h->xvec : (host_x ? h->stage_x : x);
   const bool flexible = h->prec != P_FP64;
-  double bb = 0.0, rr = 0.0;
-  CK(dot(n, b, b, h->partials, h->scal + S_BB, st));
-  CKS(read_scalar(h, S_BB, &bb, st));
-  if (!std::isfinite(bb)) return fail(LDGMG_EINVAL, "rhs contains NaN or Inf");
+  double* S = h->scal;
+  auto slot = [&](int s) { return S + size_t(s) * R; };
+  auto hslot = [&](int s) { return h->hscal + size_t(s) * R; };
+  CK(dot_batched(N, R, int(bsz), b, nullptr, h->partials, slot(S_BB), st));
+  CKS(read_slot(h, S_BB, R, st));
+  std::vector<double> bb(hslot(S_BB), hslot(S_BB) + R);
+  for (double v : bb)
+    if (!std::isfinite(v)) return fail(LDGMG_EINVAL, "rhs contains NaN or Inf");
+  std::vector<int> it(R, 0);
+  std::vector<int> act(R);
+  int nact = 0;
+  for (int r = 0; r < R; ++r) {
+    act[r] = bb[r] > 0.0;
+    nact += act[r];
+  }
+  for (int r = 0; r < R; ++r) h->hactive[r] = act[r];
+  CK(cudaMemcpyAsync(h->active, h->hactive, R * sizeof(int), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(xd, 0, nb, st));
-  int k = 0;
   ldgmg_status result = LDGMG_OK;
-  if (bb > 0.0) {
-    const double stop2 = tol * tol * bb;
+  int k = 0;
+  if (nact > 0) {
     CK(cudaMemcpyAsync(h->r, b, nb, cudaMemcpyDeviceToDevice, st));
-    CKS(apply_V(h, h->r, h->z, st));
+    CKS(apply_V(h, h->r, h->z, R, st));
     CK(cudaMemcpyAsync(h->p, h->z, nb, cudaMemcpyDeviceToDevice, st));
-    CK(dot(n, h->r, h->z, h->partials, h->scal + S_RZ, st));
-    bool conv = false;
-    while (k < h->o.max_iter) {
-      CK(bsr_apply(h->op->A, M_Y, h->p, nullptr, nullptr, h->q, 1.0, st));
-      CK(dot(n, h->p, h->q, h->partials, h->scal + S_PQ, st));
-      CK(cg_alpha(h->scal, st));
-      CK(cg_update_xr(n, xd, h->r, h->p, h->q, h->scal, st));
-      CK(dot(n, h->r, h->r, h->partials, h->scal + S_RR, st));
+    CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZ), st));
+    while (nact > 0 && k < h->o.max_iter) {
+      CK(bsr_apply_strided(h->op->A, M_Y, h->p, nullptr, nullptr, h->q, 1.0, R, R * bsz, bsz, st));
+      CK(dot_batched(N, R, int(bsz), h->p, h->q, h->partials, slot(S_PQ), st));
+      CK(cg_alpha_b(R, S, h->active, st));
+      CK(cg_update_xr_b(N, R, int(bsz), xd, h->r, h->p, h->q, S, st));
+      CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_RR), st));
       ++k;
-      CKS(read_scalar(h, S_RR, &rr, st));
-      if (!std::isfinite(rr)) {
-        result = fail(LDGMG_ENOTCONV, "CG breakdown (non-finite residual)");
-        break;
+      CKS(read_slot(h, S_RR, R, st));
+      bool changed = false;
+      for (int r = 0; r < R; ++r) {
+        if (!act[r]) continue;
+        it[r] = k;
+        const double rr = hslot(S_RR)[r];
+        if (!std::isfinite(rr)) {
+          result = fail(LDGMG_ENOTCONV, "CG breakdown (non-finite residual)");
+          act[r] = 0;
+          changed = true;
+        } else if (rr <= tol * tol * bb[r]) {
+          act[r] = 0;
+          changed = true;
+        }
       }
-      if (rr <= stop2) {
-        conv = true;
-        break;
+      if (changed) {
+        nact = 0;
+        for (int r = 0; r < R; ++r) {
+          h->hactive[r] = act[r];
+          nact += act[r];
+        }
+        CK(cudaMemcpyAsync(h->active, h->hactive, R * sizeof(int), cudaMemcpyHostToDevice, st));
       }
-      if (flexible) CK(dot(n, h->r, h->z, h->partials, h->scal + S_RZOLD, st));
-      CKS(apply_V(h, h->r, h->z, st));
-      CK(dot(n, h->r, h->z, h->partials, h->scal + S_RZNEW, st));
-      CK(cg_beta(h->scal, flexible ? 1 : 0, st));
-      CK(cg_update_p(n, h->p, h->z, h->scal, st));
+      if (nact == 0) break;
+      if (flexible) CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZOLD), st));
+      CKS(apply_V(h, h->r, h->z, R, st));
+      CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZNEW), st));
+      CK(cg_beta_b(R, S, h->active, flexible ? 1 : 0, st));
+      CK(cg_update_p_b(N, R, int(bsz), h->p, h->z, S, st));
     }
-    if (!conv && result == LDGMG_OK) result = fail(LDGMG_ENOTCONV, "max_iter reached");
+    if (nact > 0 && result == LDGMG_OK) result = fail(LDGMG_ENOTCONV, "max_iter reached");
   }
-  // true residual of the returned iterate
-  double rel = 0.0;
-  if (bb > 0.0) {
-    CK(bsr_apply(h->op->A, M_RES, xd, b, nullptr, h->r, 1.0, st));
-    CK(dot(n, h->r, h->r, h->partials, h->scal + S_TMP, st));
-    double t = 0.0;
-    CKS(read_scalar(h, S_TMP, &t, st));
-    rel = std::sqrt(t / bb);
+  // true residual of the returned iterates
+  CK(bsr_apply_strided(h->op->A, M_RES, xd, b, nullptr, h->r, 1.0, R, R * bsz, bsz, st));
+  CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_TMP), st));
+  CKS(read_slot(h, S_TMP, R, st));
+  if (R > 1) {
+    double* dst = host_x ? h->stage_x : x;
+    CK(batch_to_stack(N, R, int(bsz), xd, dst, st));
+    if (host_x) CK(cudaMemcpyAsync(x, h->stage_x, nb, cudaMemcpyDeviceToHost, st));
+  } else if (host_x) {
+    CK(cudaMemcpyAsync(x, xd, nb, cudaMemcpyDeviceToHost, st));
   }
-  if (host_x) CK(cudaMemcpyAsync(x, xd, nb, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  if (iters) iters[0] = k;
-  if (relres) relres[0] = rel;
+  for (int r = 0; r < R; ++r) {
+    if (iters) iters[r] = it[r];
+    if (relres) relres[r] = bb[r] > 0.0 ? std::sqrt(hslot(S_TMP)[r] / bb[r]) : 0.0;
+  }
+  if (h->batched) {
+    ldgmg_status e = check_err_flag(h, st);
+    if (e != LDGMG_OK) return e;
+  }
   return result;
 }
 
@@ -631,18 +747,32 @@ static ldgmg_status check_level(ldgmg_hier* h, int l, bool need_smoother) {
   return LDGMG_OK;
 }
 
+static const DevMat* level_mat(ldgmg_hier* h, int l, int which) {
+  const DevLevel& D = h->lv[l];
+  if (which == LDGMG_MAT_A) return &D.A;
+  if (which == LDGMG_MAT_D && h->o.smoother == LDGMG_JACOBI) return &D.S;
+  if (which == LDGMG_MAT_B && h->o.smoother == LDGMG_SAI) return &D.S;
+  if (which == LDGMG_MAT_BT && h->o.smoother == LDGMG_SAI) return &D.ST;
+  return nullptr;
+}
+
 ldgmg_status ldgmg_level_apply(ldgmg_hier* h, int l, int which, const void* x, void* y, void* stream) {
   CKS(check_level(h, l, which != LDGMG_MAT_A));
   if (!x || !y) return fail(LDGMG_EINVAL, "null vector");
-  const DevLevel& D = h->lv[l];
-  const DevMat* M = nullptr;
-  if (which == LDGMG_MAT_A) M = &D.A;
-  else if (which == LDGMG_MAT_D && h->o.smoother == LDGMG_JACOBI) M = &D.S;
-  else if (which == LDGMG_MAT_B && h->o.smoother == LDGMG_SAI) M = &D.S;
-  else if (which == LDGMG_MAT_BT && h->o.smoother == LDGMG_SAI) M = &D.ST;
+  const DevMat* M = level_mat(h, l, which);
   if (!M) return fail(LDGMG_EINVAL, "matrix not present for this smoother");
-  CK(bsr_apply(*M, M_Y, x, nullptr, nullptr, y, 1.0, (cudaStream_t)stream));
-  return LDGMG_OK;
+  return apply_mat(h, *M, M_Y, x, nullptr, nullptr, y, 1.0, 1, (cudaStream_t)stream);
+}
+
+ldgmg_status ldgmg_level_apply_batched(ldgmg_hier* h, int l, int which, int nrhs, const float* x, float* y,
+                                       void* stream) {
+  CKS(check_level(h, l, which != LDGMG_MAT_A));
+  if (!x || !y) return fail(LDGMG_EINVAL, "null vector");
+  if (nrhs < 1 || nrhs > 128) return fail(LDGMG_EINVAL, "nrhs must be in 1..128");
+  if (h->vprec != 1) return fail(LDGMG_EUNSUPPORTED, "batched level apply needs an FP32 or BF16 hierarchy");
+  const DevMat* M = level_mat(h, l, which);
+  if (!M) return fail(LDGMG_EINVAL, "matrix not present for this smoother");
+  return apply_mat(h, *M, M_Y, x, nullptr, nullptr, y, 1.0, nrhs, (cudaStream_t)stream);
 }
 
 ldgmg_status ldgmg_level_smooth(ldgmg_hier* h, int l, int form, const void* rhs, const void* xin, void* xout,
@@ -650,27 +780,27 @@ ldgmg_status ldgmg_level_smooth(ldgmg_hier* h, int l, int form, const void* rhs,
   CKS(check_level(h, l, true));
   if (!rhs || !xout || (!x_is_zero && !xin)) return fail(LDGMG_EINVAL, "null vector");
   if (form != LDGMG_FORM_B1 && form != LDGMG_FORM_BT) return fail(LDGMG_EINVAL, "form");
-  return smooth(h, l, form, rhs, xin, xout, x_is_zero != 0, (cudaStream_t)stream);
+  return smooth(h, l, form, rhs, xin, xout, x_is_zero != 0, 1, (cudaStream_t)stream);
 }
 
 ldgmg_status ldgmg_level_restrict(ldgmg_hier* h, int l, const void* rhs, const void* x, void* rc,
                                   void* stream) {
   CKS(check_level(h, l, true));
   if (!rhs || !x || !rc) return fail(LDGMG_EINVAL, "null vector");
-  return restrict_residual(h, l, rhs, x, false, rc, (cudaStream_t)stream);
+  return restrict_residual(h, l, rhs, x, false, rc, 1, (cudaStream_t)stream);
 }
 
 ldgmg_status ldgmg_level_prolong(ldgmg_hier* h, int l, const void* xc, void* x, void* stream) {
   CKS(check_level(h, l, true));
   if (!xc || !x) return fail(LDGMG_EINVAL, "null vector");
-  CK(prolong_apply(h->op->host.dim, h->op->host.p + 1, h->lv[l].n, h->P1d, xc, x, h->vprec,
+  CK(prolong_apply(h->op->host.dim, h->op->host.p + 1, h->lv[l].n, h->P1d, xc, x, h->vprec, 1,
                    (cudaStream_t)stream));
   return LDGMG_OK;
 }
 
 ldgmg_status ldgmg_bottom_solve(ldgmg_hier* h, const void* rhs, void* x, void* stream) {
   if (!h || !rhs || !x) return fail(LDGMG_EINVAL, "null argument");
-  CK(dense_gemv(h->nbot, h->pinv, rhs, x, h->vprec, (cudaStream_t)stream));
+  CK(dense_gemv(h->nbot, h->lv.back().b, h->pinv, rhs, x, h->vprec, 1, (cudaStream_t)stream));
   return LDGMG_OK;
 }
 
@@ -683,12 +813,7 @@ static float bf16_to_float(uint16_t v) {
 
 ldgmg_status ldgmg_export_level(ldgmg_hier* h, int l, int which, int64_t* row_ptr, int32_t* col, double* vals) {
   CKS(check_level(h, l, which != LDGMG_MAT_A));
-  const DevLevel& D = h->lv[l];
-  const DevMat* M = nullptr;
-  if (which == LDGMG_MAT_A) M = &D.A;
-  else if (which == LDGMG_MAT_D && h->o.smoother == LDGMG_JACOBI) M = &D.S;
-  else if (which == LDGMG_MAT_B && h->o.smoother == LDGMG_SAI) M = &D.S;
-  else if (which == LDGMG_MAT_BT && h->o.smoother == LDGMG_SAI) M = &D.ST;
+  const DevMat* M = level_mat(h, l, which);
   if (!M) return fail(LDGMG_EINVAL, "matrix not present for this smoother");
   CK(cudaDeviceSynchronize());
   if (row_ptr) {
@@ -704,7 +829,9 @@ ldgmg_status ldgmg_export_level(ldgmg_hier* h, int l, int which, int64_t* row_pt
     CK(cudaMemcpy(raw.data(), M->vals, raw.size(), cudaMemcpyDeviceToHost));
     for (size_t t = 0; t < cnt; ++t) {
       const size_t nz = t / (size_t(b) * b), e = t % (size_t(b) * b);
-      const size_t c = e / b, r = e % b;   // device storage is column-major
+      size_t r, c;
+      if (M->row_major) { r = e / b; c = e % b; }
+      else { c = e / b; r = e % b; }
       double v;
       if (M->prec == P_FP64) v = reinterpret_cast<const double*>(raw.data())[t];
       else if (M->prec == P_FP32) v = reinterpret_cast<const float*>(raw.data())[t];

@@ -26,7 +26,7 @@ typedef __nv_bfloat16 bf16;
 // number of kernels this library has enqueued (all streams, all devices)
 static std::atomic<unsigned long long> g_launches{0};
 unsigned long long launches() { return g_launches.load(); }
-static inline cudaError_t launched(int count = 1) {
+cudaError_t launched(int count) {
   g_launches.fetch_add(count);
   return cudaGetLastError();
 }
@@ -66,6 +66,8 @@ template <class TA, class TV> struct BsrArgs {
   TV* y;
   double s;
   int mode;
+  int64_t es, rs;   // vector entry (element e, rhs r, mode c) at e*es + r*rs + c; rhs = blockIdx.y
+  int R;            // right-hand sides (grid y dimension)
 };
 
 template <int TEAM> __device__ __forceinline__ void team_sync() {
@@ -89,6 +91,7 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
   const int g = lt / LPC, rl = lt % LPC;
   const bool active = g < G;
   const int64_t row = int64_t(blockIdx.x) * TEAMS + team;
+  const int64_t roff = int64_t(blockIdx.y) * a.rs;
   if (TEAM == 32 && row >= a.nrows) return;   // whole warp leaves together
   TACC acc[VEC];
 #pragma unroll
@@ -99,7 +102,7 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
     for (int nz = z0; nz < z1; ++nz) {
       const int64_t j = a.col[nz];
       team_sync<TEAM>();
-      for (int c = lt; c < B; c += TEAM) xs[team][c] = TACC(a.x[j * B + c]);
+      for (int c = lt; c < B; c += TEAM) xs[team][c] = TACC(a.x[j * a.es + roff + c]);
       team_sync<TEAM>();
       if (active) {
         const TA* blk = a.vals + int64_t(nz) * (B * B) + rl * VEC;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
     TACC sum = TACC(0);
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) sum += red[team][gg][lt];
-    const int64_t o = row * B + lt;
+    const int64_t o = row * a.es + roff + lt;
     switch (a.mode) {
       case M_Y: a.y[o] = TV(sum); break;
       case M_RES: a.y[o] = TV(TACC(a.rhs[o]) - sum); break;
@@ -147,13 +150,14 @@ static cudaError_t launch_bsr_b(const DevMat& M, const BsrArgs<TA, TV>& a, cudaS
   constexpr int TEAMS = (B > 32) ? 1 : 8;
   if (M.nrows == 0) return cudaSuccess;
   const int64_t grid = (M.nrows + TEAMS - 1) / TEAMS;
-  bsr_kernel<B, TA, TV><<<dim3(unsigned(grid)), 256, 0, st>>>(a);
+  bsr_kernel<B, TA, TV><<<dim3(unsigned(grid), unsigned(a.R)), 256, 0, st>>>(a);
   return launched();
 }
 
 template <class TA, class TV>
 static cudaError_t launch_bsr_t(const DevMat& M, int mode, const void* x, const void* rhs,
-                                const void* xin, void* y, double s, cudaStream_t st) {
+                                const void* xin, void* y, double s, int R, int64_t es, int64_t rs,
+                                cudaStream_t st) {
   BsrArgs<TA, TV> a;
   a.nrows = M.nrows;
   a.row_ptr = M.row_ptr;
@@ -165,6 +169,9 @@ static cudaError_t launch_bsr_t(const DevMat& M, int mode, const void* x, const 
   a.y = static_cast<TV*>(y);
   a.s = s;
   a.mode = mode;
+  a.es = es;
+  a.rs = rs;
+  a.R = R;
   switch (M.b) {
     case 4: return launch_bsr_b<4>(M, a, st);
     case 8: return launch_bsr_b<8>(M, a, st);
@@ -178,14 +185,20 @@ static cudaError_t launch_bsr_t(const DevMat& M, int mode, const void* x, const 
   }
 }
 
-cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
-                      void* y, double s, cudaStream_t st) {
+cudaError_t bsr_apply_strided(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
+                              void* y, double s, int R, int64_t es, int64_t rs, cudaStream_t st) {
+  if (M.row_major || R < 1) return cudaErrorInvalidValue;
   switch (M.prec) {
-    case P_FP64: return launch_bsr_t<double, double>(M, mode, x, rhs, xin, y, s, st);
-    case P_FP32: return launch_bsr_t<float, float>(M, mode, x, rhs, xin, y, s, st);
-    case P_BF16: return launch_bsr_t<bf16, float>(M, mode, x, rhs, xin, y, s, st);
+    case P_FP64: return launch_bsr_t<double, double>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
+    case P_FP32: return launch_bsr_t<float, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
+    case P_BF16: return launch_bsr_t<bf16, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
+                      void* y, double s, cudaStream_t st) {
+  return bsr_apply_strided(M, mode, x, rhs, xin, y, s, 1, M.b, 0, st);
 }
 
 // --------------------------------------------------------------------------
@@ -194,25 +207,27 @@ cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs,
 
 template <class T>
 __global__ void expand_kernel(int64_t total, int b, const uint32_t* __restrict__ ids,
-                              const double* __restrict__ pool, T* __restrict__ vals) {
+                              const double* __restrict__ pool, T* __restrict__ vals, int row_major) {
   const int64_t bb = int64_t(b) * b;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
        t += int64_t(gridDim.x) * blockDim.x) {
     const int64_t nz = t / bb, e = t % bb;
-    const int c = int(e / b), r = int(e % b);        // stored column-major
+    int r, c;
+    if (row_major) { r = int(e / b); c = int(e % b); }
+    else { c = int(e / b); r = int(e % b); }
     vals[t] = from_d<T>(pool[int64_t(ids[nz]) * bb + int64_t(r) * b + c]);
   }
 }
 
 cudaError_t expand_blocks(int64_t nnzb, int b, const uint32_t* ids, const double* pool, void* vals,
-                          int prec, cudaStream_t st) {
+                          int prec, int row_major, cudaStream_t st) {
   const int64_t total = nnzb * b * b;
   if (total == 0) return cudaSuccess;
   const int grid = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
   switch (prec) {
-    case P_FP64: expand_kernel<double><<<grid, 256, 0, st>>>(total, b, ids, pool, (double*)vals); break;
-    case P_FP32: expand_kernel<float><<<grid, 256, 0, st>>>(total, b, ids, pool, (float*)vals); break;
-    case P_BF16: expand_kernel<bf16><<<grid, 256, 0, st>>>(total, b, ids, pool, (bf16*)vals); break;
+    case P_FP64: expand_kernel<double><<<grid, 256, 0, st>>>(total, b, ids, pool, (double*)vals, row_major); break;
+    case P_FP32: expand_kernel<float><<<grid, 256, 0, st>>>(total, b, ids, pool, (float*)vals, row_major); break;
+    case P_BF16: expand_kernel<bf16><<<grid, 256, 0, st>>>(total, b, ids, pool, (bf16*)vals, row_major); break;
     default: return cudaErrorInvalidValue;
   }
   return launched();
@@ -270,6 +285,7 @@ __global__ void restrict_kernel(int d, int q, int nf, const double* __restrict__
   const int b = (d == 2) ? q * q : q * q * q;
   const int64_t nc = nf / 2;
   const int64_t C = blockIdx.x;
+  const int R = gridDim.y, rr = blockIdx.y;
   const int t = threadIdx.x;
   int cc[3] = {int(C % nc), int((C / nc) % nc), int(C / (nc * nc))};
   double acc = 0.0;
@@ -277,11 +293,11 @@ __global__ void restrict_kernel(int d, int q, int nf, const double* __restrict__
     int64_t f = 0;
     for (int a = d - 1; a >= 0; --a) f = f * nf + (2 * cc[a] + ((s >> a) & 1));
     __syncthreads();
-    if (t < b) buf[0][t] = double(rf[f * b + t]);
+    if (t < b) buf[0][t] = double(rf[(f * R + rr) * b + t]);
     __syncthreads();
     acc += apply_child<true>(Ps, buf[0], buf[1], d, q, b, s, t);
   }
-  if (t < b) rc[C * b + t] = TV(acc);
+  if (t < b) rc[(C * R + rr) * b + t] = TV(acc);
 }
 
 template <class TV>
@@ -293,9 +309,10 @@ __global__ void prolong_kernel(int d, int q, int nf, const double* __restrict__ 
   const int b = (d == 2) ? q * q : q * q * q;
   const int64_t nc = nf / 2;
   const int64_t C = blockIdx.x;
+  const int R = gridDim.y, rr = blockIdx.y;
   const int t = threadIdx.x;
   int cc[3] = {int(C % nc), int((C / nc) % nc), int(C / (nc * nc))};
-  const double xv = t < b ? double(xc[C * b + t]) : 0.0;
+  const double xv = t < b ? double(xc[(C * R + rr) * b + t]) : 0.0;
   for (int s = 0; s < (1 << d); ++s) {
     int64_t f = 0;
     for (int a = d - 1; a >= 0; --a) f = f * nf + (2 * cc[a] + ((s >> a) & 1));
@@ -303,7 +320,7 @@ __global__ void prolong_kernel(int d, int q, int nf, const double* __restrict__ 
     if (t < b) buf[0][t] = xv;
     __syncthreads();
     const double v = apply_child<false>(Ps, buf[0], buf[1], d, q, b, s, t);
-    if (t < b) xf[f * b + t] = TV(double(xf[f * b + t]) + v);
+    if (t < b) xf[(f * R + rr) * b + t] = TV(double(xf[(f * R + rr) * b + t]) + v);
   }
 }
 
@@ -314,18 +331,20 @@ static int64_t coarse_count(int d, int nf) {
 }
 
 cudaError_t restrict_apply(int d, int q, int n_fine, const double* P, const void* rf, void* rc,
-                           int vprec, cudaStream_t st) {
+                           int vprec, int R, cudaStream_t st) {
   const int64_t Nc = coarse_count(d, n_fine);
-  if (vprec == 0) restrict_kernel<double><<<unsigned(Nc), 64, 0, st>>>(d, q, n_fine, P, (const double*)rf, (double*)rc);
-  else restrict_kernel<float><<<unsigned(Nc), 64, 0, st>>>(d, q, n_fine, P, (const float*)rf, (float*)rc);
+  const dim3 grid{unsigned(Nc), unsigned(R), 1u};
+  if (vprec == 0) restrict_kernel<double><<<grid, 64, 0, st>>>(d, q, n_fine, P, (const double*)rf, (double*)rc);
+  else restrict_kernel<float><<<grid, 64, 0, st>>>(d, q, n_fine, P, (const float*)rf, (float*)rc);
   return launched();
 }
 
 cudaError_t prolong_apply(int d, int q, int n_fine, const double* P, const void* xc, void* xf,
-                          int vprec, cudaStream_t st) {
+                          int vprec, int R, cudaStream_t st) {
   const int64_t Nc = coarse_count(d, n_fine);
-  if (vprec == 0) prolong_kernel<double><<<unsigned(Nc), 64, 0, st>>>(d, q, n_fine, P, (const double*)xc, (double*)xf);
-  else prolong_kernel<float><<<unsigned(Nc), 64, 0, st>>>(d, q, n_fine, P, (const float*)xc, (float*)xf);
+  const dim3 grid{unsigned(Nc), unsigned(R), 1u};
+  if (vprec == 0) prolong_kernel<double><<<grid, 64, 0, st>>>(d, q, n_fine, P, (const double*)xc, (double*)xf);
+  else prolong_kernel<float><<<grid, 64, 0, st>>>(d, q, n_fine, P, (const float*)xc, (float*)xf);
   return launched();
 }
 
@@ -333,24 +352,26 @@ cudaError_t prolong_apply(int d, int q, int n_fine, const double* P, const void*
 // bottom solve: dense FP64 pseudo-inverse times vector, one warp per row
 // --------------------------------------------------------------------------
 
+// dof i = e*b + c of right-hand side r lives at (e*R + r)*b + c
 template <class TV>
-__global__ void gemv_kernel(int64_t n, const double* __restrict__ P, const TV* __restrict__ v,
+__global__ void gemv_kernel(int64_t n, int b, const double* __restrict__ P, const TV* __restrict__ v,
                             TV* __restrict__ y) {
   const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
+  const int R = gridDim.y, rr = blockIdx.y;
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   double s = 0.0;
   const double* pr = P + row * n;
-  for (int64_t j = lane; j < n; j += 32) s += pr[j] * double(v[j]);
+  for (int64_t j = lane; j < n; j += 32) s += pr[j] * double(v[((j / b) * R + rr) * b + j % b]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = TV(s);
+  if (lane == 0) y[((row / b) * R + rr) * b + row % b] = TV(s);
 }
 
-cudaError_t dense_gemv(int64_t n, const double* Pinv, const void* v, void* y, int vprec,
+cudaError_t dense_gemv(int64_t n, int b, const double* Pinv, const void* v, void* y, int vprec, int R,
                        cudaStream_t st) {
-  const int64_t grid = (n * 32 + 255) / 256;
-  if (vprec == 0) gemv_kernel<double><<<unsigned(grid), 256, 0, st>>>(n, Pinv, (const double*)v, (double*)y);
-  else gemv_kernel<float><<<unsigned(grid), 256, 0, st>>>(n, Pinv, (const float*)v, (float*)y);
+  const dim3 grid{unsigned((n * 32 + 255) / 256), unsigned(R), 1u};
+  if (vprec == 0) gemv_kernel<double><<<grid, 256, 0, st>>>(n, b, Pinv, (const double*)v, (double*)y);
+  else gemv_kernel<float><<<grid, 256, 0, st>>>(n, b, Pinv, (const float*)v, (float*)y);
   return launched();
 }
 
@@ -471,6 +492,103 @@ cudaError_t cg_update_xr(int64_t n, double* x, double* r, const double* p, const
 }
 cudaError_t cg_update_p(int64_t n, double* p, const double* z, const double* scal, cudaStream_t st) {
   cg_update_p_kernel<<<grid_for(n), 256, 0, st>>>(n, p, z, scal);
+  return launched();
+}
+
+// --------------------------------------------------------------------------
+// batched right-hand sides: layout changes, per-RHS dots and CG updates
+// --------------------------------------------------------------------------
+
+__global__ void relayout_kernel(int64_t N, int R, int b, const double* __restrict__ src,
+                                double* __restrict__ dst, int to_batch) {
+  const int64_t total = N * R * b;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += int64_t(gridDim.x) * blockDim.x) {
+    // t indexes the batched layout [e][r][c]
+    const int64_t e = t / (int64_t(R) * b), r = (t / b) % R, c = t % b;
+    const int64_t stacked = (r * N + e) * b + c;
+    if (to_batch) dst[t] = src[stacked];
+    else dst[stacked] = src[t];
+  }
+}
+
+cudaError_t stack_to_batch(int64_t N, int R, int b, const double* src, double* dst, cudaStream_t st) {
+  relayout_kernel<<<grid_for(N * R * b), 256, 0, st>>>(N, R, b, src, dst, 1);
+  return launched();
+}
+cudaError_t batch_to_stack(int64_t N, int R, int b, const double* src, double* dst, cudaStream_t st) {
+  relayout_kernel<<<grid_for(N * R * b), 256, 0, st>>>(N, R, b, src, dst, 0);
+  return launched();
+}
+
+// block (p, r) sums entries of right-hand side r over a fixed slice of the element range
+__global__ void dot_batched_partial(int64_t N, int b, const double* __restrict__ u, const double* __restrict__ v,
+                                    double* __restrict__ partials) {
+  const int R = gridDim.y, rr = blockIdx.y;
+  const int64_t n = N * b;
+  double s = 0.0;
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t o = ((t / b) * R + rr) * b + t % b;
+    const double a = u[o];
+    s += a * (v ? v[o] : a);
+  }
+  s = block_reduce(s);
+  if (threadIdx.x == 0) partials[int64_t(rr) * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void dot_batched_final(int P, const double* __restrict__ partials, double* __restrict__ out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s += partials[int64_t(blockIdx.x) * P + i];
+  s = block_reduce(s);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+cudaError_t dot_batched(int64_t N, int R, int b, const double* u, const double* v, double* partials,
+                        double* out, cudaStream_t st) {
+  dot_batched_partial<<<dim3(kBatchDotBlocks, unsigned(R)), 256, 0, st>>>(N, b, u, v, partials);
+  dot_batched_final<<<unsigned(R), 256, 0, st>>>(kBatchDotBlocks, partials, out);
+  return launched(2);
+}
+
+__global__ void cg_alpha_b_kernel(int R, double* s, const int* active) {
+  const int r = threadIdx.x + blockIdx.x * blockDim.x;
+  if (r < R) s[S_ALPHA * R + r] = active[r] ? s[S_RZ * R + r] / s[S_PQ * R + r] : 0.0;
+}
+__global__ void cg_beta_b_kernel(int R, double* s, const int* active, int flexible) {
+  const int r = threadIdx.x + blockIdx.x * blockDim.x;
+  if (r >= R) return;
+  const double num = flexible ? (s[S_RZNEW * R + r] - s[S_RZOLD * R + r]) : s[S_RZNEW * R + r];
+  s[S_BETA * R + r] = active[r] ? num / s[S_RZ * R + r] : 0.0;
+  if (active[r]) s[S_RZ * R + r] = s[S_RZNEW * R + r];
+}
+__global__ void cg_update_xr_b_kernel(int64_t n, int R, int b, double* x, double* r, const double* p,
+                                      const double* q, const double* s) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double al = s[S_ALPHA * R + (i / b) % R];
+    x[i] += al * p[i];
+    r[i] -= al * q[i];
+  }
+}
+__global__ void cg_update_p_b_kernel(int64_t n, int R, int b, double* p, const double* z, const double* s) {
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = z[i] + s[S_BETA * R + (i / b) % R] * p[i];
+}
+
+cudaError_t cg_alpha_b(int R, double* scal, const int* active, cudaStream_t st) {
+  cg_alpha_b_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, scal, active);
+  return launched();
+}
+cudaError_t cg_beta_b(int R, double* scal, const int* active, int flexible, cudaStream_t st) {
+  cg_beta_b_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, scal, active, flexible);
+  return launched();
+}
+cudaError_t cg_update_xr_b(int64_t N, int R, int b, double* x, double* r, const double* p, const double* q,
+                           const double* scal, cudaStream_t st) {
+  cg_update_xr_b_kernel<<<grid_for(N * R * b), 256, 0, st>>>(N * R * b, R, b, x, r, p, q, scal);
+  return launched();
+}
+cudaError_t cg_update_p_b(int64_t N, int R, int b, double* p, const double* z, const double* scal,
+                          cudaStream_t st) {
+  cg_update_p_b_kernel<<<grid_for(N * R * b), 256, 0, st>>>(N * R * b, R, b, p, z, scal);
   return launched();
 }
 

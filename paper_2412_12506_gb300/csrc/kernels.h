@@ -14,6 +14,7 @@ enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2 };
 struct DevMat {
   int64_t nrows = 0, nnzb = 0;
   int b = 0, prec = P_FP64;
+  int row_major = 0;        // 1: blocks stored row-major (tensor-core batched path)
   int* row_ptr = nullptr;   // nrows + 1
   int* col = nullptr;       // nnzb
   void* vals = nullptr;     // nnzb * b * b elements
@@ -35,23 +36,54 @@ unsigned long long launches();
 // vector type: double when prec == P_FP64, float otherwise
 cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
                       void* y, double s, cudaStream_t st);
+// Same on R right-hand sides (CUDA cores, column-major blocks): entry (element e,
+// rhs r, mode c) of every vector lives at e*es + r*rs + c.  Each right-hand side
+// is computed exactly as the single-RHS apply would compute it.
+cudaError_t bsr_apply_strided(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
+                              void* y, double s, int R, int64_t es, int64_t rs, cudaStream_t st);
 
-// vals[nz] = transpose(pool[ids[nz]]) converted to `prec` (pool blocks row-major FP64)
+// Batched apply on tensor cores (tc_apply.cu): BF16 row-major blocks, FP32 vectors.
+struct BatchArgs {
+  int64_t nrows;
+  const int* row_ptr;
+  const int* col;
+  const void* vals;       // row-major BF16 blocks
+  const float* x;
+  const float* rhs;
+  const float* xin;
+  float* y;
+  double s;
+  int mode;
+  int R;                  // right-hand sides, 1..128
+  int64_t es, rs;         // element and right-hand-side strides of the vectors (floats)
+  int* err;               // set to 1 if a bounded wait gave up (may be null)
+};
+bool tc_block_size_supported(int b);
+cudaError_t bsr_apply_tc(const BatchArgs& a, int b, cudaStream_t st);
+
+// vals[nz] = pool[ids[nz]] converted to `prec`, stored column-major
+// (row_major = 0) or row-major (row_major = 1); pool blocks are row-major FP64
 cudaError_t expand_blocks(int64_t nnzb, int b, const uint32_t* ids, const double* pool, void* vals,
-                          int prec, cudaStream_t st);
+                          int prec, int row_major, cudaStream_t st);
 
 // P: device array of the 1D child-injection matrices P[s][i][j] (2*q*q doubles,
 // q = p + 1 <= 8).  Level vectors are double (vprec 0) or float (vprec 1).
+// Vectors of R right-hand sides use the layout [element][rhs][mode] (R = 1:
+// plain [element][mode]).
 // rc_C = sum_children P_c^T rf_c
 cudaError_t restrict_apply(int d, int q, int n_fine, const double* P, const void* rf, void* rc,
-                           int vprec, cudaStream_t st);
+                           int vprec, int R, cudaStream_t st);
 // xf_c += P_c xc_C
 cudaError_t prolong_apply(int d, int q, int n_fine, const double* P, const void* xc, void* xf,
-                          int vprec, cudaStream_t st);
+                          int vprec, int R, cudaStream_t st);
 
-// y = Pinv v, Pinv dense n x n FP64 row-major; v, y of type vprec
-cudaError_t dense_gemv(int64_t n, const double* Pinv, const void* v, void* y, int vprec,
+// y = Pinv v, Pinv dense n x n FP64 row-major (n = N*b), per right-hand side
+cudaError_t dense_gemv(int64_t n, int b, const double* Pinv, const void* v, void* y, int vprec, int R,
                        cudaStream_t st);
+
+// layout changes between R stacked vectors [rhs][element][mode] and [element][rhs][mode]
+cudaError_t stack_to_batch(int64_t N, int R, int b, const double* src, double* dst, cudaStream_t st);
+cudaError_t batch_to_stack(int64_t N, int R, int b, const double* src, double* dst, cudaStream_t st);
 
 // conversions and BLAS-1 (FP64 unless stated)
 cudaError_t cast_d2f(int64_t n, const double* a, float* b, cudaStream_t st);
@@ -69,6 +101,12 @@ cudaError_t strided_sum(int64_t count, int64_t stride, const double* v, double* 
 cudaError_t strided_sub_mean(int64_t count, int64_t stride, double* v, const double* sum,
                              cudaStream_t st);
 
+// per right-hand-side dots on [element][rhs][mode] vectors: out[r] = sum u_r v_r
+// (v may be null: sum of squares of u).  partials: kBatchDotBlocks * R doubles.
+constexpr int kBatchDotBlocks = 256;
+cudaError_t dot_batched(int64_t N, int R, int b, const double* u, const double* v, double* partials,
+                        double* out, cudaStream_t st);
+
 // CG scalar slots
 enum CgSlot { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZNEW = 3, S_RZOLD = 4, S_ALPHA = 5, S_BETA = 6,
               S_BB = 7, S_TMP = 8, kCgSlots = 16 };
@@ -78,5 +116,14 @@ cudaError_t cg_update_xr(int64_t n, double* x, double* r, const double* p, const
 cudaError_t cg_beta(double* scal, int flexible, cudaStream_t st);       // beta, rz <- rz_new
 cudaError_t cg_update_p(int64_t n, double* p, const double* z, const double* scal,
                         cudaStream_t st);                              // p = z + beta p
+// Batched CG: scalars scal[slot * R + r]; active[r] = 0 freezes right-hand side r
+cudaError_t cg_alpha_b(int R, double* scal, const int* active, cudaStream_t st);
+cudaError_t cg_update_xr_b(int64_t N, int R, int b, double* x, double* r, const double* p, const double* q,
+                           const double* scal, cudaStream_t st);
+cudaError_t cg_beta_b(int R, double* scal, const int* active, int flexible, cudaStream_t st);
+cudaError_t cg_update_p_b(int64_t N, int R, int b, double* p, const double* z, const double* scal,
+                          cudaStream_t st);
+// launch-count bookkeeping for kernels defined in other translation units
+cudaError_t launched(int count = 1);
 
 }  // namespace ldgmg

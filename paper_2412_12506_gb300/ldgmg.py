@@ -43,7 +43,7 @@ class SetupOpts(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("sai_level", ctypes.c_int), ("balance", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("pre_form", ctypes.c_int), ("post_form", ctypes.c_int),
-                ("vcycle_precision", ctypes.c_int), ("max_iter", ctypes.c_int)]
+                ("vcycle_precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_rhs", ctypes.c_int)]
 
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -60,6 +60,7 @@ _SIGS = {
     "ldgmg_solve": (_i, [_vp, _vp, _d, _vp, _i, _P(_i), _P(_d), _vp]),
     "ldgmg_level_apply": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "ldgmg_level_smooth": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _vp]),
+    "ldgmg_level_apply_batched": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
     "ldgmg_level_restrict": (_i, [_vp, _i, _vp, _vp, _vp, _vp]),
     "ldgmg_level_prolong": (_i, [_vp, _i, _vp, _vp, _vp]),
     "ldgmg_bottom_solve": (_i, [_vp, _vp, _vp, _vp]),
@@ -104,7 +105,7 @@ def project_kernel_noalloc(v, N, b, stream=None):
 
 
 def make_opts(smoother="sai", sai_level=1, balance=True, nu1=3, nu2=3, omega=0.8, pre="B1", post="BT",
-              precision="fp64", max_iter=200) -> SetupOpts:
+              precision="fp64", max_iter=200, max_rhs=1) -> SetupOpts:
     o = SetupOpts()
     _lib.ldgmg_default_opts(ctypes.byref(o))
     o.smoother = _SMOOTHER[smoother]
@@ -114,6 +115,7 @@ def make_opts(smoother="sai", sai_level=1, balance=True, nu1=3, nu2=3, omega=0.8
     o.pre_form, o.post_form = _FORM[pre], _FORM[post]
     o.vcycle_precision = _PREC[precision]
     o.max_iter = max_iter
+    o.max_rhs = max_rhs
     return o
 
 
@@ -195,15 +197,22 @@ class Operator:
         self.N, self.b, self.nnzb = N.value, b.value, nnz.value
         self.size = self.N * self.b
 
+    def _nrhs(self, t):
+        n = t.numel() // self.size
+        if n * self.size != t.numel():
+            raise ValueError("vector length is not a multiple of N*b")
+        return n
+
     def apply(self, x, y=None, stream=None):
+        """y = A x; x holds one or several stacked vectors (shape (size,) or (nrhs, size))."""
         import torch
         if y is None:
             y = torch.empty_like(x)
-        _check(_lib.ldgmg_apply(self._h, _ptr(x), _ptr(y), 1, _stream(stream)))
+        _check(_lib.ldgmg_apply(self._h, _ptr(x), _ptr(y), self._nrhs(x), _stream(stream)))
         return y
 
     def project_kernel(self, v, stream=None):
-        _check(_lib.ldgmg_project_kernel(self._h, _ptr(v), 1, _stream(stream)))
+        _check(_lib.ldgmg_project_kernel(self._h, _ptr(v), self._nrhs(v), _stream(stream)))
         return v
 
     def __del__(self):
@@ -241,21 +250,34 @@ class Hierarchy:
         import torch
         if x is None:
             x = torch.empty_like(b)
-        _check(_lib.ldgmg_vcycle(self._h, _ptr(b), _ptr(x), 1, _stream(stream)))
+        _check(_lib.ldgmg_vcycle(self._h, _ptr(b), _ptr(x), self.op._nrhs(b), _stream(stream)))
         return x
 
     def solve(self, rhs, tol=1e-10, x=None, stream=None, check=True):
         """Returns (x, iterations, true relative residual, status).  rhs/x may be
-        CUDA or CPU tensors (host buffers are staged by the library)."""
+        CUDA or CPU tensors (host buffers are staged by the library).  With
+        nrhs stacked right-hand sides (shape (nrhs, size)), iterations and
+        residuals are lists."""
         import torch
         if x is None:
             x = torch.empty_like(rhs)
-        it, rr = ctypes.c_int(), ctypes.c_double()
-        st = _lib.ldgmg_solve(self._h, _ptr(rhs), tol, _ptr(x), 1, ctypes.byref(it), ctypes.byref(rr),
-                              _stream(stream))
+        nr = self.op._nrhs(rhs)
+        it = (ctypes.c_int * nr)()
+        rr = (ctypes.c_double * nr)()
+        st = _lib.ldgmg_solve(self._h, _ptr(rhs), tol, _ptr(x), nr, it, rr, _stream(stream))
         if check and st not in (OK,):
             _check(st)
-        return x, it.value, rr.value, st
+        if nr == 1:
+            return x, it[0], rr[0], st
+        return x, list(it), list(rr), st
+
+    def level_apply_batched(self, level, which, x, nrhs, y=None, stream=None):
+        """y = M x for nrhs right-hand sides, float vectors [element][rhs][mode]."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        _check(_lib.ldgmg_level_apply_batched(self._h, level, which, nrhs, _ptr(x), _ptr(y), _stream(stream)))
+        return y
 
     # per-level entry points (vectors in the hierarchy's working dtype)
     def level_apply(self, level, which, x, y=None, stream=None):
