@@ -52,7 +52,7 @@ typedef enum {
 
 enum { LDGMG_JACOBI = 0, LDGMG_SAI = 1 };                  /* smoother kind */
 enum { LDGMG_FORM_B1 = 0, LDGMG_FORM_BT = 1 };            /* SAI smoother form, Eqs. B1 / BT */
-enum { LDGMG_FP64 = 0, LDGMG_FP32 = 1, LDGMG_BF16 = 2 };   /* V-cycle precision */
+enum { LDGMG_FP64 = 0, LDGMG_FP32 = 1, LDGMG_BF16 = 2, LDGMG_FP16 = 3 };   /* V-cycle precision */
 enum { LDGMG_MAT_A = 0, LDGMG_MAT_B = 1, LDGMG_MAT_BT = 2, LDGMG_MAT_D = 3 }; /* level matrices */
 
 typedef struct {
@@ -69,11 +69,14 @@ typedef struct {
   double omega;          /* Jacobi damping (paper: 0.8, Eq. Jsmooth) */
   int pre_form;          /* SAI form of the pre-sweeps  (B1 = Eq. B1) */
   int post_form;         /* SAI form of the post-sweeps (BT = Eq. BT); B1/BT is symmetric */
-  int vcycle_precision;  /* LDGMG_FP64, LDGMG_FP32 or LDGMG_BF16 (matrix storage; FP32 accumulate) */
+  int vcycle_precision;  /* V-cycle matrix storage, FP32 accumulate: LDGMG_FP64, LDGMG_FP32,
+                            LDGMG_BF16, or LDGMG_FP16 (each level matrix scaled by a power of
+                            two so its largest entry is in [2^14, 2^15)) */
   int max_iter;          /* Krylov iteration cap for ldgmg_solve */
   int max_rhs;           /* right-hand sides per call, 1..128.  > 1 builds the batched
-                            hierarchy: BF16 storage (vcycle_precision must be LDGMG_BF16),
-                            b = 16 or 64, V-cycle block applies on tensor cores */
+                            hierarchy: b = 16 or 64, V-cycle block applies on tensor cores,
+                            vcycle_precision LDGMG_BF16 (BF16 blocks) or LDGMG_FP32 (FP32
+                            blocks split into two BF16 parts on the fly) */
 } ldgmg_setup_opts;
 
 typedef struct ldgmg_op ldgmg_op;
@@ -181,7 +184,7 @@ ldgmg_status ldgmg_level_prolong(ldgmg_hier* h, int level, const void* xc_dev, v
 ldgmg_status ldgmg_bottom_solve(ldgmg_hier* h, const void* rhs_dev, void* x_dev, void* stream);
 
 /* Copy a level matrix to host memory as FP64 block-CSR (values as stored on the
- * device, converted to double).  row_ptr: N+1 int64, col: nnzb int32, vals:
+ * device, converted to double and divided by the storage scale).  row_ptr: N+1 int64, col: nnzb int32, vals:
  * nnzb*b*b doubles, block (r, c) at vals[nz*b*b + r*b + c].  Any of the three
  * may be NULL to skip it.  Test/inspection entry point. */
 ldgmg_status ldgmg_export_level(ldgmg_hier* h, int level, int which, int64_t* row_ptr,

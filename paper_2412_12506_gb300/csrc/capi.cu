@@ -52,6 +52,18 @@ static ldgmg_status fail(ldgmg_status s, const std::string& msg) {
 
 static size_t esize(int prec) { return prec == P_FP64 ? 8 : (prec == P_FP32 ? 4 : 2); }
 
+// Power-of-two storage scale for FP16 blocks: the largest entry lands in
+// [2^14, 2^15), well inside the FP16 range (max 65504); 1 for other types.
+static double storage_scale(const PBSR& H, int prec) {
+  if (prec != P_FP16) return 1.0;
+  double mx = 0.0;
+  for (double v : H.pool.data) mx = std::max(mx, std::fabs(v));
+  if (!(mx > 0.0)) return 1.0;
+  int e = 0;
+  std::frexp(mx, &e);            // mx in [2^(e-1), 2^e)
+  return std::ldexp(1.0, 15 - e);
+}
+
 template <class T>
 static ldgmg_status dalloc(T** p, size_t bytes) {
   *p = nullptr;
@@ -79,6 +91,7 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat
   M.b = b;
   M.prec = prec;
   M.row_major = row_major;
+  M.scale = storage_scale(H, prec);
   std::vector<int> rp(H.row_ptr.begin(), H.row_ptr.end());
   CKS(dalloc(&M.row_ptr, rp.size() * sizeof(int)));
   CKS(dalloc(&M.col, H.col.size() * sizeof(int)));
@@ -93,7 +106,7 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat
     CK(cudaMemcpyAsync(d_ids, H.id.data(), H.id.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_pool, H.pool.data.data(), H.pool.data.size() * sizeof(double),
                        cudaMemcpyHostToDevice, st));
-    CK(expand_blocks(M.nnzb, b, d_ids, d_pool, M.vals, prec, row_major, st));
+    CK(expand_blocks(M.nnzb, b, d_ids, d_pool, M.vals, prec, row_major, M.scale, st));
   }
   CK(cudaStreamSynchronize(st));
   cudaFree(d_ids);
@@ -171,7 +184,7 @@ static ldgmg_status apply_mat(ldgmg_hier* h, const DevMat& M, int mode, const vo
     a.es = R * b;
     a.rs = b;
     a.err = h ? h->err : nullptr;
-    CK(bsr_apply_tc(a, M.b, st));
+    CK(bsr_apply_tc(a, M.b, M.prec, st));
     return LDGMG_OK;
   }
   CK(bsr_apply_strided(M, mode, x, rhs, xin, y, s, R, R * b, b, st));
@@ -392,13 +405,13 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   *out = nullptr;
   if (o->smoother != LDGMG_JACOBI && o->smoother != LDGMG_SAI) return fail(LDGMG_EINVAL, "smoother");
   if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 > 64 || o->nu2 > 64) return fail(LDGMG_EINVAL, "nu1/nu2");
-  if (o->vcycle_precision < 0 || o->vcycle_precision > 2) return fail(LDGMG_EINVAL, "precision");
+  if (o->vcycle_precision < 0 || o->vcycle_precision > 3) return fail(LDGMG_EINVAL, "precision");
   if (o->max_iter < 1) return fail(LDGMG_EINVAL, "max_iter");
   if (o->max_rhs < 1 || o->max_rhs > 128) return fail(LDGMG_EINVAL, "max_rhs must be in 1..128");
   if (o->smoother == LDGMG_JACOBI && !(o->omega > 0.0 && o->omega < 2.0)) return fail(LDGMG_EINVAL, "omega");
   const bool batched = o->max_rhs > 1;
-  if (batched && o->vcycle_precision != LDGMG_BF16)
-    return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 needs vcycle_precision = LDGMG_BF16 (tensor-core path)");
+  if (batched && o->vcycle_precision != LDGMG_BF16 && o->vcycle_precision != LDGMG_FP32)
+    return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 needs vcycle_precision LDGMG_BF16 or LDGMG_FP32 (tensor-core path)");
   if (batched && !tc_block_size_supported(op->host.b))
     return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 needs b = 16 or 64 (p = 3)");
   cudaStream_t st = (cudaStream_t)stream;
@@ -804,6 +817,15 @@ ldgmg_status ldgmg_bottom_solve(ldgmg_hier* h, const void* rhs, void* x, void* s
   return LDGMG_OK;
 }
 
+static double fp16_to_double(uint16_t v) {
+  const int sign = v >> 15, ex = (v >> 10) & 0x1F, man = v & 0x3FF;
+  double mag;
+  if (ex == 0) mag = std::ldexp(double(man), -24);                 // subnormal
+  else if (ex == 31) mag = man ? NAN : INFINITY;
+  else mag = std::ldexp(double(man | 0x400), ex - 25);
+  return sign ? -mag : mag;
+}
+
 static float bf16_to_float(uint16_t v) {
   uint32_t u = uint32_t(v) << 16;
   float f;
@@ -835,8 +857,9 @@ ldgmg_status ldgmg_export_level(ldgmg_hier* h, int l, int which, int64_t* row_pt
       double v;
       if (M->prec == P_FP64) v = reinterpret_cast<const double*>(raw.data())[t];
       else if (M->prec == P_FP32) v = reinterpret_cast<const float*>(raw.data())[t];
-      else v = bf16_to_float(reinterpret_cast<const uint16_t*>(raw.data())[t]);
-      vals[nz * b * b + r * b + c] = v;
+      else if (M->prec == P_BF16) v = bf16_to_float(reinterpret_cast<const uint16_t*>(raw.data())[t]);
+      else v = fp16_to_double(reinterpret_cast<const uint16_t*>(raw.data())[t]);
+      vals[nz * b * b + r * b + c] = v / M->scale;
     }
   }
   return LDGMG_OK;

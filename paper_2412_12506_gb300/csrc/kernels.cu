@@ -14,6 +14,7 @@
 #include "kernels.h"
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <atomic>
@@ -22,6 +23,7 @@
 namespace ldgmg {
 
 typedef __nv_bfloat16 bf16;
+typedef __half f16;
 
 // number of kernels this library has enqueued (all streams, all devices)
 static std::atomic<unsigned long long> g_launches{0};
@@ -36,12 +38,14 @@ template <class T> __device__ __forceinline__ T from_d(double v);
 template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_d<float>(double v) { return float(v); }
 template <> __device__ __forceinline__ bf16 from_d<bf16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ f16 from_d<f16>(double v) { return __double2half(v); }
 
 template <class TACC, class TA> __device__ __forceinline__ TACC cvt(TA v) { return TACC(v); }
 template <> __device__ __forceinline__ float cvt<float, bf16>(bf16 v) { return __bfloat162float(v); }
 template <> __device__ __forceinline__ double cvt<double, bf16>(bf16 v) {
   return double(__bfloat162float(v));
 }
+template <> __device__ __forceinline__ float cvt<float, f16>(f16 v) { return __half2float(v); }
 
 template <class T, int N> struct alignas(sizeof(T) * N) VecT { T v[N]; };
 
@@ -68,6 +72,7 @@ template <class TA, class TV> struct BsrArgs {
   int mode;
   int64_t es, rs;   // vector entry (element e, rhs r, mode c) at e*es + r*rs + c; rhs = blockIdx.y
   int R;            // right-hand sides (grid y dimension)
+  double inv_scale; // 1 / storage scale of the matrix (exact power of two)
 };
 
 template <int TEAM> __device__ __forceinline__ void team_sync() {
@@ -128,6 +133,7 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
     TACC sum = TACC(0);
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) sum += red[team][gg][lt];
+    sum *= TACC(a.inv_scale);
     const int64_t o = row * a.es + roff + lt;
     switch (a.mode) {
       case M_Y: a.y[o] = TV(sum); break;
@@ -172,6 +178,7 @@ static cudaError_t launch_bsr_t(const DevMat& M, int mode, const void* x, const 
   a.es = es;
   a.rs = rs;
   a.R = R;
+  a.inv_scale = 1.0 / M.scale;
   switch (M.b) {
     case 4: return launch_bsr_b<4>(M, a, st);
     case 8: return launch_bsr_b<8>(M, a, st);
@@ -192,6 +199,7 @@ cudaError_t bsr_apply_strided(const DevMat& M, int mode, const void* x, const vo
     case P_FP64: return launch_bsr_t<double, double>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
     case P_FP32: return launch_bsr_t<float, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
     case P_BF16: return launch_bsr_t<bf16, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
+    case P_FP16: return launch_bsr_t<f16, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -207,7 +215,7 @@ cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs,
 
 template <class T>
 __global__ void expand_kernel(int64_t total, int b, const uint32_t* __restrict__ ids,
-                              const double* __restrict__ pool, T* __restrict__ vals, int row_major) {
+                              const double* __restrict__ pool, T* __restrict__ vals, int row_major, double scale) {
   const int64_t bb = int64_t(b) * b;
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
        t += int64_t(gridDim.x) * blockDim.x) {
@@ -215,19 +223,20 @@ __global__ void expand_kernel(int64_t total, int b, const uint32_t* __restrict__
     int r, c;
     if (row_major) { r = int(e / b); c = int(e % b); }
     else { c = int(e / b); r = int(e % b); }
-    vals[t] = from_d<T>(pool[int64_t(ids[nz]) * bb + int64_t(r) * b + c]);
+    vals[t] = from_d<T>(scale * pool[int64_t(ids[nz]) * bb + int64_t(r) * b + c]);
   }
 }
 
 cudaError_t expand_blocks(int64_t nnzb, int b, const uint32_t* ids, const double* pool, void* vals,
-                          int prec, int row_major, cudaStream_t st) {
+                          int prec, int row_major, double scale, cudaStream_t st) {
   const int64_t total = nnzb * b * b;
   if (total == 0) return cudaSuccess;
   const int grid = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
   switch (prec) {
-    case P_FP64: expand_kernel<double><<<grid, 256, 0, st>>>(total, b, ids, pool, (double*)vals, row_major); break;
-    case P_FP32: expand_kernel<float><<<grid, 256, 0, st>>>(total, b, ids, pool, (float*)vals, row_major); break;
-    case P_BF16: expand_kernel<bf16><<<grid, 256, 0, st>>>(total, b, ids, pool, (bf16*)vals, row_major); break;
+    case P_FP64: expand_kernel<double><<<grid, 256, 0, st>>>(total, b, ids, pool, (double*)vals, row_major, scale); break;
+    case P_FP32: expand_kernel<float><<<grid, 256, 0, st>>>(total, b, ids, pool, (float*)vals, row_major, scale); break;
+    case P_BF16: expand_kernel<bf16><<<grid, 256, 0, st>>>(total, b, ids, pool, (bf16*)vals, row_major, scale); break;
+    case P_FP16: expand_kernel<f16><<<grid, 256, 0, st>>>(total, b, ids, pool, (f16*)vals, row_major, scale); break;
     default: return cudaErrorInvalidValue;
   }
   return launched();

@@ -6,7 +6,7 @@
 
 namespace ldgmg {
 
-enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2 };
+enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2, P_FP16 = 3 };
 
 // Block-CSR matrix resident on the device.  Block nz of row i is the dense
 // b x b block M_{i, col[nz]}, stored column-major: element (r, c) at
@@ -15,6 +15,7 @@ struct DevMat {
   int64_t nrows = 0, nnzb = 0;
   int b = 0, prec = P_FP64;
   int row_major = 0;        // 1: blocks stored row-major (tensor-core batched path)
+  double scale = 1.0;       // stored value = scale * entry (a power of two; FP16 storage only)
   int* row_ptr = nullptr;   // nrows + 1
   int* col = nullptr;       // nnzb
   void* vals = nullptr;     // nnzb * b * b elements
@@ -47,7 +48,7 @@ struct BatchArgs {
   int64_t nrows;
   const int* row_ptr;
   const int* col;
-  const void* vals;       // row-major BF16 blocks
+  const void* vals;       // row-major blocks, BF16 or FP32 (split into hi/lo BF16 while staging)
   const float* x;
   const float* rhs;
   const float* xin;
@@ -59,12 +60,13 @@ struct BatchArgs {
   int* err;               // set to 1 if a bounded wait gave up (may be null)
 };
 bool tc_block_size_supported(int b);
-cudaError_t bsr_apply_tc(const BatchArgs& a, int b, cudaStream_t st);
+// prec: P_BF16 (2 MMAs per K step) or P_FP32 (3 MMAs: A_hi x_hi + A_hi x_lo + A_lo x_hi)
+cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st);
 
-// vals[nz] = pool[ids[nz]] converted to `prec`, stored column-major
+// vals[nz] = scale * pool[ids[nz]] converted to `prec`, stored column-major
 // (row_major = 0) or row-major (row_major = 1); pool blocks are row-major FP64
 cudaError_t expand_blocks(int64_t nnzb, int b, const uint32_t* ids, const double* pool, void* vals,
-                          int prec, int row_major, cudaStream_t st);
+                          int prec, int row_major, double scale, cudaStream_t st);
 
 // P: device array of the 1D child-injection matrices P[s][i][j] (2*q*q doubles,
 // q = p + 1 <= 8).  Level vectors are double (vprec 0) or float (vprec 1).

@@ -8,6 +8,10 @@
 // are split into hi + lo BF16 parts (hi = bf16(x), lo = bf16(x - hi)) and both
 // are multiplied, so the product carries ~16 bits of x -- the same accuracy
 // as the CUDA-core path that multiplies BF16-stored blocks by FP32 vectors.
+// With FP32-stored blocks the matrix is split the same way while it is staged
+// and three products are accumulated (A_hi x_hi + A_hi x_lo + A_lo x_hi;
+// A_lo x_lo is below 2^-16 of the result), which gives FP32-like accuracy on
+// the BF16 tensor cores.
 //
 // Operands are staged into shared memory in the canonical K-major,
 // no-swizzle layout: 8-row x 16-byte core matrices, rows 16 B apart, core
@@ -112,15 +116,15 @@ __device__ __forceinline__ uint32_t core_off(int row, int kq, int KQ) {
   return uint32_t(((row >> 3) * KQ + kq) * 128 + (row & 7) * 16);
 }
 
-template <int B>
+template <int B, bool SPLIT>
 struct TcSmem {
   static constexpr int KQ = B / 8;
   static constexpr int A_BYTES = kTcM * B * 2;   // one BF16 operand part (hi or lo)
   static constexpr int B_BYTES = B * B * 2;
-  static constexpr int TOTAL = 2 * A_BYTES + B_BYTES + 128;
+  static constexpr int TOTAL = 2 * A_BYTES + (SPLIT ? 2 : 1) * B_BYTES + 128;
 };
 
-template <int B>
+template <int B, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   static_assert(B == 16 || B == 64, "tensor-core path supports b = 16 and b = 64");
   constexpr int KQ = B / 8;
@@ -128,10 +132,12 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   constexpr uint32_t NCOLS = B < 32 ? 32 : B;
   constexpr uint32_t IDESC = make_idesc(kTcM, B);
   extern __shared__ __align__(1024) unsigned char smem[];
+  typedef TcSmem<B, SPLIT> L;
   unsigned char* a_hi = smem;
-  unsigned char* a_lo = smem + TcSmem<B>::A_BYTES;
-  unsigned char* b_op = smem + 2 * TcSmem<B>::A_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(b_op + TcSmem<B>::B_BYTES);
+  unsigned char* a_lo = smem + L::A_BYTES;
+  unsigned char* b_op = smem + 2 * L::A_BYTES;
+  unsigned char* b_lo = b_op + L::B_BYTES;       // used only when SPLIT
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::TOTAL - 128);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -158,7 +164,7 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo), sb = smem_u32(b_op);
+  const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo), sb = smem_u32(b_op), sb_lo = smem_u32(b_lo);
   constexpr uint32_t SBO = KQ * 128;
   uint32_t phase = 0;
   bool timed_out = false;
@@ -167,11 +173,30 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
     const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
     for (int nz = z0; nz < z1; ++nz) {
       const int64_t j = a.col[nz];
-      // stage A_ij (row-major BF16): chunk (r, kq) = 8 consecutive columns of row r
-      const uint4* blk = reinterpret_cast<const uint4*>(a.vals) + int64_t(nz) * (B * B / 8);
-      for (int t = tid; t < B * KQ; t += kTcThreads) {
-        const int r = t / KQ, kq = t % KQ;
-        *reinterpret_cast<uint4*>(b_op + core_off(r, kq, KQ)) = __ldg(blk + t);
+      // stage A_ij (row-major): chunk (r, kq) = 8 consecutive columns of row r
+      if (!SPLIT) {
+        const uint4* blk = reinterpret_cast<const uint4*>(a.vals) + int64_t(nz) * (B * B / 8);
+        for (int t = tid; t < B * KQ; t += kTcThreads) {
+          const int r = t / KQ, kq = t % KQ;
+          *reinterpret_cast<uint4*>(b_op + core_off(r, kq, KQ)) = __ldg(blk + t);
+        }
+      } else {
+        const float4* blk = reinterpret_cast<const float4*>(a.vals) + int64_t(nz) * (B * B / 4);
+        for (int t = tid; t < B * KQ; t += kTcThreads) {
+          const int r = t / KQ, kq = t % KQ;
+          const float4 v0 = __ldg(blk + 2 * t), v1 = __ldg(blk + 2 * t + 1);
+          const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+            const float2 hf = __bfloat1622float2(h);
+            hi[e] = *reinterpret_cast<const uint32_t*>(&h);
+            lo[e] = pack_bf16(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+          }
+          *reinterpret_cast<uint4*>(b_op + core_off(r, kq, KQ)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(b_lo + core_off(r, kq, KQ)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
       }
       // stage X_j^T as hi/lo BF16: chunk (m, kq) = modes 8kq..8kq+7 of right-hand side m
       const float* xj = a.x + j * a.es;
@@ -198,8 +223,10 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
 #pragma unroll
         for (int s = 0; s < KSTEPS; ++s) {
           const uint64_t bd = make_sdesc(sb + 256u * s, 128u, SBO);
-          mma_bf16(tmem, make_sdesc(sa_hi + 256u * s, 128u, SBO), bd, IDESC, (nz > z0 || s > 0) ? 1u : 0u);
+          const uint64_t ah = make_sdesc(sa_hi + 256u * s, 128u, SBO);
+          mma_bf16(tmem, ah, bd, IDESC, (nz > z0 || s > 0) ? 1u : 0u);
           mma_bf16(tmem, make_sdesc(sa_lo + 256u * s, 128u, SBO), bd, IDESC, 1u);
+          if (SPLIT) mma_bf16(tmem, ah, make_sdesc(sb_lo + 256u * s, 128u, SBO), IDESC, 1u);
         }
         mma_commit(bar);
       }
@@ -272,27 +299,30 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
 
 bool tc_block_size_supported(int b) { return b == 16 || b == 64; }
 
-template <int B>
+template <int B, bool SPLIT>
 static cudaError_t launch_tc(const BatchArgs& a, cudaStream_t st) {
-  const int smem = TcSmem<B>::TOTAL;
+  const int smem = TcSmem<B, SPLIT>::TOTAL;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(bsr_tc_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(bsr_tc_kernel<B, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   // at most 8 CTAs per SM (TMEM: 8 x 64 columns = 512), persistent over rows
   const int64_t grid = std::min<int64_t>(a.nrows, 152 * 8);
   if (grid <= 0) return cudaSuccess;
-  bsr_tc_kernel<B><<<unsigned(grid), kTcThreads, smem, st>>>(a);
+  bsr_tc_kernel<B, SPLIT><<<unsigned(grid), kTcThreads, smem, st>>>(a);
   return launched();
 }
 
-cudaError_t bsr_apply_tc(const BatchArgs& a, int b, cudaStream_t st) {
+cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st) {
   if (a.R < 1 || a.R > kTcM) return cudaErrorInvalidValue;
+  const bool split = prec == P_FP32;
+  if (!split && prec != P_BF16) return cudaErrorInvalidValue;
   switch (b) {
-    case 16: return launch_tc<16>(a, st);
-    case 64: return launch_tc<64>(a, st);
+    case 16: return split ? launch_tc<16, true>(a, st) : launch_tc<16, false>(a, st);
+    case 64: return split ? launch_tc<64, true>(a, st) : launch_tc<64, false>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -22,9 +22,9 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, EUNSUPPORTED = range(7)
 JACOBI, SAI = 0, 1
 FORM_B1, FORM_BT = 0, 1
-FP64, FP32, BF16 = 0, 1, 2
+FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 MAT_A, MAT_B, MAT_BT, MAT_D = 0, 1, 2, 3
-_PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
+_PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
 _FORM = {"B1": FORM_B1, "BT": FORM_BT}
 _SMOOTHER = {"jacobi": JACOBI, "sai": SAI}
 

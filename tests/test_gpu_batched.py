@@ -33,11 +33,13 @@ def _batch_layout(stacked, N, b):
     return np.ascontiguousarray(stacked.reshape(R, N, b).transpose(1, 0, 2))
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
 @pytest.mark.parametrize("d,n,p", [(2, 10, 3), (3, 6, 3)])
 @pytest.mark.parametrize("R", [1, 5, 64, 128])
-def test_tensor_core_apply_matches_stored_blocks(lib, d, n, p, R):
+def test_tensor_core_apply_matches_stored_blocks(lib, d, n, p, R, prec):
+    """BF16 blocks: 2 MMAs (x hi/lo); FP32 blocks: 3 MMAs (A and x hi/lo)."""
     op = lib.Operator(d, n, p)
-    H = lib.Hierarchy(op, smoother="sai", precision="bf16", max_rhs=2, nu1=1, nu2=1)
+    H = lib.Hierarchy(op, smoother="sai", precision=prec, max_rhs=2, nu1=1, nu2=1)
     N, b = op.N, op.b
     rng = np.random.default_rng(R)
     for which in (lib.MAT_A, lib.MAT_B, lib.MAT_BT):
@@ -65,14 +67,16 @@ def test_stacked_apply_and_vcycle_equal_single(lib):
         assert torch.equal(V[r], H.vcycle(X[r].clone()))
 
 
-@pytest.mark.parametrize("d,n,p,mu_kind", [(2, 16, 3, None), (3, 6, 3, None), (2, 16, 3, "square100")])
-def test_batched_solve_equals_alone_and_oracle(lib, d, n, p, mu_kind):
-    mu = square_mu(d, n, mu_in=1e2) if mu_kind else None
+@pytest.mark.parametrize("prec,d,n,p,mu_kind", [("bf16", 2, 16, 3, None), ("bf16", 3, 6, 3, None),
+                                                ("bf16", 2, 16, 3, "square100"), ("fp32", 2, 16, 3, None),
+                                                ("fp32", 3, 6, 3, None), ("fp32", 2, 32, 3, "square")])
+def test_batched_solve_equals_alone_and_oracle(lib, prec, d, n, p, mu_kind):
+    mu = None if mu_kind is None else square_mu(d, n, mu_in=1e2 if mu_kind == "square100" else 1e4)
     N, b = n ** d, (p + 1) ** d
     R = 6
     rhs = np.stack([ldg.project_out_constant(random_rhs(N, b, seed=100 + r), d, p, N) for r in range(R)])
     op = lib.Operator(d, n, p, mu)
-    H = lib.Hierarchy(op, smoother="sai", precision="bf16", max_rhs=R)
+    H = lib.Hierarchy(op, smoother="sai", precision=prec, max_rhs=R)
     X, its, res, st = H.solve(torch.tensor(rhs, device="cuda"))
     assert st == lib.OK
     assert max(res) <= 1.05e-10
@@ -86,7 +90,7 @@ def test_batched_solve_equals_alone_and_oracle(lib, d, n, p, mu_kind):
         xg = ldg.project_out_constant(X[r].cpu().numpy(), d, p, N)
         xo = ldg.project_out_constant(xo, d, p, N)
         assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
-    print(f"\nbatched bf16 d={d} n={n} p={p} mu={mu_kind}: iterations {its}")
+    print(f"\nbatched {prec} d={d} n={n} p={p} mu={mu_kind}: iterations {its}")
 
 
 def test_batched_setup_rejects_unsupported(lib):
@@ -96,7 +100,7 @@ def test_batched_setup_rejects_unsupported(lib):
     assert e.value.status == lib.EUNSUPPORTED
     op3 = lib.Operator(2, 8, 3)
     with pytest.raises(lib.LdgmgError):
-        lib.Hierarchy(op3, smoother="sai", precision="fp32", max_rhs=8)
+        lib.Hierarchy(op3, smoother="sai", precision="fp16", max_rhs=8)
     H = lib.Hierarchy(op3, smoother="sai", precision="bf16", max_rhs=2)
     with pytest.raises(lib.LdgmgError):
         H.solve(torch.zeros(3, op3.size, dtype=torch.float64, device="cuda"))
