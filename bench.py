@@ -9,12 +9,16 @@ zero mean.  One step = one complete solve (every row of the hot path: FP64
 operator apply + CG vector work, and per V-cycle the smoother sweeps,
 residuals, restrictions, prolongations and the bottom solve).
 
-`value` is the mixed-precision path (V-cycle in --precision, FP64 outer
-flexible CG); the plain FP64 GPU solver is timed beside it.  `e2e` repeats
-the mixed solves through the C-ABI with pinned host buffers (host<->device
-copies inside the timed region).  `roofline` covers the dominant kernel, the
-block-row apply (ldgmg bsr_kernel) on the finest level's SAI matrix.
-`cpu_baseline` / `--impl reference` time the CPU oracle on a bounded sample.
+`value` is the mixed-precision path (V-cycle in --precision, default FP16
+storage with FP32 accumulation, FP64 outer flexible CG); the plain FP64 GPU
+solver is timed beside it.  `e2e` repeats the mixed solves through the C-ABI
+with pinned host buffers (host<->device copies inside the timed region).
+`roofline` covers the dominant kernel, the block-row apply (ldgmg
+bsr_kernel) on the finest level's SAI matrix.  `batched` reports the
+interface workload with 64 right-hand sides per call on the tensor-core path
+(2D 256^2, p = 3, mu 1 / 1e4 on the inclusion (1/4, 3/4)^2, balanced SAI1)
+against one-at-a-time FP64 solves.  `cpu_baseline` / `--impl reference` time
+the CPU oracle on a bounded sample.
 
 Multi-GPU (torchrun): every rank runs an independent replica (the solves do
 not shard across GPUs); value = all ranks' solves / max elapsed.
@@ -58,10 +62,15 @@ def parse():
     ap.add_argument("--n", type=int, default=48)
     ap.add_argument("--p", type=int, default=3)
     ap.add_argument("--dim", type=int, default=3)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "fp32", "bf16", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-rhs", type=int, default=64, help="0 disables the batched section")
+    ap.add_argument("--batched-n", type=int, default=256)
+    ap.add_argument("--batched-steps", type=int, default=3)
+    ap.add_argument("--section", default="all", choices=["all", "batched"],
+                    help="batched: run only the batched section and print its object (profiling)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-n", type=int, default=8)
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
@@ -168,6 +177,90 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# batched right-hand sides on the tensor-core path
+# ---------------------------------------------------------------------------
+
+def run_batched(args, ldgmg, torch, np, dev, stream, barrier):
+    from paper_2412_12506_gb300.inputs import square_mu
+    d, n, p, R = 2, args.batched_n, 3, args.batched_rhs
+    op = ldgmg.Operator(d, n, p, square_mu(d, n, mu_in=1e4))
+    Hb = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp32", max_rhs=R)
+    H64 = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp64")
+    gen = torch.Generator(device=dev).manual_seed(4321)
+    B = op.project_kernel(torch.randn(R, op.size, dtype=torch.float64, device=dev, generator=gen))
+    X = torch.empty_like(B)
+    Hb.solve(B, args.tol, x=X)                                   # warm-up
+    torch.cuda.synchronize()
+    barrier()
+    lat, its = [], []
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.batched_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, it, rr, st = Hb.solve(B, args.tol, x=X)
+        e1.record(stream)
+        its.append(it)
+        lat.append((e0, e1))
+    g1.record(stream)
+    torch.cuda.synchronize()
+    ms = g0.elapsed_time(g1)
+    lat_ms = [a.elapsed_time(b) for a, b in lat]
+    # one-at-a-time FP64 GPU solves of the same right-hand sides (a sample of 8)
+    x64 = torch.empty(op.size, dtype=torch.float64, device=dev)
+    H64.solve(B[0].clone(), args.tol, x=x64)
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    it64 = []
+    for r in range(8):
+        _, k, _, _ = H64.solve(B[r].clone(), args.tol, x=x64)
+        it64.append(k)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = s0.elapsed_time(s1) / 8
+    xr = op.project_kernel(X[7].clone())
+    x64p = op.project_kernel(x64.clone())
+    err = float(torch.linalg.norm(xr - x64p) / torch.linalg.norm(x64p))
+    # dominant kernel: batched finest-level B apply on the tensor cores
+    inf = Hb.info(0)
+    b = op.b
+    xv = torch.randn(op.size * R, dtype=torch.float32, device=dev)
+    yv = torch.empty_like(xv)
+    for _ in range(3):
+        Hb.level_apply_batched(0, ldgmg.MAT_B, xv, R, yv)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    k0.record(stream)
+    for _ in range(reps):
+        Hb.level_apply_batched(0, ldgmg.MAT_B, xv, R, yv)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kms = k0.elapsed_time(k1) / reps
+    nnzb = inf["nnzb_S"]
+    flops = 2.0 * nnzb * b * b * R                      # useful multiply-adds of Y = B X
+    bytes_ = nnzb * b * b * 4 + 2 * op.size * R * 4     # FP32 blocks once, X and Y once
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tc_peak = peaks.get("bf16_tflops", 1900.0)
+    return {
+        "workload": f"interface2d_n{n}_p{p}_square1e4_sai1_{R}rhs", "rhs_per_call": R,
+        "solves_per_s": R * args.batched_steps / (ms / 1e3),
+        "latency_ms_per_call": {"p50": float(np.percentile(lat_ms, 50)), "p99": float(np.percentile(lat_ms, 99))},
+        "iterations": sorted(set(k for it in its for k in it)),
+        "vcycle": "FP32 blocks, tcgen05 3xBF16 (A and x split hi/lo), FP32 accumulate; FP64 flexible CG",
+        "fp64_single": {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "iterations": sorted(set(it64))},
+        "speedup_vs_fp64_single": (R * args.batched_steps / (ms / 1e3)) / (1e3 / ms64),
+        "rel_err_vs_fp64": err,
+        "roofline": {"bound": "hbm", "kernel": "bsr_tc_kernel<16, fp32 split> finest-level B apply, 64 RHS",
+                     "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": bytes_ / (kms / 1e3) / 1e9 / hbm, "ms_per_launch": kms,
+                     "tensor_TFLOPs": flops / (kms / 1e3) / 1e12, "tensor_peak_TFLOPs": tc_peak},
+    }
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -193,6 +286,16 @@ def main():
                                              "inputs": "larger than L2"},
             "cpu_baseline": cb,
             "e2e": {"value": s["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return
+
+    if args.section == "batched":
+        import numpy as np
+        import torch
+        torch.cuda.set_device(local_rank)
+        from paper_2412_12506_gb300 import ldgmg
+        dev = torch.device("cuda", local_rank)
+        out = run_batched(args, ldgmg, torch, np, dev, torch.cuda.current_stream(), lambda: None)
+        print(json.dumps(out))
         return
 
     # the CPU oracle sample runs first, in a separate process, before any GPU work
@@ -300,7 +403,7 @@ def main():
 
     # dominant kernel: block-row apply of the finest SAI matrix, in the V-cycle precision
     inf = H.info(0)
-    es = {"fp64": 8, "fp32": 4, "bf16": 2}[args.precision]
+    es = {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2}[args.precision]
     vs = 8 if args.precision == "fp64" else 4
     xv = torch.randn(size, device=dev, dtype=H.vdtype)
     yv = torch.empty_like(xv)
@@ -339,11 +442,14 @@ def main():
     spmv_ms = k0.elapsed_time(k1) / 10
     spmv_bytes = op.nnzb * b * b * 8 + 2 * size * 8
 
+    # every replica runs the batched section (it contains barriers)
+    batched = run_batched(args, ldgmg, torch, np, dev, stream, barrier) if args.batched_rhs > 0 else None
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    dtype = {"fp32": "f32 V-cycle + f64 CG", "bf16": "bf16-stored/f32 V-cycle + f64 CG", "fp64": "f64"}[args.precision]
+    dtype = {"fp16": "f16-stored/f32 V-cycle + f64 CG", "fp32": "f32 V-cycle + f64 CG",
+             "bf16": "bf16-stored/f32 V-cycle + f64 CG", "fp64": "f64"}[args.precision]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -356,7 +462,7 @@ def main():
         "fp64_path": fp64,
         "spmv_fp64": {"ms": spmv_ms, "GB_per_s": spmv_bytes / (spmv_ms / 1e3) / 1e9,
                       "frac_of_hbm": spmv_bytes / (spmv_ms / 1e3) / 1e9 / peak},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "roofline": roofline, "batched": batched, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "setup_s": setup_s,
     }
     print(json.dumps(line))

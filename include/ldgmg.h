@@ -54,6 +54,7 @@ enum { LDGMG_JACOBI = 0, LDGMG_SAI = 1 };                  /* smoother kind */
 enum { LDGMG_FORM_B1 = 0, LDGMG_FORM_BT = 1 };            /* SAI smoother form, Eqs. B1 / BT */
 enum { LDGMG_FP64 = 0, LDGMG_FP32 = 1, LDGMG_BF16 = 2, LDGMG_FP16 = 3 };   /* V-cycle precision */
 enum { LDGMG_MAT_A = 0, LDGMG_MAT_B = 1, LDGMG_MAT_BT = 2, LDGMG_MAT_D = 3 }; /* level matrices */
+enum { LDGMG_OUTER_AUTO = 0, LDGMG_OUTER_FP64 = 1, LDGMG_OUTER_DF = 2 };  /* batched outer apply */
 
 typedef struct {
   int dim;          /* 2 or 3 */
@@ -77,13 +78,18 @@ typedef struct {
                             hierarchy: b = 16 or 64, V-cycle block applies on tensor cores,
                             vcycle_precision LDGMG_BF16 (BF16 blocks) or LDGMG_FP32 (FP32
                             blocks split into two BF16 parts on the fly) */
+  int outer_apply;       /* operator apply of the batched outer CG: LDGMG_OUTER_FP64, or
+                            LDGMG_OUTER_DF = double-FP32 arithmetic (FP32 pairs, ~2^-44 of
+                            sum |a x|: ~100x FP64's rounding, on the fast FP32 pipes), or
+                            LDGMG_OUTER_AUTO = DF when max mu / min mu <= 10, else FP64 */
 } ldgmg_setup_opts;
 
 typedef struct ldgmg_op ldgmg_op;
 typedef struct ldgmg_hier ldgmg_hier;
 
 /* Fill *o with the paper's defaults: SAI, ell = 1, balanced, nu1 = nu2 = 3,
- * omega = 0.8, B1 pre / BT post, FP64, max_iter = 200, max_rhs = 1. */
+ * omega = 0.8, B1 pre / BT post, FP64, max_iter = 200, max_rhs = 1,
+ * outer_apply = LDGMG_OUTER_AUTO. */
 void ldgmg_default_opts(ldgmg_setup_opts* o);
 
 /* Assemble the LDG Laplacian A = sum_a G_a^T M_mu G_a + E of Sec. 2.1 (display

@@ -121,7 +121,9 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat
 struct ldgmg_op {
   HostLevel host;
   DevMat A;              // FP64 finest-level operator (column-major blocks)
+  void* A_pairs = nullptr;  // A's entries as (hi, lo) FP32 pairs, built for batched solves
   double tau0 = 1.0;
+  double mu_contrast = 1.0; // max mu / min mu
   double* partials = nullptr;
   double* scal = nullptr;
 };
@@ -145,6 +147,7 @@ struct ldgmg_hier {
   size_t vsz = 8;
   int Rmax = 1;          // right-hand sides per call
   bool batched = false;  // tensor-core hierarchy (row-major BF16 blocks)
+  bool use_df = false;   // batched outer apply in double-FP32 arithmetic
   std::vector<HostLevel> host;   // host[0] is unused (the op holds the finest level)
   std::vector<DevLevel> lv;
   double* P1d = nullptr;         // 2 * q * q injection matrices
@@ -210,11 +213,13 @@ void ldgmg_default_opts(ldgmg_setup_opts* o) {
   o->vcycle_precision = LDGMG_FP64;
   o->max_iter = 200;
   o->max_rhs = 1;
+  o->outer_apply = LDGMG_OUTER_AUTO;
 }
 
 void ldgmg_op_free(ldgmg_op* op) {
   if (!op) return;
   free_mat(op->A);
+  cudaFree(op->A_pairs);
   cudaFree(op->partials);
   cudaFree(op->scal);
   delete op;
@@ -239,6 +244,14 @@ ldgmg_status ldgmg_assemble(const ldgmg_mesh* mesh, int p, const double* mu_host
     return fail(LDGMG_EINVAL, err);
   }
   op->tau0 = tau0;
+  if (mu_host) {
+    double lo = mu_host[0], hi = mu_host[0];
+    for (int64_t e = 1; e < op->host.N; ++e) {
+      lo = std::min(lo, mu_host[e]);
+      hi = std::max(hi, mu_host[e]);
+    }
+    op->mu_contrast = hi / lo;
+  }
   ldgmg_status s = upload(op->host.A, b, P_FP64, 0, op->A, 0);
   if (s == LDGMG_OK) s = dalloc(&op->partials, kDotBlocks * sizeof(double));
   if (s == LDGMG_OK) s = dalloc(&op->scal, kCgSlots * sizeof(double));
@@ -408,6 +421,7 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   if (o->vcycle_precision < 0 || o->vcycle_precision > 3) return fail(LDGMG_EINVAL, "precision");
   if (o->max_iter < 1) return fail(LDGMG_EINVAL, "max_iter");
   if (o->max_rhs < 1 || o->max_rhs > 128) return fail(LDGMG_EINVAL, "max_rhs must be in 1..128");
+  if (o->outer_apply < 0 || o->outer_apply > 2) return fail(LDGMG_EINVAL, "outer_apply");
   if (o->smoother == LDGMG_JACOBI && !(o->omega > 0.0 && o->omega < 2.0)) return fail(LDGMG_EINVAL, "omega");
   const bool batched = o->max_rhs > 1;
   if (batched && o->vcycle_precision != LDGMG_BF16 && o->vcycle_precision != LDGMG_FP32)
@@ -489,6 +503,16 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   {
     ldgmg_status s = bottom_pinv(h, host_level(h, nl - 1), st);
     if (s != LDGMG_OK) return bail(s);
+  }
+  h->use_df = batched && (o->outer_apply == LDGMG_OUTER_DF ||
+                          (o->outer_apply == LDGMG_OUTER_AUTO && op->mu_contrast <= 10.0));
+  if (h->use_df && !op->A_pairs) {
+    // FP32-pair copy of the FP64 operator for the batched outer apply (df_apply.cu)
+    const int64_t cnt = op->A.nnzb * int64_t(op->A.b) * op->A.b;
+    ldgmg_status s = dalloc((char**)&op->A_pairs, size_t(cnt) * 8);
+    if (s != LDGMG_OK) return bail(s);
+    if (split_to_float_pairs(cnt, static_cast<const double*>(op->A.vals), op->A_pairs, st) != cudaSuccess)
+      return bail(fail(LDGMG_ECUDA, "split_to_float_pairs"));
   }
   const size_t n0 = size_t(L0.N) * L0.b * sizeof(double) * h->Rmax;
   for (double** v : {&h->r, &h->z, &h->p, &h->q, &h->bvec, &h->xvec, &h->stage_rhs, &h->stage_x}) {
@@ -687,8 +711,14 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     CKS(apply_V(h, h->r, h->z, R, st));
     CK(cudaMemcpyAsync(h->p, h->z, nb, cudaMemcpyDeviceToDevice, st));
     CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZ), st));
+    // Batched hierarchies apply A once per block row for all right-hand sides,
+    // in double-FP32 (use_df) or FP64.  The arithmetic of each right-hand side
+    // does not depend on R, so a right-hand side solved alone matches the batch.
+    const bool multi = h->batched && R <= 64;
     while (nact > 0 && k < h->o.max_iter) {
-      CK(bsr_apply_strided(h->op->A, M_Y, h->p, nullptr, nullptr, h->q, 1.0, R, R * bsz, bsz, st));
+      if (multi && h->use_df) CK(bsr_apply_df(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, R, st));
+      else if (multi) CK(bsr_apply_multi64(h->op->A, M_Y, h->p, nullptr, h->q, R, st));
+      else CK(bsr_apply_strided(h->op->A, M_Y, h->p, nullptr, nullptr, h->q, 1.0, R, R * bsz, bsz, st));
       CK(dot_batched(N, R, int(bsz), h->p, h->q, h->partials, slot(S_PQ), st));
       CK(cg_alpha_b(R, S, h->active, st));
       CK(cg_update_xr_b(N, R, int(bsz), xd, h->r, h->p, h->q, S, st));

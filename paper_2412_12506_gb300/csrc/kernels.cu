@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
   constexpr int TEAMS = 256 / TEAM;        // block rows per CTA
   constexpr int STEPS = (B + G - 1) / G;   // load steps per block
   static_assert(G >= 1, "team too small");
-  __shared__ TACC xs[TEAMS][B];
+  constexpr int KMAX = 16;                 // blocks whose x_j are staged at once
+  __shared__ TACC xs[TEAMS][KMAX][B];
   __shared__ TACC red[TEAMS][G][B];
 
   const int team = threadIdx.x / TEAM, lt = threadIdx.x % TEAM;
@@ -104,21 +105,28 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
 
   if (row < a.nrows) {
     const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
-    for (int nz = z0; nz < z1; ++nz) {
-      const int64_t j = a.col[nz];
+    // stage the neighbour vectors of up to KMAX blocks, then stream those
+    // blocks with no barrier in between (many loads in flight per thread)
+    for (int zb = z0; zb < z1; zb += KMAX) {
+      const int nb = min(KMAX, z1 - zb);
       team_sync<TEAM>();
-      for (int c = lt; c < B; c += TEAM) xs[team][c] = TACC(a.x[j * a.es + roff + c]);
+      for (int t = lt; t < nb * B; t += TEAM) {
+        const int kk = t / B, c = t % B;
+        xs[team][kk][c] = TACC(a.x[int64_t(a.col[zb + kk]) * a.es + roff + c]);
+      }
       team_sync<TEAM>();
       if (active) {
-        const TA* blk = a.vals + int64_t(nz) * (B * B) + rl * VEC;
+        for (int kk = 0; kk < nb; ++kk) {
+          const TA* blk = a.vals + int64_t(zb + kk) * (B * B) + rl * VEC;
 #pragma unroll 4
-        for (int st = 0; st < STEPS; ++st) {
-          const int c = st * G + g;
-          if (c < B) {
-            const VecT<TA, VEC> w = *reinterpret_cast<const VecT<TA, VEC>*>(blk + c * B);
-            const TACC xc = xs[team][c];
+          for (int st = 0; st < STEPS; ++st) {
+            const int c = st * G + g;
+            if (c < B) {
+              const VecT<TA, VEC> w = *reinterpret_cast<const VecT<TA, VEC>*>(blk + c * B);
+              const TACC xc = xs[team][kk][c];
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) acc[v] += cvt<TACC>(w.v[v]) * xc;
+              for (int v = 0; v < VEC; ++v) acc[v] += cvt<TACC>(w.v[v]) * xc;
+            }
           }
         }
       }
@@ -249,34 +257,13 @@ cudaError_t expand_blocks(int64_t nnzb, int b, const uint32_t* ids, const double
 // time, in shared memory.  One CTA per coarse element.
 // --------------------------------------------------------------------------
 
-template <bool TRANSPOSE>
-__device__ __forceinline__ double apply_child(const double (*Ps)[8][8], double* buf0, double* buf1,
-                                              int d, int q, int b, int sidx, int t) {
-  // buf0 holds the input (b values); returns this thread's output entry t.
-  double* in = buf0;
-  double* out = buf1;
-  int stride = 1;
-  for (int a = 0; a < d; ++a) {
-    const int s = (sidx >> a) & 1;
-    double v = 0.0;
-    if (t < b) {
-      const int ka = (t / stride) % q;
-      const int base = t - ka * stride;
-      for (int k = 0; k < q; ++k) {
-        const double pk = TRANSPOSE ? Ps[s][k][ka] : Ps[s][ka][k];
-        v += pk * in[base + k * stride];
-      }
-    }
-    __syncthreads();
-    if (t < b) out[t] = v;
-    __syncthreads();
-    double* tmp = in;
-    in = out;
-    out = tmp;
-    stride *= q;
-  }
-  return t < b ? in[t] : 0.0;
-}
+// One CTA per coarse element handles all R right-hand sides: the R*b entries
+// of an element are contiguous in the [element][rhs][mode] layout.  Each
+// thread owns outputs o = rr*b + t (right-hand side rr, mode t); the 1D
+// transforms along the d axes run in shared memory with a barrier per axis.
+// The arithmetic of every output is independent of R.
+constexpr int kXferThreads = 256;
+constexpr int kXferMaxOut = 16;        // outputs per thread: R*b <= 4096
 
 __device__ __forceinline__ void load_P(double (*Ps)[8][8], const double* P, int q) {
   for (int i = threadIdx.x; i < 2 * q * q; i += blockDim.x) {
@@ -285,51 +272,88 @@ __device__ __forceinline__ void load_P(double (*Ps)[8][8], const double* P, int 
   }
 }
 
-template <class TV>
-__global__ void restrict_kernel(int d, int q, int nf, const double* __restrict__ P,
-                                const TV* __restrict__ rf, TV* __restrict__ rc) {
-  __shared__ double buf[2][64];
-  __shared__ double Ps[2][8][8];
-  load_P(Ps, P, q);
-  const int b = (d == 2) ? q * q : q * q * q;
-  const int64_t nc = nf / 2;
-  const int64_t C = blockIdx.x;
-  const int R = gridDim.y, rr = blockIdx.y;
-  const int t = threadIdx.x;
-  int cc[3] = {int(C % nc), int((C / nc) % nc), int(C / (nc * nc))};
-  double acc = 0.0;
-  for (int s = 0; s < (1 << d); ++s) {
-    int64_t f = 0;
-    for (int a = d - 1; a >= 0; --a) f = f * nf + (2 * cc[a] + ((s >> a) & 1));
+// in -> out along all d axes for child offsets sidx; TRANSPOSE applies P_s^T.
+// Returns the buffer that holds the result.
+template <bool TRANSPOSE>
+__device__ __forceinline__ double* child_transform(const double (*Ps)[8][8], double* in, double* out, int d, int q,
+                                                   int b, int nout, int sidx) {
+  int stride = 1;
+  for (int a = 0; a < d; ++a) {
+    const int s = (sidx >> a) & 1;
+    for (int o = threadIdx.x; o < nout; o += kXferThreads) {
+      const int rr = o / b, t = o % b;
+      const int ka = (t / stride) % q;
+      const int base = rr * b + t - ka * stride;
+      double v = 0.0;
+      for (int k = 0; k < q; ++k) v += (TRANSPOSE ? Ps[s][k][ka] : Ps[s][ka][k]) * in[base + k * stride];
+      out[o] = v;
+    }
     __syncthreads();
-    if (t < b) buf[0][t] = double(rf[(f * R + rr) * b + t]);
-    __syncthreads();
-    acc += apply_child<true>(Ps, buf[0], buf[1], d, q, b, s, t);
+    double* tmp = in;
+    in = out;
+    out = tmp;
+    stride *= q;
   }
-  if (t < b) rc[(C * R + rr) * b + t] = TV(acc);
+  return in;
 }
 
 template <class TV>
-__global__ void prolong_kernel(int d, int q, int nf, const double* __restrict__ P,
-                               const TV* __restrict__ xc, TV* __restrict__ xf) {
-  __shared__ double buf[2][64];
+__global__ void __launch_bounds__(kXferThreads) restrict_kernel(int d, int q, int nf, const double* __restrict__ P,
+                                                                const TV* __restrict__ rf, TV* __restrict__ rc, int R) {
+  extern __shared__ double xbuf[];
   __shared__ double Ps[2][8][8];
   load_P(Ps, P, q);
   const int b = (d == 2) ? q * q : q * q * q;
+  const int nout = R * b;
+  double* buf0 = xbuf;
+  double* buf1 = xbuf + nout;
   const int64_t nc = nf / 2;
   const int64_t C = blockIdx.x;
-  const int R = gridDim.y, rr = blockIdx.y;
-  const int t = threadIdx.x;
   int cc[3] = {int(C % nc), int((C / nc) % nc), int(C / (nc * nc))};
-  const double xv = t < b ? double(xc[(C * R + rr) * b + t]) : 0.0;
+  double acc[kXferMaxOut];
+#pragma unroll
+  for (int k = 0; k < kXferMaxOut; ++k) acc[k] = 0.0;
   for (int s = 0; s < (1 << d); ++s) {
     int64_t f = 0;
     for (int a = d - 1; a >= 0; --a) f = f * nf + (2 * cc[a] + ((s >> a) & 1));
     __syncthreads();
-    if (t < b) buf[0][t] = xv;
+    for (int o = threadIdx.x; o < nout; o += kXferThreads) buf0[o] = double(rf[f * nout + o]);
     __syncthreads();
-    const double v = apply_child<false>(Ps, buf[0], buf[1], d, q, b, s, t);
-    if (t < b) xf[(f * R + rr) * b + t] = TV(double(xf[(f * R + rr) * b + t]) + v);
+    const double* res = child_transform<true>(Ps, buf0, buf1, d, q, b, nout, s);
+#pragma unroll
+    for (int k = 0; k < kXferMaxOut; ++k) {
+      const int o = threadIdx.x + k * kXferThreads;
+      if (o < nout) acc[k] += res[o];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kXferMaxOut; ++k) {
+    const int o = threadIdx.x + k * kXferThreads;
+    if (o < nout) rc[C * nout + o] = TV(acc[k]);
+  }
+}
+
+template <class TV>
+__global__ void __launch_bounds__(kXferThreads) prolong_kernel(int d, int q, int nf, const double* __restrict__ P,
+                                                               const TV* __restrict__ xc, TV* __restrict__ xf, int R) {
+  extern __shared__ double xbuf[];
+  __shared__ double Ps[2][8][8];
+  load_P(Ps, P, q);
+  const int b = (d == 2) ? q * q : q * q * q;
+  const int nout = R * b;
+  double* buf0 = xbuf;
+  double* buf1 = xbuf + nout;
+  const int64_t nc = nf / 2;
+  const int64_t C = blockIdx.x;
+  int cc[3] = {int(C % nc), int((C / nc) % nc), int(C / (nc * nc))};
+  for (int s = 0; s < (1 << d); ++s) {
+    int64_t f = 0;
+    for (int a = d - 1; a >= 0; --a) f = f * nf + (2 * cc[a] + ((s >> a) & 1));
+    __syncthreads();
+    for (int o = threadIdx.x; o < nout; o += kXferThreads) buf0[o] = double(xc[C * nout + o]);
+    __syncthreads();
+    const double* res = child_transform<false>(Ps, buf0, buf1, d, q, b, nout, s);
+    for (int o = threadIdx.x; o < nout; o += kXferThreads) xf[f * nout + o] = TV(double(xf[f * nout + o]) + res[o]);
   }
 }
 
@@ -339,21 +363,42 @@ static int64_t coarse_count(int d, int nf) {
   return r;
 }
 
+static cudaError_t xfer_config(int smem) {
+  static int configured = 0;
+  if (smem > 48 * 1024 && configured < smem) {
+    cudaError_t e = cudaFuncSetAttribute(restrict_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(restrict_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(prolong_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(prolong_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t restrict_apply(int d, int q, int n_fine, const double* P, const void* rf, void* rc,
                            int vprec, int R, cudaStream_t st) {
+  const int b = (d == 2) ? q * q : q * q * q;
+  if (R * b > kXferThreads * kXferMaxOut) return cudaErrorInvalidValue;
+  const int smem = 2 * R * b * int(sizeof(double));
+  cudaError_t e = xfer_config(smem);
+  if (e != cudaSuccess) return e;
   const int64_t Nc = coarse_count(d, n_fine);
-  const dim3 grid{unsigned(Nc), unsigned(R), 1u};
-  if (vprec == 0) restrict_kernel<double><<<grid, 64, 0, st>>>(d, q, n_fine, P, (const double*)rf, (double*)rc);
-  else restrict_kernel<float><<<grid, 64, 0, st>>>(d, q, n_fine, P, (const float*)rf, (float*)rc);
+  if (vprec == 0) restrict_kernel<double><<<unsigned(Nc), kXferThreads, smem, st>>>(d, q, n_fine, P, (const double*)rf, (double*)rc, R);
+  else restrict_kernel<float><<<unsigned(Nc), kXferThreads, smem, st>>>(d, q, n_fine, P, (const float*)rf, (float*)rc, R);
   return launched();
 }
 
 cudaError_t prolong_apply(int d, int q, int n_fine, const double* P, const void* xc, void* xf,
                           int vprec, int R, cudaStream_t st) {
+  const int b = (d == 2) ? q * q : q * q * q;
+  if (R * b > kXferThreads * kXferMaxOut) return cudaErrorInvalidValue;
+  const int smem = 2 * R * b * int(sizeof(double));
+  cudaError_t e = xfer_config(smem);
+  if (e != cudaSuccess) return e;
   const int64_t Nc = coarse_count(d, n_fine);
-  const dim3 grid{unsigned(Nc), unsigned(R), 1u};
-  if (vprec == 0) prolong_kernel<double><<<grid, 64, 0, st>>>(d, q, n_fine, P, (const double*)xc, (double*)xf);
-  else prolong_kernel<float><<<grid, 64, 0, st>>>(d, q, n_fine, P, (const float*)xc, (float*)xf);
+  if (vprec == 0) prolong_kernel<double><<<unsigned(Nc), kXferThreads, smem, st>>>(d, q, n_fine, P, (const double*)xc, (double*)xf, R);
+  else prolong_kernel<float><<<unsigned(Nc), kXferThreads, smem, st>>>(d, q, n_fine, P, (const float*)xc, (float*)xf, R);
   return launched();
 }
 

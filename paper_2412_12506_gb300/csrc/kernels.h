@@ -125,6 +125,18 @@ cudaError_t cg_update_xr_b(int64_t N, int R, int b, double* x, double* r, const 
 cudaError_t cg_beta_b(int R, double* scal, const int* active, int flexible, cudaStream_t st);
 cudaError_t cg_update_p_b(int64_t N, int R, int b, double* p, const double* z, const double* scal,
                           cudaStream_t st);
+// Double-FP32 operator apply (df_apply.cu): `pairs` holds A's FP64 entries as
+// (hi, lo) FP32 pairs in the layout of M (column-major blocks, b = 16 or 64);
+// x, rhs, y are FP64 [element][rhs][mode] with R <= 64 right-hand sides.
+// mode: M_Y or M_RES.  Accuracy ~2^-44 of sum |a x|.
+cudaError_t split_to_float_pairs(int64_t n, const double* src, void* dst, cudaStream_t st);
+cudaError_t bsr_apply_df(const DevMat& M, const void* pairs, int mode, const double* x, const double* rhs, double* y,
+                         int R, cudaStream_t st);
+
+// FP64 apply with the same block reuse over R <= 64 right-hand sides (b = 16, 64)
+cudaError_t bsr_apply_multi64(const DevMat& M, int mode, const double* x, const double* rhs, double* y, int R,
+                              cudaStream_t st);
+
 // launch-count bookkeeping for kernels defined in other translation units
 cudaError_t launched(int count = 1);
 

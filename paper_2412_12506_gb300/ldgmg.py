@@ -43,7 +43,8 @@ class SetupOpts(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("sai_level", ctypes.c_int), ("balance", ctypes.c_int),
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("pre_form", ctypes.c_int), ("post_form", ctypes.c_int),
-                ("vcycle_precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_rhs", ctypes.c_int)]
+                ("vcycle_precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_rhs", ctypes.c_int),
+                ("outer_apply", ctypes.c_int)]
 
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -104,8 +105,11 @@ def project_kernel_noalloc(v, N, b, stream=None):
     return v
 
 
+_OUTER = {"auto": 0, "fp64": 1, "df": 2}
+
+
 def make_opts(smoother="sai", sai_level=1, balance=True, nu1=3, nu2=3, omega=0.8, pre="B1", post="BT",
-              precision="fp64", max_iter=200, max_rhs=1) -> SetupOpts:
+              precision="fp64", max_iter=200, max_rhs=1, outer="auto") -> SetupOpts:
     o = SetupOpts()
     _lib.ldgmg_default_opts(ctypes.byref(o))
     o.smoother = _SMOOTHER[smoother]
@@ -116,6 +120,7 @@ def make_opts(smoother="sai", sai_level=1, balance=True, nu1=3, nu2=3, omega=0.8
     o.vcycle_precision = _PREC[precision]
     o.max_iter = max_iter
     o.max_rhs = max_rhs
+    o.outer_apply = _OUTER[outer]
     return o
 
 
