@@ -78,10 +78,13 @@ typedef struct {
                             hierarchy: b = 16 or 64, V-cycle block applies on tensor cores,
                             vcycle_precision LDGMG_BF16 (BF16 blocks) or LDGMG_FP32 (FP32
                             blocks split into two BF16 parts on the fly) */
-  int outer_apply;       /* operator apply of the batched outer CG: LDGMG_OUTER_FP64, or
+  int outer_apply;       /* operator apply of the outer CG of reduced-precision or batched
+                            hierarchies with b = 16 or 64: LDGMG_OUTER_FP64, or
                             LDGMG_OUTER_DF = double-FP32 arithmetic (FP32 pairs, ~2^-44 of
                             sum |a x|: ~100x FP64's rounding, on the fast FP32 pipes), or
-                            LDGMG_OUTER_AUTO = DF when max mu / min mu <= 10, else FP64 */
+                            LDGMG_OUTER_AUTO = DF when max mu / min mu <= 10, else FP64.
+                            FP64 hierarchies always use FP64.  The final residual that
+                            ldgmg_solve reports is always computed in FP64. */
 } ldgmg_setup_opts;
 
 typedef struct ldgmg_op ldgmg_op;

@@ -504,8 +504,11 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
     ldgmg_status s = bottom_pinv(h, host_level(h, nl - 1), st);
     if (s != LDGMG_OK) return bail(s);
   }
-  h->use_df = batched && (o->outer_apply == LDGMG_OUTER_DF ||
-                          (o->outer_apply == LDGMG_OUTER_AUTO && op->mu_contrast <= 10.0));
+  // double-FP32 outer apply: batched hierarchies (b = 16 / 64), and the single
+  // right-hand-side mixed-precision path for b = 16 / 64; the plain FP64
+  // hierarchy always keeps the FP64 apply
+  h->use_df = (batched || h->prec != P_FP64) && tc_block_size_supported(op->host.b) &&
+              (o->outer_apply == LDGMG_OUTER_DF || (o->outer_apply == LDGMG_OUTER_AUTO && op->mu_contrast <= 10.0));
   if (h->use_df && !op->A_pairs) {
     // FP32-pair copy of the FP64 operator for the batched outer apply (df_apply.cu)
     const int64_t cnt = op->A.nnzb * int64_t(op->A.b) * op->A.b;
@@ -718,6 +721,7 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     while (nact > 0 && k < h->o.max_iter) {
       if (multi && h->use_df) CK(bsr_apply_df(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, R, st));
       else if (multi) CK(bsr_apply_multi64(h->op->A, M_Y, h->p, nullptr, h->q, R, st));
+      else if (h->use_df && R == 1) CK(bsr_apply_df1(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, st));
       else CK(bsr_apply_strided(h->op->A, M_Y, h->p, nullptr, nullptr, h->q, 1.0, R, R * bsz, bsz, st));
       CK(dot_batched(N, R, int(bsz), h->p, h->q, h->partials, slot(S_PQ), st));
       CK(cg_alpha_b(R, S, h->active, st));

@@ -143,6 +143,83 @@ __global__ void __launch_bounds__(256, 2) bsr_multi64_kernel(int64_t nrows, cons
   }
 }
 
+// Single right-hand side: the team layout of the CUDA-core block-row kernel
+// (a warp per row for b = 16, the CTA for b = 64; column groups of threads
+// read 16-byte runs = 2 pairs of one column), with the same double-FP32
+// arithmetic and a fixed-order TwoSum reduction of the group partials.
+template <int B>
+__global__ void __launch_bounds__(256) bsr_df1_kernel(int64_t nrows, const int* __restrict__ row_ptr,
+                                                      const int* __restrict__ col, const float2* __restrict__ vals,
+                                                      const double* __restrict__ x, const double* __restrict__ rhs,
+                                                      double* __restrict__ y, int mode) {
+  constexpr int VEC = 2;                    // pairs per 16-byte load
+  constexpr int TEAM = (B > 32) ? 256 : 32;
+  constexpr int LPC = B / VEC;
+  constexpr int G = TEAM / LPC;
+  constexpr int TEAMS = 256 / TEAM;
+  constexpr int STEPS = B / G;
+  constexpr int KMAX = 16;
+  __shared__ float2 xs[TEAMS][KMAX][B];
+  __shared__ float red_hi[TEAMS][G][B], red_lo[TEAMS][G][B];
+  const int team = threadIdx.x / TEAM, lt = threadIdx.x % TEAM;
+  const int g = lt / LPC, rl = lt % LPC;
+  const int64_t row = int64_t(blockIdx.x) * TEAMS + team;
+  if (TEAM == 32 && row >= nrows) return;
+  float hi[VEC] = {0.0f, 0.0f}, lo[VEC] = {0.0f, 0.0f};
+  if (row < nrows) {
+    const int z0 = row_ptr[row], z1 = row_ptr[row + 1];
+    for (int zb = z0; zb < z1; zb += KMAX) {
+      const int nb = min(KMAX, z1 - zb);
+      if (TEAM == 32) __syncwarp(); else __syncthreads();
+      for (int t = lt; t < nb * B; t += TEAM) {
+        const int kk = t / B, c = t % B;
+        const double v = x[int64_t(col[zb + kk]) * B + c];
+        const float h = float(v);
+        xs[team][kk][c] = make_float2(h, float(v - double(h)));
+      }
+      if (TEAM == 32) __syncwarp(); else __syncthreads();
+      for (int kk = 0; kk < nb; ++kk) {
+        const float4* blk = reinterpret_cast<const float4*>(vals + int64_t(zb + kk) * (B * B) + rl * VEC);
+#pragma unroll 4
+        for (int st = 0; st < STEPS; ++st) {
+          const int c = st * G + g;
+          const float4 w = blk[c * (B / 2)];          // pairs (r, c), (r+1, c): a_hi, a_lo, a_hi', a_lo'
+          const float2 xv = xs[team][kk][c];
+          const float a[2][2] = {{w.x, w.y}, {w.z, w.w}};
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            const float p = a[v][0] * xv.x;
+            const float pe = fmaf(a[v][0], xv.x, -p);
+            const float cross = fmaf(a[v][0], xv.y, a[v][1] * xv.x);
+            float t, te;
+            two_sum(hi[v], p, t, te);
+            hi[v] = t;
+            lo[v] += te + pe + cross;
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < VEC; ++v) {
+    red_hi[team][g][rl * VEC + v] = hi[v];
+    red_lo[team][g][rl * VEC + v] = lo[v];
+  }
+  if (TEAM == 32) __syncwarp(); else __syncthreads();
+  if (row < nrows && lt < B) {
+    float S = 0.0f, E = 0.0f;
+    for (int gg = 0; gg < G; ++gg) {
+      float t, te;
+      two_sum(S, red_hi[team][gg][lt], t, te);
+      S = t;
+      E += te + red_lo[team][gg][lt];
+    }
+    const double acc = double(S) + double(E);
+    const int64_t o = row * B + lt;
+    y[o] = (mode == M_RES) ? rhs[o] - acc : acc;
+  }
+}
+
 __global__ void split_kernel(int64_t n, const double* __restrict__ src, float2* __restrict__ dst) {
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
     const double v = src[t];
@@ -183,6 +260,22 @@ cudaError_t bsr_apply_df(const DevMat& M, const void* pairs, int mode, const dou
     LDGMG_DF_CASE(16)
     LDGMG_DF_CASE(64)
 #undef LDGMG_DF_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t bsr_apply_df1(const DevMat& M, const void* pairs, int mode, const double* x, const double* rhs,
+                          double* y, cudaStream_t st) {
+  if (M.nrows == 0) return cudaSuccess;
+  if (mode != M_Y && mode != M_RES) return cudaErrorInvalidValue;
+  const float2* v = static_cast<const float2*>(pairs);
+  switch (M.b) {
+    case 16:
+      bsr_df1_kernel<16><<<unsigned((M.nrows + 7) / 8), 256, 0, st>>>(M.nrows, M.row_ptr, M.col, v, x, rhs, y, mode);
+      return launched();
+    case 64:
+      bsr_df1_kernel<64><<<unsigned(M.nrows), 256, 0, st>>>(M.nrows, M.row_ptr, M.col, v, x, rhs, y, mode);
+      return launched();
     default: return cudaErrorInvalidValue;
   }
 }

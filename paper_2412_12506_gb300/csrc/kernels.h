@@ -133,6 +133,9 @@ cudaError_t split_to_float_pairs(int64_t n, const double* src, void* dst, cudaSt
 cudaError_t bsr_apply_df(const DevMat& M, const void* pairs, int mode, const double* x, const double* rhs, double* y,
                          int R, cudaStream_t st);
 
+// single right-hand side version of the double-FP32 apply (b = 16, 64)
+cudaError_t bsr_apply_df1(const DevMat& M, const void* pairs, int mode, const double* x, const double* rhs,
+                          double* y, cudaStream_t st);
 // FP64 apply with the same block reuse over R <= 64 right-hand sides (b = 16, 64)
 cudaError_t bsr_apply_multi64(const DevMat& M, int mode, const double* x, const double* rhs, double* y, int R,
                               cudaStream_t st);

@@ -116,39 +116,75 @@ __device__ __forceinline__ uint32_t core_off(int row, int kq, int KQ) {
   return uint32_t(((row >> 3) * KQ + kq) * 128 + (row & 7) * 16);
 }
 
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 1D bulk copy global -> shared, completion counted on `bar` (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// bounded wait on an mbarrier phase; returns false if it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity))
+    if (++spins > kSpinLimit) return false;
+  return true;
+}
+
+__host__ __device__ __forceinline__ uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
+
+// Shared-memory plan of one CTA for b = B, R right-hand sides.
 template <int B, bool SPLIT>
-struct TcSmem {
+struct TcPlan {
   static constexpr int KQ = B / 8;
-  static constexpr int A_BYTES = kTcM * B * 2;   // one BF16 operand part (hi or lo)
-  static constexpr int B_BYTES = B * B * 2;
-  static constexpr int TOTAL = 2 * A_BYTES + (SPLIT ? 2 : 1) * B_BYTES + 128;
+  static constexpr uint32_t A_BYTES = kTcM * B * 2;             // one BF16 part of X^T
+  static constexpr uint32_t B_BYTES = B * B * 2;                // one BF16 part of A_ij
+  static constexpr uint32_t OP_BYTES = 2 * A_BYTES + (SPLIT ? 2 : 1) * B_BYTES;
+  static constexpr uint32_t RAWA_BYTES = B * B * (SPLIT ? 4 : 2);
+  __host__ __device__ static uint32_t rawx_bytes(int R) { return round128(uint32_t(R) * B * 4); }
+  __host__ __device__ static uint32_t total(int R) {
+    return 2 * OP_BYTES + 2 * RAWA_BYTES + 2 * rawx_bytes(R) + 128;
+  }
 };
 
+// Software pipeline over the flattened sequence of (block row, block) items of
+// this CTA: thread 0 keeps the raw X_j slab and matrix block of the next two
+// items in flight with bulk copies (raw buffers 0/1), all threads convert the
+// current item into BF16 core-matrix operands (operand buffers 0/1) while the
+// tensor cores still work on the previous item, and thread 0 issues the MMAs.
 template <int B, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   static_assert(B == 16 || B == 64, "tensor-core path supports b = 16 and b = 64");
-  constexpr int KQ = B / 8;
+  typedef TcPlan<B, SPLIT> P;
+  constexpr int KQ = P::KQ;
   constexpr int KSTEPS = B / 16;
   constexpr uint32_t NCOLS = B < 32 ? 32 : B;
   constexpr uint32_t IDESC = make_idesc(kTcM, B);
+  constexpr uint32_t SBO = KQ * 128;
   extern __shared__ __align__(1024) unsigned char smem[];
-  typedef TcSmem<B, SPLIT> L;
-  unsigned char* a_hi = smem;
-  unsigned char* a_lo = smem + L::A_BYTES;
-  unsigned char* b_op = smem + 2 * L::A_BYTES;
-  unsigned char* b_lo = b_op + L::B_BYTES;       // used only when SPLIT
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::TOTAL - 128);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int R = a.R;
-  // zero the A-operand rows of absent right-hand sides once (staging never writes them)
+  const uint32_t rawx_bytes = P::rawx_bytes(R);
+  // operand buffer bf at smem + bf*OP_BYTES; raw buffers after them
+  auto op = [&](int bf) { return smem + bf * P::OP_BYTES; };
+  auto rawa = [&](int bf) { return smem + 2 * P::OP_BYTES + bf * P::RAWA_BYTES; };
+  auto rawx = [&](int bf) { return smem + 2 * P::OP_BYTES + 2 * P::RAWA_BYTES + bf * rawx_bytes; };
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P::total(R) - 128);   // full[0..1], mma[2..3]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // rows of absent right-hand sides stay zero in both operand buffers
   for (int t = tid; t < kTcM * KQ; t += kTcThreads) {
     const int m = t / KQ, kq = t % KQ;
-    if (m >= R) {
-      *reinterpret_cast<uint4*>(a_hi + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
-      *reinterpret_cast<uint4*>(a_lo + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
-    }
+    if (m >= R)
+      for (int bf = 0; bf < 2; ++bf) {
+        *reinterpret_cast<uint4*>(op(bf) + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(op(bf) + P::A_BYTES + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
+      }
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -157,96 +193,121 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int i = 0; i < 4; ++i) mbar_init(bars + i, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo), sb = smem_u32(b_op), sb_lo = smem_u32(b_lo);
-  constexpr uint32_t SBO = KQ * 128;
-  uint32_t phase = 0;
+
+  // lookahead iterator over items (only thread 0 advances it)
+  int64_t la_row = blockIdx.x;
+  int la_nz = 0, la_z1 = 0;
+  if (la_row < a.nrows) { la_nz = a.row_ptr[la_row]; la_z1 = a.row_ptr[la_row + 1]; }
+  auto la_skip_empty = [&]() {
+    while (la_row < a.nrows && la_nz >= la_z1) {
+      la_row += gridDim.x;
+      if (la_row < a.nrows) { la_nz = a.row_ptr[la_row]; la_z1 = a.row_ptr[la_row + 1]; }
+    }
+  };
+  const uint32_t item_bytes = uint32_t(R) * B * 4 + P::RAWA_BYTES;
+  auto issue = [&](int bf) {     // thread 0: copies of the lookahead item into raw buffer bf
+    la_skip_empty();
+    if (la_row >= a.nrows) return false;
+    const int64_t j = a.col[la_nz];
+    mbar_arrive_expect_tx(bars + bf, item_bytes);
+    bulk_g2s(rawx(bf), a.x + j * a.es, uint32_t(R) * B * 4, bars + bf);
+    bulk_g2s(rawa(bf), static_cast<const unsigned char*>(a.vals) + int64_t(la_nz) * P::RAWA_BYTES, P::RAWA_BYTES,
+             bars + bf);
+    ++la_nz;
+    return true;
+  };
+  int issued = 0;                // items whose copies were issued (thread 0's count)
+  if (tid == 0) {
+    if (issue(0)) ++issued;
+    if (issue(1)) ++issued;
+  }
+
+  // per buffer: bit bf of fph / mph = phase parity to wait for; bit bf of pend = MMA outstanding
+  uint32_t fph = 0, mph = 0, pend = 0;
+  int consumed = 0;              // items converted so far
   bool timed_out = false;
 
   for (int64_t row = blockIdx.x; row < a.nrows && !timed_out; row += gridDim.x) {
     const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
     for (int nz = z0; nz < z1; ++nz) {
-      const int64_t j = a.col[nz];
-      // stage A_ij (row-major): chunk (r, kq) = 8 consecutive columns of row r
+      const int bf = consumed & 1;
+      bool ok = mbar_wait_bounded(bars + bf, (fph >> bf) & 1u);                        // raw data of this item
+      if (ok && ((pend >> bf) & 1u)) ok = mbar_wait_bounded(bars + 2 + bf, (mph >> bf) & 1u);   // operands free
+      if (__syncthreads_or(!ok)) { timed_out = true; break; }
+      fph ^= 1u << bf;
+      if ((pend >> bf) & 1u) { mph ^= 1u << bf; pend &= ~(1u << bf); }
+      // convert: X_j^T -> hi/lo BF16 (A operand), A_ij -> BF16 (hi [, lo]) (B operand)
+      unsigned char* o = op(bf);
+      const float* xr = reinterpret_cast<const float*>(rawx(bf));
+      // one float4 (4 modes of one right-hand side) per thread: consecutive
+      // 16-byte reads, 8-byte stores that tile the core matrices without conflicts
+      for (int t = tid; t < R * (B / 4); t += kTcThreads) {
+        const int m = t / (B / 4), q4 = t % (B / 4);
+        const float4 v = *reinterpret_cast<const float4*>(xr + m * B + q4 * 4);
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+        const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+        const uint32_t off = core_off(m, q4 >> 1, KQ) + (q4 & 1) * 8;
+        *reinterpret_cast<uint2*>(o + off) =
+            make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+        *reinterpret_cast<uint2*>(o + P::A_BYTES + off) =
+            make_uint2(pack_bf16(v.x - f0.x, v.y - f0.y), pack_bf16(v.z - f1.x, v.w - f1.y));
+      }
+      unsigned char* bo = o + 2 * P::A_BYTES;
       if (!SPLIT) {
-        const uint4* blk = reinterpret_cast<const uint4*>(a.vals) + int64_t(nz) * (B * B / 8);
+        const uint4* ra = reinterpret_cast<const uint4*>(rawa(bf));
         for (int t = tid; t < B * KQ; t += kTcThreads) {
           const int r = t / KQ, kq = t % KQ;
-          *reinterpret_cast<uint4*>(b_op + core_off(r, kq, KQ)) = __ldg(blk + t);
+          *reinterpret_cast<uint4*>(bo + core_off(r, kq, KQ)) = ra[t];
         }
       } else {
-        const float4* blk = reinterpret_cast<const float4*>(a.vals) + int64_t(nz) * (B * B / 4);
-        for (int t = tid; t < B * KQ; t += kTcThreads) {
-          const int r = t / KQ, kq = t % KQ;
-          const float4 v0 = __ldg(blk + 2 * t), v1 = __ldg(blk + 2 * t + 1);
-          const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-          uint32_t hi[4], lo[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-            const float2 hf = __bfloat1622float2(h);
-            hi[e] = *reinterpret_cast<const uint32_t*>(&h);
-            lo[e] = pack_bf16(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
-          }
-          *reinterpret_cast<uint4*>(b_op + core_off(r, kq, KQ)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(b_lo + core_off(r, kq, KQ)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        const float4* ra = reinterpret_cast<const float4*>(rawa(bf));
+        for (int t = tid; t < B * (B / 4); t += kTcThreads) {
+          const int r = t / (B / 4), q4 = t % (B / 4);
+          const float4 v = ra[t];
+          const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+          const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+          const uint32_t off = core_off(r, q4 >> 1, KQ) + (q4 & 1) * 8;
+          *reinterpret_cast<uint2*>(bo + off) =
+              make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+          *reinterpret_cast<uint2*>(bo + P::B_BYTES + off) =
+              make_uint2(pack_bf16(v.x - f0.x, v.y - f0.y), pack_bf16(v.z - f1.x, v.w - f1.y));
         }
       }
-      // stage X_j^T as hi/lo BF16: chunk (m, kq) = modes 8kq..8kq+7 of right-hand side m
-      const float* xj = a.x + j * a.es;
-      for (int t = tid; t < R * KQ; t += kTcThreads) {
-        const int m = t / KQ, kq = t % KQ;
-        const float4* src = reinterpret_cast<const float4*>(xj + int64_t(m) * a.rs + kq * 8);
-        const float4 v0 = __ldg(src), v1 = __ldg(src + 1);
-        const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
-        uint32_t hi[4], lo[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
-          const float2 hf = __bfloat1622float2(h);
-          hi[e] = *reinterpret_cast<const uint32_t*>(&h);
-          lo[e] = pack_bf16(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
-        }
-        *reinterpret_cast<uint4*>(a_hi + core_off(m, kq, KQ)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(a_lo + core_off(m, kq, KQ)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-      }
-      fence_proxy_async();
+      fence_proxy_async();     // operands visible to the tensor cores; raw reads ordered before new copies
       __syncthreads();
       if (tid == 0) {
+        if (issue(bf)) ++issued;                         // raw buffer bf is free again
         tc_fence_after();
+        const uint32_t sa = smem_u32(o), sbh = smem_u32(bo);
 #pragma unroll
         for (int s = 0; s < KSTEPS; ++s) {
-          const uint64_t bd = make_sdesc(sb + 256u * s, 128u, SBO);
-          const uint64_t ah = make_sdesc(sa_hi + 256u * s, 128u, SBO);
+          const uint64_t ah = make_sdesc(sa + 256u * s, 128u, SBO);
+          const uint64_t bd = make_sdesc(sbh + 256u * s, 128u, SBO);
           mma_bf16(tmem, ah, bd, IDESC, (nz > z0 || s > 0) ? 1u : 0u);
-          mma_bf16(tmem, make_sdesc(sa_lo + 256u * s, 128u, SBO), bd, IDESC, 1u);
-          if (SPLIT) mma_bf16(tmem, ah, make_sdesc(sb_lo + 256u * s, 128u, SBO), IDESC, 1u);
+          mma_bf16(tmem, make_sdesc(sa + P::A_BYTES + 256u * s, 128u, SBO), bd, IDESC, 1u);
+          if (SPLIT) mma_bf16(tmem, ah, make_sdesc(sbh + P::B_BYTES + 256u * s, 128u, SBO), IDESC, 1u);
         }
-        mma_commit(bar);
+        mma_commit(bars + 2 + bf);
       }
-      // wait for the MMAs (they read the staged operands) before restaging;
-      // the give-up decision is made together so no thread is left at a barrier
-      bool gave_up = false;
-      unsigned spins = 0;
-      while (!mbar_try_wait(bar, phase)) {
-        if (++spins > kSpinLimit) {
-          gave_up = true;
-          break;
-        }
-      }
-      if (__syncthreads_or(gave_up)) {
-        timed_out = true;
-        break;
-      }
-      phase ^= 1u;
+      pend |= 1u << bf;
+      ++consumed;
     }
     if (timed_out) break;
+    // the row's products are complete once both operand buffers' MMAs are
+    bool ok = true;
+    if (ok && (pend & 1u)) ok = mbar_wait_bounded(bars + 2, mph & 1u);
+    if (ok && (pend & 2u)) ok = mbar_wait_bounded(bars + 3, (mph >> 1) & 1u);
+    if (__syncthreads_or(!ok)) { timed_out = true; break; }
+    mph ^= pend;
+    pend = 0;
     tc_fence_after();
     // epilogue: warp w holds right-hand sides 32w..32w+31, one per lane
     const int m = warp * 32 + lane;
@@ -263,13 +324,13 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
           float* yy = reinterpret_cast<float*>(&y);
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const float s = empty ? 0.0f : acc[q + e];
+            const float sv = empty ? 0.0f : acc[q + e];
             float out;
             switch (a.mode) {
-              case M_Y: out = s; break;
-              case M_RES: out = a.rhs[o + q + e] - s; break;
-              case M_AXPY: out = a.xin[o + q + e] + float(a.s) * s; break;
-              default: out = float(a.s) * s; break;
+              case M_Y: out = sv; break;
+              case M_RES: out = a.rhs[o + q + e] - sv; break;
+              case M_AXPY: out = a.xin[o + q + e] + float(a.s) * sv; break;
+              default: out = float(a.s) * sv; break;
             }
             yy[e] = out;
           }
@@ -282,12 +343,17 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   }
   if (timed_out) {
     if (tid == 0 && a.err) atomicExch(a.err, 1);
-    // give the outstanding MMAs a second bounded chance to finish before TMEM is released
-    unsigned spins = 0;
-    while (!mbar_try_wait(bar, phase) && ++spins < kSpinLimit) {
+    // bounded drain of this CTA's own copies and MMAs before TMEM and shared memory go away
+    if (tid == 0) {
+      for (int k = consumed; k < issued; ++k) {
+        const int bf = k & 1;
+        mbar_wait_bounded(bars + bf, (fph >> bf) & 1u);
+        fph ^= 1u << bf;
+      }
+      if (pend & 1u) mbar_wait_bounded(bars + 2, mph & 1u);
+      if (pend & 2u) mbar_wait_bounded(bars + 3, (mph >> 1) & 1u);
     }
   }
-  // every thread is past its last MMA wait (or gave up); release TMEM
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -301,16 +367,27 @@ bool tc_block_size_supported(int b) { return b == 16 || b == 64; }
 
 template <int B, bool SPLIT>
 static cudaError_t launch_tc(const BatchArgs& a, cudaStream_t st) {
-  const int smem = TcSmem<B, SPLIT>::TOTAL;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(bsr_tc_kernel<B, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  typedef TcPlan<B, SPLIT> P;
+  const int smem = int(P::total(a.R));
+  static int configured = 0;
+  static int per_sm[129] = {};     // CTAs per SM by R (occupancy), 0 = not computed
+  if (configured < smem) {
+    cudaError_t e = cudaFuncSetAttribute(bsr_tc_kernel<B, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(P::total(kTcM)));
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured = int(P::total(kTcM));
   }
-  // at most 8 CTAs per SM (TMEM: 8 x 64 columns = 512), persistent over rows
-  const int64_t grid = std::min<int64_t>(a.nrows, 152 * 8);
+  if (!per_sm[a.R]) {
+    // resident CTAs per SM from the kernel's own needs: shared memory (227 KB
+    // per SM, ~1 KB reserved per CTA), TMEM (512 columns), threads (2048)
+    const int by_smem = (227 * 1024) / (smem + 1024);
+    const int by_tmem = 512 / (B < 32 ? 32 : B);
+    const int by_threads = 2048 / kTcThreads;
+    per_sm[a.R] = std::max(1, std::min(by_smem, std::min(by_tmem, by_threads)));
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int64_t grid = std::min<int64_t>(a.nrows, int64_t(std::max(sms, 1)) * per_sm[a.R]);
   if (grid <= 0) return cudaSuccess;
   bsr_tc_kernel<B, SPLIT><<<unsigned(grid), kTcThreads, smem, st>>>(a);
   return launched();
