@@ -181,17 +181,24 @@ class SAI:
     matrices with the block pattern of A^ell (Sec. 2.3.3)."""
 
     def __init__(self, A: BOp, ell: int = 1, balance: bool = True, pre: str = "B1",
-                 post: str = "BT"):
+                 post: str = "BT", alpha=None):
+        """alpha: optional per-dof balancing vector (Sec. 3.3, Stokes); by default
+        alpha_i = ||A_ii||_F^{-1/2} on every dof of element i (Sec. 2.3.3)."""
         self.A, self.ell = A, ell
         self.pre, self.post = pre, post
         b, N = A.b, A.nblocks
         self.b, self.N = b, N
-        if balance:
-            alpha_el = np.array([np.linalg.norm(A.block(i, i), "fro") ** -0.5 for i in range(N)])
+        if alpha is not None:
+            self.alpha = np.asarray(alpha, dtype=np.float64)
+            self.alpha_el = None
         else:
-            alpha_el = np.ones(N)
-        self.alpha_el = alpha_el
-        self.alpha = np.repeat(alpha_el, b)
+            if balance:
+                alpha_el = np.array([np.linalg.norm(A.block(i, i), "fro") ** -0.5 for i in range(N)])
+            else:
+                alpha_el = np.ones(N)
+            self.alpha_el = alpha_el
+            self.alpha = np.repeat(alpha_el, b)
+        self._alpha_blk = self.alpha.reshape(N, b)
         Da = sp.diags(self.alpha)
         self._At = (Da @ A.mat @ Da).tocsc()
         self._Pc = pattern_power(A.pat, ell).tocsc()
@@ -214,8 +221,8 @@ class SAI:
         X = ls_solve(Mloc, rhs)
         out = {}
         for t, k in enumerate(S):
-            # B_ki = alpha_k Btilde_ki alpha_i (alpha is constant per element)
-            out[(int(k), i)] = self.alpha_el[k] * X[t * b:(t + 1) * b, :] * self.alpha_el[i]
+            # B = diag(alpha) Btilde diag(alpha)
+            out[(int(k), i)] = self._alpha_blk[k][:, None] * X[t * b:(t + 1) * b, :] * self._alpha_blk[i][None, :]
         return out
 
     def sweep(self, x: np.ndarray, rhs: np.ndarray, form: str) -> np.ndarray:
