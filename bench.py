@@ -40,16 +40,19 @@ if ROOT not in sys.path:
 METRIC = "1e-10 solves/s (mixed-precision V-cycle + FP64 CG)"
 
 # DRAM bytes (read + write) per block row of the finest-level B apply, from one
-# ncu capture on the 16^3 case (profiles/bsr_kernel_fp32_poisson3d_n16_p3.md),
-# scaled by rows to the launch timed here; valid only for the kernel source it
-# was taken on (sha256 prefix of kernels.cu), else reported as null.
-TRAFFIC_PER_ROW = {"fp32": (476.5e6 / 4096, "3cb9903e9aba4e64")}
+# ncu capture on the 16^3 case (profiles/bsr_kernel_fp16_poisson3d_n16_p3.md,
+# mean of 3 launches), scaled by rows to the launch timed here; valid only for
+# the kernel source it was taken on (sha256 prefix of bsr_apply.cu), else
+# reported as null.
+TRAFFIC_PER_ROW = {"fp16": (241.08e6 / 4096, "014095b3432c0255")}
 
 
 def kernel_source_hash():
     import hashlib
-    with open(os.path.join(ROOT, "paper_2412_12506_gb300", "csrc", "kernels.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_2412_12506_gb300", "csrc", "bsr_apply.cu"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
 UNIT = "solves/s"
 
 
@@ -126,6 +129,45 @@ def cpu_baseline_obj(s, args):
                        f"on a {s['n']}^{args.dim} mesh (p={args.p}), {s['solves']} solves, median "
                        f"{s['solve_s']:.3f} s/solve, iterations {sorted(set(s['iters']))}; scaled by the element "
                        f"ratio {s['scale']:.0f} to {args.n}^{args.dim} (iteration counts are mesh independent)")}
+
+
+# ---------------------------------------------------------------------------
+# replicas: one independent solver per GPU (the solves do not shard)
+# ---------------------------------------------------------------------------
+
+class Replicas:
+    """Process-group bookkeeping for independent replicas: barriers and the
+    max-over-ranks elapsed time.  There is no data-path collective."""
+
+    def __init__(self, backend="nccl"):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend, init_method="env://")
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, value, device):
+        import torch
+        t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+        if self.dist is not None:
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def throughput(self, local_ms, units_per_rank, device):
+        """(max elapsed ms over ranks, all ranks' units per second)."""
+        ms = self.max(local_ms, device)
+        return ms, self.world * units_per_rank / (ms / 1e3)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
 
 
 # ---------------------------------------------------------------------------
@@ -305,11 +347,8 @@ def main():
 
     import numpy as np
     import torch
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local_rank)
+    reps = Replicas("nccl")
     dev = torch.device("cuda", local_rank)
     from paper_2412_12506_gb300 import ldgmg
 
@@ -331,9 +370,7 @@ def main():
     xs = torch.empty(size, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = reps.barrier
 
     def timed(hier, count, warm, rhs_list, x_out):
         iters = []
@@ -368,11 +405,7 @@ def main():
     x_mixed = xs.clone()
 
     # max over ranks
-    t_all = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
-    total_ms = float(t_all.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms, value = reps.throughput(total_ms, args.steps, dev)
 
     # plain FP64 GPU solver beside it
     fp64 = None
@@ -407,16 +440,16 @@ def main():
     vs = 8 if args.precision == "fp64" else 4
     xv = torch.randn(size, device=dev, dtype=H.vdtype)
     yv = torch.empty_like(xv)
-    reps = 20
+    nrep = 20
     for _ in range(3):
         H.level_apply(0, ldgmg.MAT_B, xv, yv)
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0.record(stream)
-    for _ in range(reps):
+    for _ in range(nrep):
         H.level_apply(0, ldgmg.MAT_B, xv, yv)
     k1.record(stream)
     torch.cuda.synchronize()
-    kern_ms = k0.elapsed_time(k1) / reps
+    kern_ms = k0.elapsed_time(k1) / nrep
     alg_bytes = inf["nnzb_S"] * b * b * es + 2 * size * vs   # matrix once, x and y once
     traffic = None
     if args.precision in TRAFFIC_PER_ROW and kernel_source_hash() == TRAFFIC_PER_ROW[args.precision][1]:
@@ -445,8 +478,7 @@ def main():
     # every replica runs the batched section (it contains barriers)
     batched = run_batched(args, ldgmg, torch, np, dev, stream, barrier) if args.batched_rhs > 0 else None
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
+        reps.close()
         return
     dtype = {"fp16": "f16-stored/f32 V-cycle + f64 CG", "fp32": "f32 V-cycle + f64 CG",
              "bf16": "bf16-stored/f32 V-cycle + f64 CG", "fp64": "f64"}[args.precision]
@@ -466,8 +498,7 @@ def main():
         "gpu_launches": launches, "setup_s": setup_s,
     }
     print(json.dumps(line))
-    if dist is not None:
-        dist.destroy_process_group()
+    reps.close()
 
 
 if __name__ == "__main__":

@@ -1,16 +1,6 @@
-// Device kernels of the LDG multigrid hot path, written for sm_103a (GB300).
-//
-// Block-row apply (Sec. 2.3: sum_j A_ij x_j over the element-block pattern;
-// the same kernel applies A, B, B^T and the Jacobi inverse blocks): the
-// matrix is streamed exactly once from HBM.  A "team" of threads owns one
-// block row (a warp for b <= 32, the whole 256-thread CTA for b > 32).  Each
-// team splits the block's columns into G groups; inside a group, LPC threads
-// cover the b rows of one column with 16-byte vector loads, so every load
-// step of the team reads G consecutive columns = one contiguous run of the
-// column-major block.  The neighbour vector x_j is staged in shared memory
-// and broadcast.  Partial sums of the G groups are reduced in shared memory
-// in a fixed order (results are deterministic), then a fused epilogue writes
-// y = acc, rhs - acc (residual), xin + s*acc (smoother update) or s*acc.
+// Device kernels of the LDG multigrid hot path other than the operator
+// applies: pool expansion, restriction/prolongation, bottom solve, FP64
+// vector and CG kernels, batched layouts.  Written for sm_103a (GB300).
 #include "kernels.h"
 
 #include <cuda_bf16.h>
@@ -33,189 +23,11 @@ cudaError_t launched(int count) {
   return cudaGetLastError();
 }
 
-__device__ __forceinline__ float to_f(bf16 v) { return __bfloat162float(v); }
 template <class T> __device__ __forceinline__ T from_d(double v);
 template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
 template <> __device__ __forceinline__ float from_d<float>(double v) { return float(v); }
 template <> __device__ __forceinline__ bf16 from_d<bf16>(double v) { return __double2bfloat16(v); }
 template <> __device__ __forceinline__ f16 from_d<f16>(double v) { return __double2half(v); }
-
-template <class TACC, class TA> __device__ __forceinline__ TACC cvt(TA v) { return TACC(v); }
-template <> __device__ __forceinline__ float cvt<float, bf16>(bf16 v) { return __bfloat162float(v); }
-template <> __device__ __forceinline__ double cvt<double, bf16>(bf16 v) {
-  return double(__bfloat162float(v));
-}
-template <> __device__ __forceinline__ float cvt<float, f16>(f16 v) { return __half2float(v); }
-
-template <class T, int N> struct alignas(sizeof(T) * N) VecT { T v[N]; };
-
-// largest power-of-two element count <= 16 bytes that divides B
-template <class TA> constexpr int vec_for(int B) {
-  int v = 16 / int(sizeof(TA));
-  while (v > 1 && (B % v) != 0) v /= 2;
-  return v;
-}
-
-template <class TA> struct AccOf { typedef float type; };
-template <> struct AccOf<double> { typedef double type; };
-
-template <class TA, class TV> struct BsrArgs {
-  int64_t nrows;
-  const int* __restrict__ row_ptr;
-  const int* __restrict__ col;
-  const TA* __restrict__ vals;
-  const TV* __restrict__ x;
-  const TV* rhs;
-  const TV* xin;
-  TV* y;
-  double s;
-  int mode;
-  int64_t es, rs;   // vector entry (element e, rhs r, mode c) at e*es + r*rs + c; rhs = blockIdx.y
-  int R;            // right-hand sides (grid y dimension)
-  double inv_scale; // 1 / storage scale of the matrix (exact power of two)
-};
-
-template <int TEAM> __device__ __forceinline__ void team_sync() {
-  if (TEAM == 32) __syncwarp(); else __syncthreads();
-}
-
-template <int B, class TA, class TV>
-__global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
-  typedef typename AccOf<TA>::type TACC;
-  constexpr int VEC = vec_for<TA>(B);
-  constexpr int TEAM = (B > 32) ? 256 : 32;
-  constexpr int LPC = B / VEC;             // threads per column
-  constexpr int G = TEAM / LPC;            // column groups per team
-  constexpr int TEAMS = 256 / TEAM;        // block rows per CTA
-  constexpr int STEPS = (B + G - 1) / G;   // load steps per block
-  static_assert(G >= 1, "team too small");
-  constexpr int KMAX = 16;                 // blocks whose x_j are staged at once
-  __shared__ TACC xs[TEAMS][KMAX][B];
-  __shared__ TACC red[TEAMS][G][B];
-
-  const int team = threadIdx.x / TEAM, lt = threadIdx.x % TEAM;
-  const int g = lt / LPC, rl = lt % LPC;
-  const bool active = g < G;
-  const int64_t row = int64_t(blockIdx.x) * TEAMS + team;
-  const int64_t roff = int64_t(blockIdx.y) * a.rs;
-  if (TEAM == 32 && row >= a.nrows) return;   // whole warp leaves together
-  TACC acc[VEC];
-#pragma unroll
-  for (int v = 0; v < VEC; ++v) acc[v] = TACC(0);
-
-  if (row < a.nrows) {
-    const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
-    // stage the neighbour vectors of up to KMAX blocks, then stream those
-    // blocks with no barrier in between (many loads in flight per thread)
-    for (int zb = z0; zb < z1; zb += KMAX) {
-      const int nb = min(KMAX, z1 - zb);
-      team_sync<TEAM>();
-      for (int t = lt; t < nb * B; t += TEAM) {
-        const int kk = t / B, c = t % B;
-        xs[team][kk][c] = TACC(a.x[int64_t(a.col[zb + kk]) * a.es + roff + c]);
-      }
-      team_sync<TEAM>();
-      if (active) {
-        for (int kk = 0; kk < nb; ++kk) {
-          const TA* blk = a.vals + int64_t(zb + kk) * (B * B) + rl * VEC;
-#pragma unroll 4
-          for (int st = 0; st < STEPS; ++st) {
-            const int c = st * G + g;
-            if (c < B) {
-              const VecT<TA, VEC> w = *reinterpret_cast<const VecT<TA, VEC>*>(blk + c * B);
-              const TACC xc = xs[team][kk][c];
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) acc[v] += cvt<TACC>(w.v[v]) * xc;
-            }
-          }
-        }
-      }
-    }
-  }
-  if (active) {
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) red[team][g][rl * VEC + v] = acc[v];
-  }
-  team_sync<TEAM>();
-  if (row < a.nrows && lt < B) {
-    TACC sum = TACC(0);
-#pragma unroll
-    for (int gg = 0; gg < G; ++gg) sum += red[team][gg][lt];
-    sum *= TACC(a.inv_scale);
-    const int64_t o = row * a.es + roff + lt;
-    switch (a.mode) {
-      case M_Y: a.y[o] = TV(sum); break;
-      case M_RES: a.y[o] = TV(TACC(a.rhs[o]) - sum); break;
-      case M_AXPY: a.y[o] = TV(TACC(a.xin[o]) + TACC(a.s) * sum); break;
-      default: a.y[o] = TV(TACC(a.s) * sum); break;
-    }
-  }
-}
-
-bool block_size_supported(int b) {
-  switch (b) {
-    case 4: case 8: case 9: case 16: case 25: case 27: case 36: case 64: return true;
-    default: return false;
-  }
-}
-
-template <int B, class TA, class TV>
-static cudaError_t launch_bsr_b(const DevMat& M, const BsrArgs<TA, TV>& a, cudaStream_t st) {
-  constexpr int TEAMS = (B > 32) ? 1 : 8;
-  if (M.nrows == 0) return cudaSuccess;
-  const int64_t grid = (M.nrows + TEAMS - 1) / TEAMS;
-  bsr_kernel<B, TA, TV><<<dim3(unsigned(grid), unsigned(a.R)), 256, 0, st>>>(a);
-  return launched();
-}
-
-template <class TA, class TV>
-static cudaError_t launch_bsr_t(const DevMat& M, int mode, const void* x, const void* rhs,
-                                const void* xin, void* y, double s, int R, int64_t es, int64_t rs,
-                                cudaStream_t st) {
-  BsrArgs<TA, TV> a;
-  a.nrows = M.nrows;
-  a.row_ptr = M.row_ptr;
-  a.col = M.col;
-  a.vals = static_cast<const TA*>(M.vals);
-  a.x = static_cast<const TV*>(x);
-  a.rhs = static_cast<const TV*>(rhs);
-  a.xin = static_cast<const TV*>(xin);
-  a.y = static_cast<TV*>(y);
-  a.s = s;
-  a.mode = mode;
-  a.es = es;
-  a.rs = rs;
-  a.R = R;
-  a.inv_scale = 1.0 / M.scale;
-  switch (M.b) {
-    case 4: return launch_bsr_b<4>(M, a, st);
-    case 8: return launch_bsr_b<8>(M, a, st);
-    case 9: return launch_bsr_b<9>(M, a, st);
-    case 16: return launch_bsr_b<16>(M, a, st);
-    case 25: return launch_bsr_b<25>(M, a, st);
-    case 27: return launch_bsr_b<27>(M, a, st);
-    case 36: return launch_bsr_b<36>(M, a, st);
-    case 64: return launch_bsr_b<64>(M, a, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t bsr_apply_strided(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
-                              void* y, double s, int R, int64_t es, int64_t rs, cudaStream_t st) {
-  if (M.row_major || R < 1) return cudaErrorInvalidValue;
-  switch (M.prec) {
-    case P_FP64: return launch_bsr_t<double, double>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
-    case P_FP32: return launch_bsr_t<float, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
-    case P_BF16: return launch_bsr_t<bf16, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
-    case P_FP16: return launch_bsr_t<f16, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
-                      void* y, double s, cudaStream_t st) {
-  return bsr_apply_strided(M, mode, x, rhs, xin, y, s, 1, M.b, 0, st);
-}
 
 // --------------------------------------------------------------------------
 // pool expansion (setup): vals[nz] = transpose(pool[ids[nz]]) in precision T
@@ -258,102 +70,93 @@ cudaError_t expand_blocks(int64_t nnzb, int b, const uint32_t* ids, const double
 // --------------------------------------------------------------------------
 
 // One CTA per coarse element handles all R right-hand sides: the R*b entries
-// of an element are contiguous in the [element][rhs][mode] layout.  Each
-// thread owns outputs o = rr*b + t (right-hand side rr, mode t); the 1D
-// transforms along the d axes run in shared memory with a barrier per axis.
-// The arithmetic of every output is independent of R.
-constexpr int kXferThreads = 256;
-constexpr int kXferMaxOut = 16;        // outputs per thread: R*b <= 4096
+// of an element are contiguous in the [element][rhs][mode] layout.  The
+// right-hand sides are taken in chunks of Rc; within a chunk the 2^d children
+// are transformed together, so a chunk costs d + 2 barriers whatever d and R.
+// Work item i = (child s, rhs rr, mode t) with i = (s*Rc + rr)*b + t.  The 1D
+// transform along axis a uses the child's own factor P[s_a]; the arithmetic
+// of every output (the order of the k-sums and of the sum over children) is
+// independent of R and of Rc.  The arithmetic runs in the vector precision:
+// FP64 for FP64 vectors, FP32 for the reduced-precision V-cycle (GB300's FP64
+// pipe would otherwise bound these kernels well below HBM speed).
+constexpr int kXferCap = 2048;          // work items per chunk (2 buffers of TV)
+constexpr int kXferMaxThreads = 256;
 
-__device__ __forceinline__ void load_P(double (*Ps)[8][8], const double* P, int q) {
+template <class TV>
+__device__ __forceinline__ void load_P(TV (*Ps)[8][8], const double* P, int q) {
   for (int i = threadIdx.x; i < 2 * q * q; i += blockDim.x) {
     const int s = i / (q * q), r = (i / q) % q, c = i % q;
-    Ps[s][r][c] = P[i];
+    Ps[s][r][c] = TV(P[i]);
   }
 }
 
-// in -> out along all d axes for child offsets sidx; TRANSPOSE applies P_s^T.
-// Returns the buffer that holds the result.
-template <bool TRANSPOSE>
-__device__ __forceinline__ double* child_transform(const double (*Ps)[8][8], double* in, double* out, int d, int q,
-                                                   int b, int nout, int sidx) {
-  int stride = 1;
-  for (int a = 0; a < d; ++a) {
-    const int s = (sidx >> a) & 1;
-    for (int o = threadIdx.x; o < nout; o += kXferThreads) {
-      const int rr = o / b, t = o % b;
-      const int ka = (t / stride) % q;
-      const int base = rr * b + t - ka * stride;
-      double v = 0.0;
-      for (int k = 0; k < q; ++k) v += (TRANSPOSE ? Ps[s][k][ka] : Ps[s][ka][k]) * in[base + k * stride];
-      out[o] = v;
-    }
-    __syncthreads();
-    double* tmp = in;
-    in = out;
-    out = tmp;
-    stride *= q;
-  }
-  return in;
+static int xfer_chunk(int d, int b, int R) {
+  const int per = (1 << d) * b;
+  return std::max(1, std::min(R, kXferCap / per));
 }
 
-template <class TV>
-__global__ void __launch_bounds__(kXferThreads) restrict_kernel(int d, int q, int nf, const double* __restrict__ P,
-                                                                const TV* __restrict__ rf, TV* __restrict__ rc, int R) {
-  extern __shared__ double xbuf[];
-  __shared__ double Ps[2][8][8];
+template <bool RESTRICT, class TV>
+__global__ void __launch_bounds__(kXferMaxThreads) xfer_kernel(int d, int q, int nf, const double* __restrict__ P,
+                                                               const TV* __restrict__ src, TV* __restrict__ dst,
+                                                               int R, int Rc) {
+  extern __shared__ __align__(16) unsigned char xraw[];
+  TV* xbuf = reinterpret_cast<TV*>(xraw);
+  __shared__ TV Ps[2][8][8];
   load_P(Ps, P, q);
   const int b = (d == 2) ? q * q : q * q * q;
-  const int nout = R * b;
-  double* buf0 = xbuf;
-  double* buf1 = xbuf + nout;
+  const int nch = 1 << d;
   const int64_t nc = nf / 2;
   const int64_t C = blockIdx.x;
-  int cc[3] = {int(C % nc), int((C / nc) % nc), int(C / (nc * nc))};
-  double acc[kXferMaxOut];
-#pragma unroll
-  for (int k = 0; k < kXferMaxOut; ++k) acc[k] = 0.0;
-  for (int s = 0; s < (1 << d); ++s) {
-    int64_t f = 0;
-    for (int a = d - 1; a >= 0; --a) f = f * nf + (2 * cc[a] + ((s >> a) & 1));
-    __syncthreads();
-    for (int o = threadIdx.x; o < nout; o += kXferThreads) buf0[o] = double(rf[f * nout + o]);
-    __syncthreads();
-    const double* res = child_transform<true>(Ps, buf0, buf1, d, q, b, nout, s);
-#pragma unroll
-    for (int k = 0; k < kXferMaxOut; ++k) {
-      const int o = threadIdx.x + k * kXferThreads;
-      if (o < nout) acc[k] += res[o];
+  // fine element of child s: fbase + (s_0) + (s_1) nf + (s_2) nf^2
+  const int64_t c0 = C % nc, c1 = (C / nc) % nc, c2 = C / (nc * nc);
+  const int64_t nf2 = int64_t(nf) * nf;
+  const int64_t fbase = 2 * c0 + 2 * c1 * nf + (d == 3 ? 2 * c2 * nf2 : 0);
+  auto fidx = [&](int s) -> int64_t { return fbase + (s & 1) + ((s >> 1) & 1) * nf + ((s >> 2) & 1) * nf2; };
+  const int64_t row = int64_t(R) * b;            // entries per element
+  TV* buf0 = xbuf;
+  TV* buf1 = xbuf + nch * Rc * b;
+  for (int r0 = 0; r0 < R; r0 += Rc) {
+    const int seg = min(Rc, R - r0) * b;          // entries per child in this chunk
+    const int tot = nch * seg;
+    __syncthreads();                               // previous chunk done with the buffers
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+      const int s = i / seg, o = i - s * seg;
+      buf0[i] = RESTRICT ? src[fidx(s) * row + int64_t(r0) * b + o] : src[C * row + int64_t(r0) * b + o];
     }
-  }
-#pragma unroll
-  for (int k = 0; k < kXferMaxOut; ++k) {
-    const int o = threadIdx.x + k * kXferThreads;
-    if (o < nout) rc[C * nout + o] = TV(acc[k]);
-  }
-}
-
-template <class TV>
-__global__ void __launch_bounds__(kXferThreads) prolong_kernel(int d, int q, int nf, const double* __restrict__ P,
-                                                               const TV* __restrict__ xc, TV* __restrict__ xf, int R) {
-  extern __shared__ double xbuf[];
-  __shared__ double Ps[2][8][8];
-  load_P(Ps, P, q);
-  const int b = (d == 2) ? q * q : q * q * q;
-  const int nout = R * b;
-  double* buf0 = xbuf;
-  double* buf1 = xbuf + nout;
-  const int64_t nc = nf / 2;
-  const int64_t C = blockIdx.x;
-  int cc[3] = {int(C % nc), int((C / nc) % nc), int(C / (nc * nc))};
-  for (int s = 0; s < (1 << d); ++s) {
-    int64_t f = 0;
-    for (int a = d - 1; a >= 0; --a) f = f * nf + (2 * cc[a] + ((s >> a) & 1));
     __syncthreads();
-    for (int o = threadIdx.x; o < nout; o += kXferThreads) buf0[o] = double(xc[C * nout + o]);
-    __syncthreads();
-    const double* res = child_transform<false>(Ps, buf0, buf1, d, q, b, nout, s);
-    for (int o = threadIdx.x; o < nout; o += kXferThreads) xf[f * nout + o] = TV(double(xf[f * nout + o]) + res[o]);
+    TV* in = buf0;
+    TV* out = buf1;
+    int stride = 1;
+    for (int a = 0; a < d; ++a) {
+      for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+        const int s = i / seg, o = i - s * seg;
+        const int t = o % b;
+        const int ka = (t / stride) % q;
+        const int base = i - ka * stride;
+        const int sa = (s >> a) & 1;
+        TV v = TV(0);
+        for (int k = 0; k < q; ++k) v += (RESTRICT ? Ps[sa][k][ka] : Ps[sa][ka][k]) * in[base + k * stride];
+        out[i] = v;
+      }
+      __syncthreads();
+      TV* tmp = in;
+      in = out;
+      out = tmp;
+      stride *= q;
+    }
+    if (RESTRICT) {
+      for (int o = threadIdx.x; o < seg; o += blockDim.x) {
+        TV acc = TV(0);
+        for (int s = 0; s < nch; ++s) acc += in[s * seg + o];
+        dst[C * row + int64_t(r0) * b + o] = acc;
+      }
+    } else {
+      for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+        const int s = i / seg, o = i - s * seg;
+        TV* y = dst + fidx(s) * row + int64_t(r0) * b + o;
+        *y = *y + in[i];
+      }
+    }
   }
 }
 
@@ -366,40 +169,43 @@ static int64_t coarse_count(int d, int nf) {
 static cudaError_t xfer_config(int smem) {
   static int configured = 0;
   if (smem > 48 * 1024 && configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(restrict_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(restrict_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(prolong_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(prolong_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(xfer_kernel<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(xfer_kernel<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(xfer_kernel<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(xfer_kernel<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
   return cudaSuccess;
 }
 
-cudaError_t restrict_apply(int d, int q, int n_fine, const double* P, const void* rf, void* rc,
-                           int vprec, int R, cudaStream_t st) {
+template <bool RESTRICT>
+static cudaError_t xfer_apply(int d, int q, int n_fine, const double* P, const void* src, void* dst,
+                              int vprec, int R, cudaStream_t st) {
+  if (q < 1 || q > 8 || (d != 2 && d != 3) || R < 1 || n_fine < 2) return cudaErrorInvalidValue;
   const int b = (d == 2) ? q * q : q * q * q;
-  if (R * b > kXferThreads * kXferMaxOut) return cudaErrorInvalidValue;
-  const int smem = 2 * R * b * int(sizeof(double));
+  const int Rc = xfer_chunk(d, b, R);
+  const int tot = (1 << d) * Rc * b;
+  const int smem = 2 * tot * (vprec == 0 ? 8 : 4);
   cudaError_t e = xfer_config(smem);
   if (e != cudaSuccess) return e;
+  const int threads = std::min(kXferMaxThreads, (tot + 31) / 32 * 32);
   const int64_t Nc = coarse_count(d, n_fine);
-  if (vprec == 0) restrict_kernel<double><<<unsigned(Nc), kXferThreads, smem, st>>>(d, q, n_fine, P, (const double*)rf, (double*)rc, R);
-  else restrict_kernel<float><<<unsigned(Nc), kXferThreads, smem, st>>>(d, q, n_fine, P, (const float*)rf, (float*)rc, R);
+  if (vprec == 0)
+    xfer_kernel<RESTRICT, double><<<unsigned(Nc), threads, smem, st>>>(d, q, n_fine, P, (const double*)src, (double*)dst, R, Rc);
+  else
+    xfer_kernel<RESTRICT, float><<<unsigned(Nc), threads, smem, st>>>(d, q, n_fine, P, (const float*)src, (float*)dst, R, Rc);
   return launched();
+}
+
+cudaError_t restrict_apply(int d, int q, int n_fine, const double* P, const void* rf, void* rc,
+                           int vprec, int R, cudaStream_t st) {
+  return xfer_apply<true>(d, q, n_fine, P, rf, rc, vprec, R, st);
 }
 
 cudaError_t prolong_apply(int d, int q, int n_fine, const double* P, const void* xc, void* xf,
                           int vprec, int R, cudaStream_t st) {
-  const int b = (d == 2) ? q * q : q * q * q;
-  if (R * b > kXferThreads * kXferMaxOut) return cudaErrorInvalidValue;
-  const int smem = 2 * R * b * int(sizeof(double));
-  cudaError_t e = xfer_config(smem);
-  if (e != cudaSuccess) return e;
-  const int64_t Nc = coarse_count(d, n_fine);
-  if (vprec == 0) prolong_kernel<double><<<unsigned(Nc), kXferThreads, smem, st>>>(d, q, n_fine, P, (const double*)xc, (double*)xf, R);
-  else prolong_kernel<float><<<unsigned(Nc), kXferThreads, smem, st>>>(d, q, n_fine, P, (const float*)xc, (float*)xf, R);
-  return launched();
+  return xfer_apply<false>(d, q, n_fine, P, xc, xf, vprec, R, st);
 }
 
 // --------------------------------------------------------------------------
@@ -490,6 +296,45 @@ cudaError_t dot(int64_t n, const double* a, const double* b, double* partials, d
   dot_partial<<<kDotBlocks, 256, 0, st>>>(n, 1, a, b, partials);
   sum_final<<<1, 1024, 0, st>>>(kDotBlocks, partials, out);
   return launched(2);
+}
+
+// GMRES vector steps (FP64): y += sgn * coef[0] * x with the coefficient read on
+// the device (a Hessenberg entry), y = x / s, and x += sum_i y_i Q_i.
+__global__ void axpy_dev_kernel(int64_t n, const double* __restrict__ coef, double sgn, const double* __restrict__ x,
+                                double* __restrict__ y) {
+  const double a = sgn * coef[0];
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x)
+    y[t] += a * x[t];
+}
+
+__global__ void div_kernel(int64_t n, double s, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x)
+    y[t] = x[t] / s;
+}
+
+__global__ void combine_kernel(int64_t n, int k, const double* __restrict__ Q, int64_t ldq,
+                               const double* __restrict__ y, double* __restrict__ x) {
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += y[i] * Q[int64_t(i) * ldq + t];
+    x[t] += acc;
+  }
+}
+
+cudaError_t axpy_dev(int64_t n, const double* coef, double sgn, const double* x, double* y, cudaStream_t st) {
+  axpy_dev_kernel<<<grid_for(n), 256, 0, st>>>(n, coef, sgn, x, y);
+  return launched();
+}
+
+cudaError_t vec_div(int64_t n, double s, const double* x, double* y, cudaStream_t st) {
+  div_kernel<<<grid_for(n), 256, 0, st>>>(n, s, x, y);
+  return launched();
+}
+
+cudaError_t vec_combine(int64_t n, int k, const double* Q, int64_t ldq, const double* y, double* x,
+                        cudaStream_t st) {
+  combine_kernel<<<grid_for(n), 256, 0, st>>>(n, k, Q, ldq, y, x);
+  return launched();
 }
 
 cudaError_t strided_sum(int64_t count, int64_t stride, const double* v, double* partials,
