@@ -72,8 +72,13 @@ def parse():
     ap.add_argument("--batched-rhs", type=int, default=64, help="0 disables the batched section")
     ap.add_argument("--batched-n", type=int, default=256)
     ap.add_argument("--batched-steps", type=int, default=3)
-    ap.add_argument("--section", default="all", choices=["all", "batched"],
-                    help="batched: run only the batched section and print its object (profiling)")
+    ap.add_argument("--stokes-n", type=int, default=128, help="0 disables the Stokes section")
+    ap.add_argument("--stokes-steps", type=int, default=3)
+    ap.add_argument("--serve-requests", type=int, default=10000, help="0 disables the serving section")
+    ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-fp64-sample", type=int, default=200)
+    ap.add_argument("--section", default="all", choices=["all", "batched", "stokes", "serve"],
+                    help="batched / stokes / serve: run only that section and print its object (profiling)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-n", type=int, default=8)
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
@@ -303,6 +308,199 @@ def run_batched(args, ldgmg, torch, np, dev, stream, barrier):
 
 
 # ---------------------------------------------------------------------------
+# two-phase Stokes with GMRES (Sec. 3.4.3)
+# ---------------------------------------------------------------------------
+
+def run_stokes(args, ldgmg, torch, np, dev, stream, barrier):
+    from paper_2412_12506_gb300.inputs import STOKES2D_128_P2 as W
+    from paper_2412_12506_gb300.inputs import fourier_force_rhs, square_mu
+    d, n, p, gamma = W.dim, args.stokes_n, W.p, W.extra["gamma"]
+    t0 = time.time()
+    op = ldgmg.Operator(d, n, p, square_mu(d, n, mu_in=W.mu_in), stokes=gamma)
+    H32 = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp32")
+    H64 = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp64")
+    setup_s = time.time() - t0
+    rhs = torch.tensor(fourier_force_rhs(d, n, p, W.extra["force_seed"], W.extra["force_modes"]),
+                       dtype=torch.float64, device=dev)
+    op.project_kernel(rhs)
+
+    def timed(H, steps):
+        x = torch.empty_like(rhs)
+        H.solve(rhs, args.tol, x=x)                      # warm-up
+        torch.cuda.synchronize()
+        barrier()
+        ev, its = [], []
+        l0 = ldgmg.kernel_launches()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, k, rr, _ = H.solve(rhs, args.tol, x=x)
+            e1.record(stream)
+            ev.append((e0, e1))
+            its.append((k, rr))
+        g1.record(stream)
+        torch.cuda.synchronize()
+        lat = [a.elapsed_time(b) for a, b in ev]
+        return g0.elapsed_time(g1), lat, its, x, ldgmg.kernel_launches() - l0
+
+    ms32, lat32, it32, x32, l32 = timed(H32, args.stokes_steps)
+    ms64, lat64, it64, x64, _ = timed(H64, max(1, args.stokes_steps // 2))
+    xa = op.project_kernel(x32.clone())
+    xb = op.project_kernel(x64.clone())
+    err = float(torch.linalg.norm(xa - xb) / torch.linalg.norm(xb))
+    # dominant kernels: the FP32 finest-level B apply (V-cycle) and the FP64 A apply (GMRES)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    b = op.b
+
+    def kernel_ms(fn):
+        for _ in range(3):
+            fn()
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(20):
+            fn()
+        k1.record(stream)
+        torch.cuda.synchronize()
+        return k0.elapsed_time(k1) / 20
+
+    xv = torch.randn(op.size, dtype=torch.float32, device=dev)
+    yv = torch.empty_like(xv)
+    kB = kernel_ms(lambda: H32.level_apply(0, ldgmg.MAT_B, xv, yv))
+    bytesB = H32.info(0)["nnzb_S"] * b * b * 4 + 2 * op.size * 4
+    xd = torch.randn(op.size, dtype=torch.float64, device=dev)
+    yd = torch.empty_like(xd)
+    kA = kernel_ms(lambda: op.apply(xd, yd))
+    bytesA = op.nnzb * b * b * 8 + 2 * op.size * 8
+    return {
+        "workload": f"stokes2d_n{n}_p{p}_{'stress' if gamma else 'standard'}_square{W.mu_in:g}_sai1_gmres",
+        "dofs": op.size, "setup_s": setup_s,
+        "solves_per_s": args.stokes_steps / (ms32 / 1e3),
+        "latency_ms": {"p50": float(np.percentile(lat32, 50)), "p99": float(np.percentile(lat32, 99))},
+        "iterations": sorted(set(k for k, _ in it32)), "final_relres": max(r for _, r in it32),
+        "gpu_launches_per_solve": l32 / args.stokes_steps,
+        "krylov": "flexible GMRES(50) in FP64, FP32 V-cycle (balanced SAI1, zeta = 0.131)",
+        "fp64": {"solves_per_s": len(lat64) / (ms64 / 1e3), "p50_ms": float(np.median(lat64)),
+                 "iterations": sorted(set(k for k, _ in it64)), "krylov": "left-preconditioned GMRES(50), FP64 V-cycle"},
+        "speedup_vs_fp64": (args.stokes_steps / (ms32 / 1e3)) / (len(lat64) / (ms64 / 1e3)),
+        "rel_err_vs_fp64": err,
+        "roofline": {"bound": "hbm", "kernel": "bsr_kernel<27, float> finest-level B apply",
+                     "achieved": bytesB / (kB / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                     "frac": bytesB / (kB / 1e3) / 1e9 / hbm, "ms_per_launch": kB, "bytes_per_launch": bytesB},
+        "fp64_apply": {"kernel": "bsr_kernel<27, double> operator apply", "GB_per_s": bytesA / (kA / 1e3) / 1e9,
+                       "frac_of_hbm": bytesA / (kA / 1e3) / 1e9 / hbm, "ms": kA},
+    }
+
+
+# ---------------------------------------------------------------------------
+# serving: a Poisson stream of mixed solve requests (continuous batching)
+# ---------------------------------------------------------------------------
+
+def run_serve(args, ldgmg, torch, np, dev, stream, barrier):
+    import threading
+
+    from paper_2412_12506_gb300.inputs import serving_requests, square_mu, zero_mean_rhs
+    reqs = serving_requests(args.serve_requests, seed=2024)
+    classes = sorted({(q["dim"], q["n"], q["p"], q["contrast"]) for q in reqs})
+    mus = {c: (None if c[3] == 1.0 else square_mu(c[0], c[1], mu_in=c[3])) for c in classes}
+    pool = {}                                   # 3 right-hand sides per class, reused
+
+    def rhs_of(q):
+        c = (q["dim"], q["n"], q["p"], q["contrast"])
+        key = (c, q["rhs_seed"] % 3)
+        if key not in pool:
+            pool[key] = zero_mean_rhs(q["n"] ** q["dim"], (q["p"] + 1) ** q["dim"], seed=q["rhs_seed"] % 3)
+        return c, pool[key]
+
+    srv = ldgmg.Server(workers=args.serve_workers, max_batch=32, precision="fp32")
+    l0 = ldgmg.kernel_launches()
+    # warm: build every class once (the hierarchy cache), then a closed burst to size the stream
+    t0 = time.time()
+    warm = [srv.submit(c[0], c[1], c[2], rhs_of({"dim": c[0], "n": c[1], "p": c[2], "contrast": c[3],
+                                                  "rhs_seed": 0})[1], mu=mus[c], tol=args.tol) for c in classes]
+    for t in warm:
+        srv.wait(t)
+    build_s = time.time() - t0
+    burst = reqs[:min(len(reqs), 1000)]
+    t0 = time.time()
+    tk = []
+    for q in burst:
+        c, r = rhs_of(q)
+        tk.append(srv.submit(q["dim"], q["n"], q["p"], r, mu=mus[c], tol=args.tol))
+    for t in tk:
+        srv.wait(t)
+    capacity = len(burst) / (time.time() - t0)
+    rate = 0.8 * capacity
+    # the timed stream: Poisson arrivals at 80% of the measured capacity
+    arr = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs)))
+    results = [None] * len(reqs)
+    tickets = [None] * len(reqs)
+    ready = threading.Semaphore(0)
+
+    def waiter():
+        for i in range(len(reqs)):
+            ready.acquire()
+            results[i] = srv.wait(tickets[i])[1]
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    base = srv.clock()
+    for i, q in enumerate(reqs):
+        delay = base + arr[i] - srv.clock()
+        if delay > 0:
+            time.sleep(delay)
+        c, r = rhs_of(q)
+        tickets[i] = srv.submit(q["dim"], q["n"], q["p"], r, mu=mus[c], tol=args.tol)
+        ready.release()
+    th.join()
+    stats = srv.stats()
+    launches = ldgmg.kernel_launches() - l0
+    srv.close()
+    lat = np.array([r["t_end"] - r["t_submit"] for r in results]) * 1e3
+    span = max(r["t_end"] for r in results) - min(r["t_submit"] for r in results)
+    ok = sum(1 for r in results if r["status"] == ldgmg.OK and r["relres"] <= 1.05 * args.tol)
+    batches = np.array([r["batch"] for r in results])
+    # FP64 one-at-a-time GPU solver on a sample of the same stream
+    sample = reqs[:args.serve_fp64_sample]
+    hier = {}
+    ms64 = []
+    for q in sample:
+        c, r = rhs_of(q)
+        if c not in hier:
+            op = ldgmg.Operator(c[0], c[1], c[2], mus[c])
+            hier[c] = (op, ldgmg.Hierarchy(op, smoother="sai", precision="fp64"))
+        H = hier[c][1]
+        x = torch.empty(r.size, dtype=torch.float64)
+        rt = torch.from_numpy(r)
+        H.solve(rt, args.tol, x=x)                              # warm this class
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.solve(rt, args.tol, x=x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64.append(e0.elapsed_time(e1))
+    del hier
+    return {
+        "workload": f"serving_{len(reqs)}req_poisson_arrivals_{len(classes)}classes",
+        "requests": len(reqs), "classes": len(classes), "workers": args.serve_workers, "max_batch": 32,
+        "arrival_rate_per_s": rate, "closed_burst_capacity_per_s": capacity,
+        "solves_per_s": len(reqs) / span, "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                                         "p99": float(np.percentile(lat, 99))},
+        "reached_tol": ok, "mean_batch": float(batches.mean()), "max_batch_seen": int(batches.max()),
+        "class_builds_s": build_s, "builds": int(stats["builds"]), "evictions": int(stats["evictions"]),
+        "hbm_resident_gb": stats["bytes_peak"] / 1e9, "gpu_launches": int(launches),
+        "vcycle": "FP32 (batched tensor-core classes for b = 16 / 64), FP64 flexible CG",
+        "fp64_one_at_a_time": {"solves_per_s": 1e3 / float(np.mean(ms64)),
+                               "latency_ms": {"p50": float(np.percentile(ms64, 50)),
+                                              "p99": float(np.percentile(ms64, 99))},
+                               "sample": len(sample)},
+    }
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -330,13 +528,14 @@ def main():
             "e2e": {"value": s["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
-    if args.section == "batched":
+    if args.section in ("batched", "stokes", "serve"):
         import numpy as np
         import torch
         torch.cuda.set_device(local_rank)
         from paper_2412_12506_gb300 import ldgmg
         dev = torch.device("cuda", local_rank)
-        out = run_batched(args, ldgmg, torch, np, dev, torch.cuda.current_stream(), lambda: None)
+        fn = {"batched": run_batched, "stokes": run_stokes, "serve": run_serve}[args.section]
+        out = fn(args, ldgmg, torch, np, dev, torch.cuda.current_stream(), lambda: None)
         print(json.dumps(out))
         return
 
@@ -477,6 +676,8 @@ def main():
 
     # every replica runs the batched section (it contains barriers)
     batched = run_batched(args, ldgmg, torch, np, dev, stream, barrier) if args.batched_rhs > 0 else None
+    stokes = run_stokes(args, ldgmg, torch, np, dev, stream, barrier) if args.stokes_n > 0 else None
+    serve = run_serve(args, ldgmg, torch, np, dev, stream, barrier) if args.serve_requests > 0 else None
     if rank != 0:
         reps.close()
         return
@@ -494,7 +695,7 @@ def main():
         "fp64_path": fp64,
         "spmv_fp64": {"ms": spmv_ms, "GB_per_s": spmv_bytes / (spmv_ms / 1e3) / 1e9,
                       "frac_of_hbm": spmv_bytes / (spmv_ms / 1e3) / 1e9 / peak},
-        "roofline": roofline, "batched": batched, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "roofline": roofline, "batched": batched, "stokes": stokes, "serve": serve, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "setup_s": setup_s,
     }
     print(json.dumps(line))

@@ -6,7 +6,8 @@
  * discontinuous Galerkin methods"): the element-block-sparse LDG operator,
  * block-Jacobi and balanced block-SAI smoothers, the per-level residual,
  * restriction and prolongation of the V-cycle (Algorithm 1), the bottom
- * pseudo-inverse, and multigrid-preconditioned CG.
+ * pseudo-inverse, and multigrid-preconditioned CG; and the same hierarchy for
+ * the LDG Stokes saddle-point system (Sec. 3) with restarted GMRES.
  *
  * Conventions shared by every call
  *   - Mesh: uniform periodic Cartesian n^dim mesh of the unit square/cube
@@ -14,6 +15,9 @@
  *     fastest: e = ix + n*iy (+ n*n*iz).
  *   - Basis: tensor-product orthonormal Legendre modes (Sec. 2.1), b = (p+1)^dim
  *     coefficients per element, mode m = kx + (p+1)*ky (+ (p+1)^2*kz).
+ *     A Stokes operator (ldgmg_assemble_stokes) has dim + 1 fields per element
+ *     in the order u_1, .., u_dim, p, each with (p+1)^dim modes: block size
+ *     b = (dim+1)(p+1)^dim, dof (field f, mode m) at f*(p+1)^dim + m.
  *   - Vector layout: a vector is N*b contiguous values [element][mode]; calls
  *     taking nrhs > 1 right-hand sides take nrhs such vectors one after another
  *     ([rhs][element][mode]).  FP64 vectors are double; V-cycle level vectors
@@ -55,6 +59,7 @@ enum { LDGMG_FORM_B1 = 0, LDGMG_FORM_BT = 1 };            /* SAI smoother form, 
 enum { LDGMG_FP64 = 0, LDGMG_FP32 = 1, LDGMG_BF16 = 2, LDGMG_FP16 = 3 };   /* V-cycle precision */
 enum { LDGMG_MAT_A = 0, LDGMG_MAT_B = 1, LDGMG_MAT_BT = 2, LDGMG_MAT_D = 3 }; /* level matrices */
 enum { LDGMG_OUTER_AUTO = 0, LDGMG_OUTER_FP64 = 1, LDGMG_OUTER_DF = 2 };  /* batched outer apply */
+enum { LDGMG_KRYLOV_AUTO = 0, LDGMG_KRYLOV_CG = 1, LDGMG_KRYLOV_GMRES = 2 }; /* outer Krylov method */
 
 typedef struct {
   int dim;          /* 2 or 3 */
@@ -85,6 +90,12 @@ typedef struct {
                             LDGMG_OUTER_AUTO = DF when max mu / min mu <= 10, else FP64.
                             FP64 hierarchies always use FP64.  The final residual that
                             ldgmg_solve reports is always computed in FP64. */
+  int krylov;            /* ldgmg_solve's method: LDGMG_KRYLOV_CG (SPD scalar problems),
+                            LDGMG_KRYLOV_GMRES (Stokes: A and V are symmetric indefinite,
+                            Sec. 3.4), or LDGMG_KRYLOV_AUTO = GMRES for Stokes, else CG */
+  int restart;           /* GMRES restart length m, 1..200 (Krylov vectors kept on the device) */
+  double zeta;           /* Stokes SAI balancing (Sec. 3.3); <= 0 takes Table tab:zeta for
+                            (gamma, dim, p), 0.1 where the table has no entry */
 } ldgmg_setup_opts;
 
 typedef struct ldgmg_op ldgmg_op;
@@ -92,7 +103,8 @@ typedef struct ldgmg_hier ldgmg_hier;
 
 /* Fill *o with the paper's defaults: SAI, ell = 1, balanced, nu1 = nu2 = 3,
  * omega = 0.8, B1 pre / BT post, FP64, max_iter = 200, max_rhs = 1,
- * outer_apply = LDGMG_OUTER_AUTO. */
+ * outer_apply = LDGMG_OUTER_AUTO, krylov = LDGMG_KRYLOV_AUTO, restart = 50,
+ * zeta = 0 (table). */
 void ldgmg_default_opts(ldgmg_setup_opts* o);
 
 /* Assemble the LDG Laplacian A = sum_a G_a^T M_mu G_a + E of Sec. 2.1 (display
@@ -110,8 +122,39 @@ void ldgmg_default_opts(ldgmg_setup_opts* o);
 ldgmg_status ldgmg_assemble(const ldgmg_mesh* mesh, int p, const double* mu_host, double tau0,
                             ldgmg_op** out);
 
+/* Assemble the LDG Stokes saddle-point operator of Sec. 3.1 (Eq. components)
+ * on the device, FP64, block size b = (dim+1)(p+1)^dim with fields
+ * (u_1, .., u_dim, p) per element:
+ *   (u_f, u_g) = delta_fg (sum_a G_a^T M_mu G_a + E) + gamma G_g^T M_mu G_f
+ *   (u_f, p) = -G_f^T M,   (p, u_g) = -M G_g,   (p, p) = -E_p
+ * with G, M_mu, E those of ldgmg_assemble and M the unweighted mass.
+ *   gamma        0: standard form, 1: stress form (Sec. 3.1).
+ *   tau0         velocity penalty constant as in ldgmg_assemble (> 0).
+ *   taup         pressure penalty: E_p = sum_faces tau_p int_f [p][q] with
+ *                tau_p = taup * h / min(mu_L, mu_U) (>= 0; 0 disables it).
+ *                The paper takes its values from [flame]; 0.05 puts the
+ *                balanced E_p sub-block at 0.2-0.7 zeta as Sec. 3.3 reports.
+ * The operator is symmetric indefinite; on the periodic mesh its kernel is the
+ * constant velocities and the constant pressure (dim + 1 modes).  b must be a
+ * supported block size (2D: p = 1, 2, 3; 3D: p = 1).  Errors: EINVAL,
+ * EUNSUPPORTED, ENOMEM, ECUDA. */
+ldgmg_status ldgmg_assemble_stokes(const ldgmg_mesh* mesh, int p, const double* mu_host, int gamma,
+                                   double tau0, double taup, ldgmg_op** out);
+
 /* Sizes of an assembled operator: N elements, b dofs per element, nnzb stored blocks. */
 ldgmg_status ldgmg_op_info(const ldgmg_op* op, int64_t* N, int* b, int64_t* nnzb);
+
+/* Device memory held by a handle: the operator (FP64 A, its double-FP32 copy
+ * once a hierarchy asked for it, scratch) or a hierarchy (level matrices and
+ * vectors, bottom pseudo-inverse, Krylov work space), in bytes.  Scratch used
+ * only while a call runs is not included.  For HBM budgeting (e.g. admission
+ * of requests by footprint). */
+ldgmg_status ldgmg_op_device_bytes(const ldgmg_op* op, size_t* bytes);
+ldgmg_status ldgmg_hier_device_bytes(const ldgmg_hier* h, size_t* bytes);
+
+/* Field structure: nfields = 1 (scalar) or dim + 1 (Stokes), field_b = (p+1)^dim
+ * dofs per field and element (b = nfields * field_b). */
+ldgmg_status ldgmg_op_fields(const ldgmg_op* op, int* nfields, int* field_b);
 
 /* y = A x in FP64 (Sec. 2.3: y_i = sum_j A_ij x_j) for nrhs >= 1 stacked
  * vectors.  x_dev, y_dev: device arrays of N*b*nrhs doubles, must not overlap. */
@@ -119,7 +162,8 @@ ldgmg_status ldgmg_apply(ldgmg_op* op, const double* x_dev, double* y_dev, int n
 
 /* Remove the kernel component (constant functions, Sec. 2.2 "Bottom solver"):
  * v <- v - (c^T v / c^T c) c with c the coefficients of u == 1, for each of the
- * nrhs stacked vectors.  In place. */
+ * nrhs stacked vectors; for a Stokes operator, once per field (constant
+ * velocity components and constant pressure).  In place. */
 ldgmg_status ldgmg_project_kernel(ldgmg_op* op, double* v_dev, int nrhs, void* stream);
 
 /* Build the multigrid hierarchy (Sec. 2.2): levels n, n/2, ... while n is even
@@ -144,9 +188,17 @@ ldgmg_status ldgmg_hier_info(const ldgmg_hier* h, int level, int* nlevels, int* 
 ldgmg_status ldgmg_vcycle(ldgmg_hier* h, const double* b_dev, double* x_dev, int nrhs,
                           void* stream);
 
-/* Solve A x = rhs by V-preconditioned CG from x0 = 0 (Sec. 2.2, last paragraph)
- * until ||rhs - A x||_2 <= tol ||rhs||_2, for nrhs <= max_rhs stacked right-hand
- * sides at once (batched hierarchy when nrhs > 1).  Every right-hand side keeps
+/* Solve A x = rhs from x0 = 0 with the V-cycle as preconditioner.
+ * CG (Sec. 2.2, last paragraph; flexible Polak-Ribiere form when the V-cycle
+ * runs in reduced precision) stops when ||rhs - A x||_2 <= tol ||rhs||_2, for
+ * nrhs <= max_rhs stacked right-hand sides at once (batched hierarchy when
+ * nrhs > 1).  GMRES (Stokes, Sec. 3.4; nrhs = 1; restarted every `restart`
+ * steps, modified Gram-Schmidt Arnoldi, Givens rotations, FP64 Krylov
+ * vectors): with an FP64 V-cycle it is left preconditioned as in the paper and
+ * stops when ||V (rhs - A x)||_2 <= tol ||V rhs||_2; with a reduced-precision
+ * V-cycle, which is not an exactly linear operator, it is the flexible
+ * right-preconditioned variant (preconditioned directions kept) and stops
+ * when ||rhs - A x||_2 <= tol ||rhs||_2.  Every right-hand side keeps
  * its own CG scalars and stops updating once it has converged, so its result
  * is the same whether it is solved alone or in a batch.  rhs and x may be
  * device pointers or host pointers (pinned or pageable); host buffers are

@@ -28,6 +28,12 @@ typedef struct ldgmg_host_hier ldgmg_host_hier;
 ldgmg_status ldgmg_host_build(const ldgmg_mesh* mesh, int p, const double* mu_host, double tau0,
                               const ldgmg_setup_opts* opts, ldgmg_host_hier** out);
 
+/* Same for the Stokes operator of ldgmg_assemble_stokes (gamma, tau0, taup as
+ * there); Stokes-balanced SAI with opts->zeta (Sec. 3.3). */
+ldgmg_status ldgmg_host_build_stokes(const ldgmg_mesh* mesh, int p, const double* mu_host, int gamma,
+                                     double tau0, double taup, const ldgmg_setup_opts* opts,
+                                     ldgmg_host_hier** out);
+
 /* Level count and, for level l, n, N, b, stored blocks of A_l and of the
  * smoother matrix (B_l for SAI, D_l for Jacobi; 0 on the bottom level), and the
  * number of distinct blocks held for A_l (the size of its block pool). */

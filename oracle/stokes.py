@@ -28,6 +28,9 @@ Readings (the paper defers these to [flame]):
   * GMRES (Sec. 2.2 / 3.4): left preconditioned (solves V A x = V b), restarted
     every `restart` steps, modified Gram-Schmidt Arnoldi and Givens rotations;
     stops when the preconditioned residual ||V (b - A x)|| <= tol ||V b||.
+    The paper does not name the orthogonalisation; MGS is the reading.
+  * fgmres: the flexible right-preconditioned variant for a V-cycle applied in
+    reduced precision (not an exactly linear operator); stops on ||b - A x||.
 """
 from __future__ import annotations
 
@@ -254,4 +257,61 @@ def gmres(A, V, b: np.ndarray, tol: float = 1e-10, restart: int = 50, max_iter: 
         if abs(g[j_done]) <= tol * beta0:
             break
         r = V(b - apply_A(x))
+    return x, k, hist
+
+
+def fgmres(A, V, b: np.ndarray, tol: float = 1e-10, restart: int = 50, max_iter: int = 200):
+    """Flexible right-preconditioned restarted GMRES (Saad's FGMRES) from x0 = 0:
+    z_j = V(q_j) is kept, the Arnoldi step orthogonalises A z_j, and
+    x = x0 + Z y minimises ||b - A x|| over span(Z).  The form of GMRES used
+    when V is applied in reduced precision and so is not exactly linear.
+    Returns (x, iterations, history of ||b - A x_k||)."""
+    apply_A = A if callable(A) else (lambda v: A @ v)
+    x = np.zeros_like(b)
+    r = b - apply_A(x)
+    beta0 = np.linalg.norm(r)
+    hist = [beta0]
+    if beta0 == 0.0:
+        return x, 0, hist
+    k = 0
+    while k < max_iter:
+        beta = np.linalg.norm(r)
+        m = min(restart, max_iter - k)
+        Q = np.zeros((len(b), m + 1))
+        Z = np.zeros((len(b), m))
+        H = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        Q[:, 0] = r / beta
+        j_done = 0
+        for j in range(m):
+            Z[:, j] = V(Q[:, j])
+            w = apply_A(Z[:, j])
+            for i in range(j + 1):                       # modified Gram-Schmidt
+                H[i, j] = Q[:, i] @ w
+                w = w - H[i, j] * Q[:, i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0:
+                Q[:, j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            k += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]))
+            if abs(g[j + 1]) <= tol * beta0:
+                break
+        y = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
+        x = x + Z[:, :j_done] @ y
+        if abs(g[j_done]) <= tol * beta0:
+            break
+        r = b - apply_A(x)
     return x, k, hist

@@ -52,7 +52,9 @@ def build(verbose: bool = False, extra_nvcc=()) -> str:
             cmds.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                          "--expt-relaxed-constexpr", *common_inc, *extra_nvcc, "-c", path, "-o", obj])
         elif src.endswith(".cpp"):
-            cmds.append(["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", *common_inc, "-c", path, "-o", obj])
+            cuda_inc = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include")
+            cmds.append(["g++", "-O3", "-std=c++17", "-fPIC", "-pthread", *common_inc, "-I", cuda_inc,
+                         "-c", path, "-o", obj])
         else:
             continue
         objs.append(obj)

@@ -64,8 +64,16 @@ static double storage_scale(const PBSR& H, int prec) {
   return std::ldexp(1.0, 15 - e);
 }
 
+// Device bytes held by the handle being built on this thread (ldgmg_*_device_bytes).
+static thread_local size_t* g_acct = nullptr;
+struct AcctScope {
+  size_t* prev;
+  explicit AcctScope(size_t* target) : prev(g_acct) { g_acct = target; }
+  ~AcctScope() { g_acct = prev; }
+};
+
 template <class T>
-static ldgmg_status dalloc(T** p, size_t bytes) {
+static ldgmg_status dalloc_impl(T** p, size_t bytes, bool persistent) {
   *p = nullptr;
   if (bytes == 0) return LDGMG_OK;
   cudaError_t e = cudaMalloc((void**)p, bytes);
@@ -73,8 +81,15 @@ static ldgmg_status dalloc(T** p, size_t bytes) {
     *p = nullptr;
     return fail(LDGMG_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
   }
+  if (persistent && g_acct) *g_acct += bytes;
   return LDGMG_OK;
 }
+// allocation owned by the handle under construction (counted)
+template <class T>
+static ldgmg_status dalloc(T** p, size_t bytes) { return dalloc_impl(p, bytes, true); }
+// scratch freed before the building call returns (not counted)
+template <class T>
+static ldgmg_status dalloc_tmp(T** p, size_t bytes) { return dalloc_impl(p, bytes, false); }
 
 static void free_mat(DevMat& M) {
   cudaFree(M.row_ptr);
@@ -100,8 +115,8 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat
   if (M.nnzb) CK(cudaMemcpyAsync(M.col, H.col.data(), H.col.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   uint32_t* d_ids = nullptr;
   double* d_pool = nullptr;
-  CKS(dalloc(&d_ids, H.id.size() * sizeof(uint32_t)));
-  CKS(dalloc(&d_pool, H.pool.data.size() * sizeof(double)));
+  CKS(dalloc_tmp(&d_ids, H.id.size() * sizeof(uint32_t)));
+  CKS(dalloc_tmp(&d_pool, H.pool.data.size() * sizeof(double)));
   if (M.nnzb) {
     CK(cudaMemcpyAsync(d_ids, H.id.data(), H.id.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_pool, H.pool.data.data(), H.pool.data.size() * sizeof(double),
@@ -126,6 +141,7 @@ struct ldgmg_op {
   double mu_contrast = 1.0; // max mu / min mu
   double* partials = nullptr;
   double* scal = nullptr;
+  size_t dev_bytes = 0;     // device memory held by this handle
 };
 
 struct DevLevel {
@@ -161,6 +177,12 @@ struct ldgmg_hier {
   int* err = nullptr;            // device flag set by bounded waits
   double* hscal = nullptr;       // pinned host mirror of per-RHS scalars
   int* hactive = nullptr;        // pinned host mirror of the flags
+  // GMRES (single right-hand side): Krylov basis Q (restart + 1 vectors),
+  // preconditioned directions Z (flexible variant, restart vectors), device
+  // Hessenberg column / coefficients, pinned host mirror
+  bool gmres = false;
+  double *gq = nullptr, *gz = nullptr, *gs = nullptr, *hgs = nullptr;
+  size_t dev_bytes = 0;          // device memory held by this handle
 };
 
 static const HostLevel& host_level(const ldgmg_hier* h, int l) {
@@ -214,6 +236,9 @@ void ldgmg_default_opts(ldgmg_setup_opts* o) {
   o->max_iter = 200;
   o->max_rhs = 1;
   o->outer_apply = LDGMG_OUTER_AUTO;
+  o->krylov = LDGMG_KRYLOV_AUTO;
+  o->restart = 50;
+  o->zeta = 0.0;
 }
 
 void ldgmg_op_free(ldgmg_op* op) {
@@ -225,24 +250,30 @@ void ldgmg_op_free(ldgmg_op* op) {
   delete op;
 }
 
-ldgmg_status ldgmg_assemble(const ldgmg_mesh* mesh, int p, const double* mu_host, double tau0,
-                            ldgmg_op** out) {
+}  // extern "C"
+
+// Common part of the assembly entry points: checks, host assembly by
+// `assemble`, and the FP64 device copy of A.
+template <class Assemble>
+static ldgmg_status make_op(const ldgmg_mesh* mesh, int p, int nfields, const double* mu_host, double tau0,
+                            ldgmg_op** out, Assemble assemble) {
   g_err.clear();
   if (!mesh || !out) return fail(LDGMG_EINVAL, "null argument");
   *out = nullptr;
   if (!mesh->periodic) return fail(LDGMG_EUNSUPPORTED, "only periodic meshes are supported");
   if (mesh->dim != 2 && mesh->dim != 3) return fail(LDGMG_EINVAL, "dim must be 2 or 3");
   if (mesh->n < 1 || mesh->n > 4096) return fail(LDGMG_EINVAL, "n out of range");
-  int b = 1;
+  int b = nfields;
   for (int t = 0; t < mesh->dim; ++t) b *= (p + 1);
   if (p < 1 || !block_size_supported(b)) return fail(LDGMG_EUNSUPPORTED, "unsupported block size");
   ldgmg_op* op = new (std::nothrow) ldgmg_op();
   if (!op) return fail(LDGMG_ENOMEM, "host allocation");
-  std::string err = assemble_fine(op->host, mesh->dim, mesh->n, p, mu_host, tau0);
+  std::string err = assemble(op->host);
   if (!err.empty()) {
     delete op;
     return fail(LDGMG_EINVAL, err);
   }
+  AcctScope acct(&op->dev_bytes);
   op->tau0 = tau0;
   if (mu_host) {
     double lo = mu_host[0], hi = mu_host[0];
@@ -260,6 +291,41 @@ ldgmg_status ldgmg_assemble(const ldgmg_mesh* mesh, int p, const double* mu_host
     return s;
   }
   *out = op;
+  return LDGMG_OK;
+}
+
+extern "C" {
+
+ldgmg_status ldgmg_assemble(const ldgmg_mesh* mesh, int p, const double* mu_host, double tau0,
+                            ldgmg_op** out) {
+  return make_op(mesh, p, 1, mu_host, tau0, out,
+                 [&](HostLevel& L) { return assemble_fine(L, mesh->dim, mesh->n, p, mu_host, tau0); });
+}
+
+ldgmg_status ldgmg_assemble_stokes(const ldgmg_mesh* mesh, int p, const double* mu_host, int gamma,
+                                   double tau0, double taup, ldgmg_op** out) {
+  if (!mesh) return fail(LDGMG_EINVAL, "null argument");
+  return make_op(mesh, p, mesh->dim + 1, mu_host, tau0, out, [&](HostLevel& L) {
+    return assemble_stokes_fine(L, mesh->dim, mesh->n, p, mu_host, gamma, tau0, taup);
+  });
+}
+
+ldgmg_status ldgmg_op_device_bytes(const ldgmg_op* op, size_t* bytes) {
+  if (!op || !bytes) return fail(LDGMG_EINVAL, "null argument");
+  *bytes = op->dev_bytes;
+  return LDGMG_OK;
+}
+
+ldgmg_status ldgmg_hier_device_bytes(const ldgmg_hier* h, size_t* bytes) {
+  if (!h || !bytes) return fail(LDGMG_EINVAL, "null argument");
+  *bytes = h->dev_bytes;
+  return LDGMG_OK;
+}
+
+ldgmg_status ldgmg_op_fields(const ldgmg_op* op, int* nfields, int* field_b) {
+  if (!op) return fail(LDGMG_EINVAL, "null op");
+  if (nfields) *nfields = op->host.nf;
+  if (field_b) *field_b = op->host.bs;
   return LDGMG_OK;
 }
 
@@ -285,12 +351,14 @@ ldgmg_status ldgmg_project_kernel(ldgmg_op* op, double* v, int nrhs, void* strea
   if (nrhs < 1) return fail(LDGMG_EINVAL, "nrhs must be >= 1");
   cudaStream_t st = (cudaStream_t)stream;
   // c has equal mode-0 entries and zeros elsewhere, so the projection
-  // subtracts the mean of the mode-0 coefficients from each of them.
-  const int64_t N = op->host.N, b = op->host.b;
-  for (int r = 0; r < nrhs; ++r) {
-    CK(strided_sum(N, b, v + r * N * b, op->partials, op->scal, st));
-    CK(strided_sub_mean(N, b, v + r * N * b, op->scal, st));
-  }
+  // subtracts the mean of the mode-0 coefficients from each of them (per
+  // field: the field's mode 0 sits at offset f * bs inside each block).
+  const int64_t N = op->host.N, b = op->host.b, bs = op->host.bs;
+  for (int r = 0; r < nrhs; ++r)
+    for (int f = 0; f < op->host.nf; ++f) {
+      CK(strided_sum(N, b, v + r * N * b + f * bs, op->partials, op->scal, st));
+      CK(strided_sub_mean(N, b, v + r * N * b + f * bs, op->scal, st));
+    }
   return LDGMG_OK;
 }
 
@@ -310,6 +378,10 @@ void ldgmg_hier_free(ldgmg_hier* h) {
     cudaFree(v);
   cudaFree(h->active);
   cudaFree(h->err);
+  cudaFree(h->gq);
+  cudaFree(h->gz);
+  cudaFree(h->gs);
+  if (h->hgs) cudaFreeHost(h->hgs);
   if (h->hscal) cudaFreeHost(h->hscal);
   if (h->hactive) cudaFreeHost(h->hactive);
   delete h;
@@ -334,11 +406,11 @@ static ldgmg_status bottom_pinv(ldgmg_hier* h, const HostLevel& L, cudaStream_t 
   h->nbot = n;
   double *dA = nullptr, *dW = nullptr, *dWork = nullptr, *dU2 = nullptr, *dInv = nullptr;
   int* dInfo = nullptr;
-  CKS(dalloc(&dA, size_t(n) * n * sizeof(double)));
-  CKS(dalloc(&dU2, size_t(n) * n * sizeof(double)));
-  CKS(dalloc(&dW, n * sizeof(double)));
-  CKS(dalloc(&dInv, n * sizeof(double)));
-  CKS(dalloc(&dInfo, sizeof(int)));
+  CKS(dalloc_tmp(&dA, size_t(n) * n * sizeof(double)));
+  CKS(dalloc_tmp(&dU2, size_t(n) * n * sizeof(double)));
+  CKS(dalloc_tmp(&dW, n * sizeof(double)));
+  CKS(dalloc_tmp(&dInv, n * sizeof(double)));
+  CKS(dalloc_tmp(&dInfo, sizeof(int)));
   CKS(dalloc(&h->pinv, size_t(n) * n * sizeof(double)));
   CK(cudaMemcpyAsync(dA, dense.data(), size_t(n) * n * sizeof(double), cudaMemcpyHostToDevice, st));
   cusolverDnHandle_t sh = nullptr;
@@ -354,7 +426,7 @@ static ldgmg_status bottom_pinv(ldgmg_hier* h, const HostLevel& L, cudaStream_t 
     status = fail(LDGMG_ECUDA, "cusolverDnDsyevd_bufferSize");
     goto done;
   }
-  if ((status = dalloc(&dWork, size_t(lwork) * sizeof(double))) != LDGMG_OK) goto done;
+  if ((status = dalloc_tmp(&dWork, size_t(lwork) * sizeof(double))) != LDGMG_OK) goto done;
   if (cusolverDnDsyevd(sh, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, int(n), dA, int(n), dW, dWork, lwork,
                        dInfo) != CUSOLVER_STATUS_SUCCESS) {
     status = fail(LDGMG_ECUDA, "cusolverDnDsyevd");
@@ -423,7 +495,11 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   if (o->max_rhs < 1 || o->max_rhs > 128) return fail(LDGMG_EINVAL, "max_rhs must be in 1..128");
   if (o->outer_apply < 0 || o->outer_apply > 2) return fail(LDGMG_EINVAL, "outer_apply");
   if (o->smoother == LDGMG_JACOBI && !(o->omega > 0.0 && o->omega < 2.0)) return fail(LDGMG_EINVAL, "omega");
+  if (o->krylov < 0 || o->krylov > 2) return fail(LDGMG_EINVAL, "krylov");
+  if (o->restart < 1 || o->restart > 200) return fail(LDGMG_EINVAL, "restart must be in 1..200");
+  if (!std::isfinite(o->zeta)) return fail(LDGMG_EINVAL, "zeta");
   const bool batched = o->max_rhs > 1;
+  if (batched && op->host.nf > 1) return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 is implemented for scalar operators");
   if (batched && o->vcycle_precision != LDGMG_BF16 && o->vcycle_precision != LDGMG_FP32)
     return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 needs vcycle_precision LDGMG_BF16 or LDGMG_FP32 (tensor-core path)");
   if (batched && !tc_block_size_supported(op->host.b))
@@ -431,6 +507,7 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   cudaStream_t st = (cudaStream_t)stream;
   ldgmg_hier* h = new (std::nothrow) ldgmg_hier();
   if (!h) return fail(LDGMG_ENOMEM, "host allocation");
+  AcctScope acct(&h->dev_bytes);
   h->op = op;
   h->o = *o;
   h->prec = o->vcycle_precision;
@@ -453,6 +530,7 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   sp.smoother = o->smoother;
   sp.sai_level = o->sai_level;
   sp.balance = o->balance;
+  sp.zeta = o->zeta;
   const int nth = std::max(1u, std::thread::hardware_concurrency());
   for (int l = 0; l + 1 < nl; ++l) {
     HostLevel& L = l == 0 ? op->host : h->host[l];
@@ -512,6 +590,7 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   if (h->use_df && !op->A_pairs) {
     // FP32-pair copy of the FP64 operator for the batched outer apply (df_apply.cu)
     const int64_t cnt = op->A.nnzb * int64_t(op->A.b) * op->A.b;
+    AcctScope acct_op(&op->dev_bytes);       // owned (and freed) by the operator
     ldgmg_status s = dalloc((char**)&op->A_pairs, size_t(cnt) * 8);
     if (s != LDGMG_OK) return bail(s);
     if (split_to_float_pairs(cnt, static_cast<const double*>(op->A.vals), op->A_pairs, st) != cudaSuccess)
@@ -529,6 +608,17 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   if (cudaMallocHost((void**)&h->hscal, size_t(kCgSlots) * h->Rmax * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void**)&h->hactive, size_t(h->Rmax) * sizeof(int)) != cudaSuccess)
     return bail(fail(LDGMG_ENOMEM, "cudaMallocHost"));
+  h->gmres = o->krylov == LDGMG_KRYLOV_GMRES || (o->krylov == LDGMG_KRYLOV_AUTO && op->host.nf > 1);
+  if (h->gmres) {
+    const size_t nv = size_t(L0.N) * L0.b * sizeof(double);
+    const int m = o->restart;
+    if (dalloc(&h->gq, nv * (m + 1)) != LDGMG_OK ||
+        (h->prec != P_FP64 && dalloc(&h->gz, nv * m) != LDGMG_OK) ||
+        dalloc(&h->gs, size_t(m + 2) * sizeof(double)) != LDGMG_OK)
+      return bail(LDGMG_ENOMEM);
+    if (cudaMallocHost((void**)&h->hgs, size_t(m + 2) * sizeof(double)) != cudaSuccess)
+      return bail(fail(LDGMG_ENOMEM, "cudaMallocHost"));
+  }
   if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "memset"));
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "setup sync"));
   *out = h;
@@ -585,7 +675,8 @@ static ldgmg_status restrict_residual(ldgmg_hier* h, int l, const void* rhs, con
     CKS(apply_mat(h, D.A, M_RES, x, rhs, nullptr, D.r, 1.0, R, st));
     r = D.r;
   }
-  CK(restrict_apply(h->op->host.dim, h->op->host.p + 1, D.n, h->P1d, r, rc, h->vprec, R, st));
+  // fields transfer independently: R right-hand sides of nf fields are R * nf scalar vectors
+  CK(restrict_apply(h->op->host.dim, h->op->host.p + 1, D.n, h->P1d, r, rc, h->vprec, R * h->op->host.nf, st));
   return LDGMG_OK;
 }
 
@@ -605,7 +696,8 @@ static ldgmg_status vcycle_level(ldgmg_hier* h, int l, int R, cudaStream_t st) {
   CKS(restrict_residual(h, l, D.rhs, D.x, xz, h->lv[l + 1].rhs, R, st));
   CKS(vcycle_level(h, l + 1, R, st));
   if (xz) CK(cudaMemsetAsync(D.x, 0, size_t(D.N) * D.b * h->vsz * R, st));
-  CK(prolong_apply(h->op->host.dim, h->op->host.p + 1, D.n, h->P1d, h->lv[l + 1].x, D.x, h->vprec, R, st));
+  CK(prolong_apply(h->op->host.dim, h->op->host.p + 1, D.n, h->P1d, h->lv[l + 1].x, D.x, h->vprec,
+                   R * h->op->host.nf, st));
   for (int s = 0; s < h->o.nu2; ++s) CKS(smooth(h, l, h->o.post_form, D.rhs, D.x, D.x, false, R, st));
   return LDGMG_OK;
 }
@@ -663,6 +755,113 @@ static ldgmg_status read_slot(ldgmg_hier* h, int slot, int R, cudaStream_t st) {
   return LDGMG_OK;
 }
 
+// Restarted GMRES from x = 0 on one right-hand side b (FP64 device vectors),
+// the outer solver for the symmetric indefinite Stokes system (Sec. 3.4).
+// Arnoldi by modified Gram-Schmidt (dots and updates on the device, the
+// Hessenberg column read back once per step), Givens rotations and the
+// least-squares update on the host.  With an FP64 V-cycle it is left
+// preconditioned (solves V A x = V b, tests ||V(b - A x)|| <= tol ||V b||);
+// with a reduced-precision V-cycle it is the flexible right-preconditioned
+// form (x = sum y_j z_j with z_j = V q_j kept, tests ||b - A x|| <= tol ||b||).
+static ldgmg_status gmres_solve(ldgmg_hier* h, const double* b, double* x, double tol, int* iters,
+                                cudaStream_t st) {
+  const HostLevel& L0 = h->op->host;
+  const int64_t n = L0.N * L0.b;
+  const int m = h->o.restart;
+  const bool flexible = h->prec != P_FP64;
+  double* Q = h->gq;
+  auto q = [&](int i) { return Q + int64_t(i) * n; };
+  auto zv = [&](int i) { return h->gz + int64_t(i) * n; };
+  auto norm2 = [&](const double* v, double* out) -> ldgmg_status {
+    CK(dot(n, v, v, h->partials, h->gs, st));
+    CK(cudaMemcpyAsync(h->hgs, h->gs, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *out = std::sqrt(h->hgs[0]);
+    return LDGMG_OK;
+  };
+  CK(cudaMemsetAsync(x, 0, size_t(n) * sizeof(double), st));
+  // r0 = V b (left) or b (flexible), held in q_0
+  if (flexible) CK(cudaMemcpyAsync(q(0), b, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  else CKS(apply_V(h, b, q(0), 1, st));
+  double beta0 = 0.0;
+  CKS(norm2(q(0), &beta0));
+  if (iters) *iters = 0;
+  if (!std::isfinite(beta0)) return fail(LDGMG_EINVAL, "rhs contains NaN or Inf");
+  if (beta0 == 0.0) return LDGMG_OK;
+  std::vector<double> H(size_t(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  auto Hij = [&](int i, int j) -> double& { return H[size_t(i) * m + j]; };
+  double beta = beta0;
+  int k = 0;
+  bool converged = false;
+  while (k < h->o.max_iter) {
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    CK(vec_div(n, beta, q(0), q(0), st));
+    const int mm = std::min(m, h->o.max_iter - k);
+    int jd = 0;
+    for (int j = 0; j < mm; ++j) {
+      double* w = q(j + 1);
+      if (flexible) {
+        CKS(apply_V(h, q(j), zv(j), 1, st));
+        CK(bsr_apply_strided(h->op->A, M_Y, zv(j), nullptr, nullptr, w, 1.0, 1, L0.b, 0, st));
+      } else {
+        CK(bsr_apply_strided(h->op->A, M_Y, q(j), nullptr, nullptr, h->q, 1.0, 1, L0.b, 0, st));
+        CKS(apply_V(h, h->q, w, 1, st));
+      }
+      for (int i = 0; i <= j; ++i) {     // modified Gram-Schmidt
+        CK(dot(n, q(i), w, h->partials, h->gs + i, st));
+        CK(axpy_dev(n, h->gs + i, -1.0, q(i), w, st));
+      }
+      CK(dot(n, w, w, h->partials, h->gs + j + 1, st));
+      CK(cudaMemcpyAsync(h->hgs, h->gs, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i <= j; ++i) Hij(i, j) = h->hgs[i];
+      Hij(j + 1, j) = std::sqrt(h->hgs[j + 1]);
+      if (!std::isfinite(Hij(j + 1, j))) return fail(LDGMG_ENOTCONV, "GMRES breakdown (non-finite Arnoldi vector)");
+      if (Hij(j + 1, j) > 0.0) CK(vec_div(n, Hij(j + 1, j), w, w, st));
+      for (int i = 0; i < j; ++i) {      // previous rotations
+        const double t = cs[i] * Hij(i, j) + sn[i] * Hij(i + 1, j);
+        Hij(i + 1, j) = -sn[i] * Hij(i, j) + cs[i] * Hij(i + 1, j);
+        Hij(i, j) = t;
+      }
+      const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+      cs[j] = Hij(j, j) / den;
+      sn[j] = Hij(j + 1, j) / den;
+      Hij(j, j) = den;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++k;
+      jd = j + 1;
+      if (std::fabs(g[j + 1]) <= tol * beta0) break;
+    }
+    // y = R^{-1} g (upper triangular), x += Q y (left) or Z y (flexible)
+    for (int i = jd - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int c = i + 1; c < jd; ++c) t -= Hij(i, c) * y[c];
+      y[i] = t / Hij(i, i);
+    }
+    CK(cudaMemcpyAsync(h->gs, y.data(), size_t(jd) * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(vec_combine(n, jd, flexible ? h->gz : Q, n, h->gs, x, st));
+    if (std::fabs(g[jd]) <= tol * beta0) {
+      converged = true;
+      break;
+    }
+    // restart from the true (preconditioned) residual
+    CK(bsr_apply_strided(h->op->A, M_RES, x, b, nullptr, h->r, 1.0, 1, L0.b, 0, st));
+    if (flexible) CK(cudaMemcpyAsync(q(0), h->r, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else CKS(apply_V(h, h->r, q(0), 1, st));
+    CKS(norm2(q(0), &beta));
+    if (!(beta > 0.0)) {
+      converged = beta == 0.0;
+      break;
+    }
+  }
+  if (iters) *iters = k;
+  return converged ? LDGMG_OK : fail(LDGMG_ENOTCONV, "max_iter reached");
+}
+
 ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x, int nrhs, int* iters,
                          double* relres, void* stream) {
   g_err.clear();
@@ -688,6 +887,27 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     b = h->bvec;
   }
   double* xd = (R > 1) ? h->xvec : (host_x ? h->stage_x : x);
+  if (h->gmres) {
+    if (R != 1) return fail(LDGMG_EUNSUPPORTED, "GMRES solves take one right-hand side per call");
+    int it = 0;
+    double bn = 0.0;
+    CK(dot(n, b, b, h->partials, h->scal + S_BB, st));
+    CK(cudaMemcpyAsync(h->hscal, h->scal + S_BB, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    bn = h->hscal[0];
+    ldgmg_status result = gmres_solve(h, b, xd, tol, &it, st);
+    if (result != LDGMG_OK && result != LDGMG_ENOTCONV) return result;
+    const std::string msg = g_err;
+    CK(bsr_apply_strided(h->op->A, M_RES, xd, b, nullptr, h->r, 1.0, 1, bsz, 0, st));
+    CK(dot(n, h->r, h->r, h->partials, h->scal + S_TMP, st));
+    CK(cudaMemcpyAsync(h->hscal + S_TMP, h->scal + S_TMP, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (host_x) CK(cudaMemcpyAsync(x, xd, nb, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (iters) iters[0] = it;
+    if (relres) relres[0] = bn > 0.0 ? std::sqrt(h->hscal[S_TMP] / bn) : 0.0;
+    if (result != LDGMG_OK) g_err = msg;
+    return result;
+  }
   const bool flexible = h->prec != P_FP64;
   double* S = h->scal;
   auto slot = [&](int s) { return S + size_t(s) * R; };
@@ -840,7 +1060,7 @@ ldgmg_status ldgmg_level_restrict(ldgmg_hier* h, int l, const void* rhs, const v
 ldgmg_status ldgmg_level_prolong(ldgmg_hier* h, int l, const void* xc, void* x, void* stream) {
   CKS(check_level(h, l, true));
   if (!xc || !x) return fail(LDGMG_EINVAL, "null vector");
-  CK(prolong_apply(h->op->host.dim, h->op->host.p + 1, h->lv[l].n, h->P1d, xc, x, h->vprec, 1,
+  CK(prolong_apply(h->op->host.dim, h->op->host.p + 1, h->lv[l].n, h->P1d, xc, x, h->vprec, h->op->host.nf,
                    (cudaStream_t)stream));
   return LDGMG_OK;
 }

@@ -16,6 +16,8 @@
 // matrix streams once regardless of R.
 #include "kernels.h"
 
+#include <mutex>
+
 #include <algorithm>
 #include <cstdint>
 
@@ -246,13 +248,13 @@ cudaError_t bsr_apply_df(const DevMat& M, const void* pairs, int mode, const dou
 #define LDGMG_DF_CASE(BB)                                                                                  \
   case BB: {                                                                                               \
     const size_t smem = size_t(BB * BB + R * BB) * sizeof(float2);                                         \
-    static bool configured = false;                                                                        \
-    if (!configured) {                                                                                     \
-      cudaError_t e = cudaFuncSetAttribute(bsr_df_kernel<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                           int(size_t(BB * BB + 64 * BB) * sizeof(float2)));              \
-      if (e != cudaSuccess) return e;                                                                      \
-      configured = true;                                                                                   \
-    }                                                                                                      \
+    static std::once_flag once;                                                                            \
+    static cudaError_t cfg = cudaSuccess;                                                                  \
+    std::call_once(once, [] {                                                                              \
+      cfg = cudaFuncSetAttribute(bsr_df_kernel<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                 int(size_t(BB * BB + 64 * BB) * sizeof(float2)));                         \
+    });                                                                                                    \
+    if (cfg != cudaSuccess) return cfg;                                                                    \
     bsr_df_kernel<BB><<<unsigned(M.nrows), 256, smem, st>>>(M.nrows, M.row_ptr, M.col, v, x, rhs, y, R,    \
                                                             mode);                                         \
     return launched();                                                                                     \
@@ -289,13 +291,13 @@ cudaError_t bsr_apply_multi64(const DevMat& M, int mode, const double* x, const 
 #define LDGMG_M64_CASE(BB)                                                                                      \
   case BB: {                                                                                                    \
     const size_t smem = size_t(BB * BB + R * BB) * sizeof(double);                                              \
-    static bool configured = false;                                                                             \
-    if (!configured) {                                                                                          \
-      cudaError_t e = cudaFuncSetAttribute(bsr_multi64_kernel<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                           int(size_t(BB * BB + 64 * BB) * sizeof(double)));                    \
-      if (e != cudaSuccess) return e;                                                                           \
-      configured = true;                                                                                        \
-    }                                                                                                           \
+    static std::once_flag once;                                                                                 \
+    static cudaError_t cfg = cudaSuccess;                                                                       \
+    std::call_once(once, [] {                                                                                   \
+      cfg = cudaFuncSetAttribute(bsr_multi64_kernel<BB>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                 int(size_t(BB * BB + 64 * BB) * sizeof(double)));                              \
+    });                                                                                                         \
+    if (cfg != cudaSuccess) return cfg;                                                                         \
     bsr_multi64_kernel<BB><<<unsigned(M.nrows), 256, smem, st>>>(M.nrows, M.row_ptr, M.col, v, x, rhs, y, R,     \
                                                                  mode);                                         \
     return launched();                                                                                          \

@@ -253,40 +253,48 @@ static void finish_rows(PBSR& M, std::vector<std::vector<std::pair<int32_t, uint
 }
 
 // --------------------------------------------------------------------------
-// A = sum_a G_a^T M_mu G_a + E   (Sec. 2.1)
+// Products of the scalar pieces (Sec. 2.1): block (i, j) of
+//   sum over (l, r) in `pairs` of G_l^T M_mu G_r   (+ E when add_E)
+// The scalar operator is A = sum_a G_a^T M_mu G_a + E (pairs (a, a)); the
+// stress-form coupling of Sec. 3.1 uses single pairs (g, f).  Terms of a
+// block are summed in a fixed order (column, pair, ...), E last.
 // --------------------------------------------------------------------------
 
-static void build_A(HostLevel& L) {
-  const int d = L.dim, b = L.b;
+static void build_products(const HostLevel& L, const std::vector<std::pair<int, int>>& pairs, bool add_E,
+                           PBSR& out) {
+  const int b = L.bs;
   const int64_t N = L.N;
   const size_t bb = size_t(b) * b;
   // transposed structure of each G_a: for column i, the (row k, id) entries
   std::vector<std::vector<std::pair<int32_t, uint32_t>>> Gt[3];
-  for (int a = 0; a < d; ++a) {
+  for (int a = 0; a < L.dim; ++a) {
     Gt[a].assign(N, {});
     const PBSR& G = L.G[a];
     for (int64_t k = 0; k < N; ++k)
       for (int64_t z = G.row_ptr[k]; z < G.row_ptr[k + 1]; ++z) Gt[a][G.col[z]].push_back({int32_t(k), G.id[z]});
   }
-  L.A = PBSR();
-  L.A.pool.b = b;
+  out = PBSR();
+  out.pool.b = b;
   Memo memo;
   std::vector<std::vector<std::pair<int32_t, uint32_t>>> rows(N);
   std::vector<std::pair<int32_t, std::array<uint32_t, 4>>> terms;
   std::vector<double> acc(bb), tmp(bb);
   for (int64_t i = 0; i < N; ++i) {
     terms.clear();
-    for (int a = 0; a < d; ++a) {
-      const PBSR& G = L.G[a];
-      for (auto& ki : Gt[a][i]) {
+    for (size_t pi = 0; pi < pairs.size(); ++pi) {
+      const PBSR& Gl = L.G[pairs[pi].first];
+      const PBSR& Gr = L.G[pairs[pi].second];
+      (void)Gl;
+      for (auto& ki : Gt[pairs[pi].first][i]) {
         const int32_t k = ki.first;
         const uint32_t m = L.mmu[k];
-        for (int64_t z = G.row_ptr[k]; z < G.row_ptr[k + 1]; ++z)
-          terms.push_back({G.col[z], {uint32_t(a), ki.second, m, G.id[z]}});
+        for (int64_t z = Gr.row_ptr[k]; z < Gr.row_ptr[k + 1]; ++z)
+          terms.push_back({Gr.col[z], {uint32_t(pi), ki.second, m, Gr.id[z]}});
       }
     }
-    for (int64_t z = L.E.row_ptr[i]; z < L.E.row_ptr[i + 1]; ++z)
-      terms.push_back({L.E.col[z], {7u, L.E.id[z], 0u, 0u}});
+    if (add_E)
+      for (int64_t z = L.E.row_ptr[i]; z < L.E.row_ptr[i + 1]; ++z)
+        terms.push_back({L.E.col[z], {0xFFFFu, L.E.id[z], 0u, 0u}});
     std::sort(terms.begin(), terms.end());
     size_t s = 0;
     while (s < terms.size()) {
@@ -294,7 +302,9 @@ static void build_A(HostLevel& L) {
       std::vector<uint64_t> key;
       while (e < terms.size() && terms[e].first == terms[s].first) {
         const auto& t = terms[e].second;
-        key.push_back((uint64_t(t[0]) << 32) | t[1]);
+        const uint32_t tag = t[0] == 0xFFFFu ? 0xFFFFu
+                                             : uint32_t(pairs[t[0]].first * 4 + pairs[t[0]].second);
+        key.push_back((uint64_t(tag) << 32) | t[1]);
         key.push_back((uint64_t(t[2]) << 32) | t[3]);
         ++e;
       }
@@ -306,23 +316,189 @@ static void build_A(HostLevel& L) {
         std::fill(acc.begin(), acc.end(), 0.0);
         for (size_t u = s; u < e; ++u) {
           const auto& t = terms[u].second;
-          if (t[0] == 7u) {
+          if (t[0] == 0xFFFFu) {
             const double* Eb = L.E.pool.get(t[1]);
             for (size_t x = 0; x < bb; ++x) acc[x] += Eb[x];
           } else {
-            const PBSR& G = L.G[t[0]];
-            mm(L.mmu_pool.get(t[2]), G.pool.get(t[3]), tmp.data(), b);
-            mtm_acc(G.pool.get(t[1]), tmp.data(), acc.data(), b);
+            const PBSR& Gl = L.G[pairs[t[0]].first];
+            const PBSR& Gr = L.G[pairs[t[0]].second];
+            mm(L.mmu_pool.get(t[2]), Gr.pool.get(t[3]), tmp.data(), b);
+            mtm_acc(Gl.pool.get(t[1]), tmp.data(), acc.data(), b);
           }
         }
-        id = L.A.pool.intern(acc.data());
+        id = out.pool.intern(acc.data());
         memo.emplace(std::move(key), id);
       }
       rows[i].push_back({terms[s].first, id});
       s = e;
     }
   }
+  finish_rows(out, rows);
+}
+
+static void build_A(HostLevel& L) {
+  std::vector<std::pair<int, int>> pairs;
+  for (int a = 0; a < L.dim; ++a) pairs.push_back({a, a});
+  build_products(L, pairs, true, L.A);
+}
+
+// --------------------------------------------------------------------------
+// Stokes saddle-point operator (Sec. 3.1, Eq. components), field order
+// (u_1, .., u_d, p) inside each block of size (d + 1) bs:
+//   (u_f, u_g): delta_fg (sum_a G_a^T M_mu G_a + E) + gamma G_g^T M_mu G_f
+//   (u_f, p):   -G_f^T M        (p, u_g): -M G_g        (p, p): -E_p
+// M = (h/2)^d I is the unweighted mass of the orthonormal modal basis.
+// --------------------------------------------------------------------------
+
+static void build_A_stokes(HostLevel& L) {
+  const int d = L.dim, bs = L.bs, nf = d + 1, b = nf * bs;
+  const int64_t N = L.N;
+  const double m = std::pow(L.h / 2.0, d);
+  PBSR lap;
+  {
+    std::vector<std::pair<int, int>> pairs;
+    for (int a = 0; a < d; ++a) pairs.push_back({a, a});
+    build_products(L, pairs, true, lap);
+  }
+  PBSR X[3][3];  // X[f][g] = G_g^T M_mu G_f (test field f, trial field g)
+  if (L.gamma)
+    for (int f = 0; f < d; ++f)
+      for (int g = 0; g < d; ++g) build_products(L, {{g, f}}, false, X[f][g]);
+  // transposed pattern of each G_f: rows j with G_f(j, i) stored, per column i
+  std::vector<std::vector<int32_t>> Gtc[3];
+  for (int a = 0; a < d; ++a) {
+    Gtc[a].assign(N, {});
+    for (int64_t k = 0; k < N; ++k)
+      for (int64_t z = L.G[a].row_ptr[k]; z < L.G[a].row_ptr[k + 1]; ++z) Gtc[a][L.G[a].col[z]].push_back(int32_t(k));
+  }
+  L.A = PBSR();
+  L.A.pool.b = b;
+  Memo memo;
+  std::vector<std::vector<std::pair<int32_t, uint32_t>>> rows(N);
+  std::vector<double> blk(size_t(b) * b);
+  std::vector<int32_t> cols;
+  for (int64_t i = 0; i < N; ++i) {
+    cols.clear();
+    auto add_row = [&](const PBSR& M) {
+      for (int64_t z = M.row_ptr[i]; z < M.row_ptr[i + 1]; ++z) cols.push_back(M.col[z]);
+    };
+    add_row(lap);
+    add_row(L.Ep);
+    for (int a = 0; a < d; ++a) {
+      add_row(L.G[a]);
+      for (int32_t j : Gtc[a][i]) cols.push_back(j);
+      if (L.gamma)
+        for (int g = 0; g < d; ++g) add_row(X[a][g]);
+    }
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    for (int32_t j : cols) {
+      std::vector<uint64_t> key;
+      key.push_back(lap.find(i, j));
+      key.push_back(L.Ep.find(i, j));
+      for (int a = 0; a < d; ++a) {
+        key.push_back(L.G[a].find(j, int32_t(i)));   // G_a(j, i), for -G_a^T M
+        key.push_back(L.G[a].find(i, j));            // G_a(i, j), for -M G_a
+        if (L.gamma)
+          for (int g = 0; g < d; ++g) key.push_back(X[a][g].find(i, j));
+      }
+      auto it = memo.find(key);
+      if (it == memo.end()) {
+        std::fill(blk.begin(), blk.end(), 0.0);
+        auto put = [&](int f, int g, const double* src, double s, bool transpose) {
+          for (int r = 0; r < bs; ++r)
+            for (int c = 0; c < bs; ++c)
+              blk[size_t(f * bs + r) * b + g * bs + c] += s * (transpose ? src[size_t(c) * bs + r] : src[size_t(r) * bs + c]);
+        };
+        size_t u = 0;
+        const uint32_t lid = uint32_t(key[u++]), eid = uint32_t(key[u++]);
+        if (lid != UINT32_MAX)
+          for (int f = 0; f < d; ++f) put(f, f, lap.pool.get(lid), 1.0, false);
+        if (eid != UINT32_MAX) put(d, d, L.Ep.pool.get(eid), -1.0, false);
+        for (int a = 0; a < d; ++a) {
+          const uint32_t gt = uint32_t(key[u++]), gi = uint32_t(key[u++]);
+          if (gt != UINT32_MAX) put(a, d, L.G[a].pool.get(gt), -m, true);
+          if (gi != UINT32_MAX) put(d, a, L.G[a].pool.get(gi), -m, false);
+          if (L.gamma)
+            for (int g = 0; g < d; ++g) {
+              const uint32_t xid = uint32_t(key[u++]);
+              if (xid != UINT32_MAX) put(a, g, X[a][g].pool.get(xid), 1.0, false);
+            }
+        }
+        it = memo.emplace(key, L.A.pool.intern(blk.data())).first;
+      }
+      rows[i].push_back({j, it->second});
+    }
+  }
   finish_rows(L.A, rows);
+}
+
+// Interior-penalty operator sum_faces c_f int_f [u][v] on the periodic grid
+// (Sec. 2.1); coef(x, e) is the face coefficient between element e and its
+// neighbour x, including the face Jacobian.
+template <class Coef>
+static void build_penalty(PBSR& out, const Grid& g, const Basis1D& B, int dim, int b, Coef coef) {
+  const int q = B.q;
+  const size_t bb = size_t(b) * b;
+  {
+    std::vector<std::vector<double>> lolo(dim), lohi(dim), hihi(dim), hilo(dim);
+    for (int a = 0; a < dim; ++a) {
+      lolo[a] = axis_op(outer(B.lo, B.lo), a, dim, q);
+      lohi[a] = axis_op(outer(B.lo, B.hi), a, dim, q);
+      hihi[a] = axis_op(outer(B.hi, B.hi), a, dim, q);
+      hilo[a] = axis_op(outer(B.hi, B.lo), a, dim, q);
+    }
+    out = PBSR();
+    out.pool.b = b;
+    std::vector<std::vector<std::pair<int32_t, uint32_t>>> rows(g.N);
+    Memo memo;  // key: per axis (flags, c_lo, c_up) -> encoded in a list of (col-role, id)
+    std::unordered_map<std::vector<uint64_t>, std::vector<std::pair<int, uint32_t>>, VecHash> rmemo;
+    for (int64_t e = 0; e < g.N; ++e) {
+      int64_t nb[3][2];
+      std::vector<uint64_t> key;
+      double clo[3], cup[3];
+      for (int a = 0; a < dim; ++a) {
+        nb[a][0] = g.shift(e, a, -1);
+        nb[a][1] = g.shift(e, a, +1);
+        clo[a] = coef(nb[a][0], e);
+        cup[a] = coef(nb[a][1], e);
+        key.push_back(uint64_t(nb[a][0] == e) | (uint64_t(nb[a][1] == e) << 1) |
+                      (uint64_t(nb[a][0] == nb[a][1]) << 2));
+        key.push_back(dbits(clo[a]));
+        key.push_back(dbits(cup[a]));
+      }
+      auto it = rmemo.find(key);
+      if (it == rmemo.end()) {
+        // distinct neighbour roles: 0 self, 1 + 2a lower of axis a, 2 + 2a upper
+        std::map<int, std::vector<double>> blk;
+        auto add = [&](int role, const std::vector<double>& M, double c) {
+          auto& v = blk[role];
+          if (v.empty()) v.assign(bb, 0.0);
+          for (size_t x = 0; x < bb; ++x) v[x] += c * M[x];
+        };
+        for (int a = 0; a < dim; ++a) {
+          const int rl = (nb[a][0] == e) ? 0 : 1 + 2 * a;
+          const int ru = (nb[a][1] == e) ? 0 : ((nb[a][1] == nb[a][0]) ? rl : 2 + 2 * a);
+          add(0, lolo[a], clo[a]);   // face (Lo, e): e is the upper element
+          add(rl, lohi[a], -clo[a]);
+          add(0, hihi[a], cup[a]);   // face (e, Up): e is the lower element
+          add(ru, hilo[a], -cup[a]);
+        }
+        std::vector<std::pair<int, uint32_t>> lst;
+        for (auto& kv : blk) lst.push_back({kv.first, out.pool.intern(kv.second.data())});
+        it = rmemo.emplace(key, lst).first;
+      }
+      for (auto& r : it->second) {
+        int64_t c = e;
+        if (r.first > 0) {
+          const int a = (r.first - 1) / 2;
+          c = nb[a][(r.first - 1) % 2];
+        }
+        rows[e].push_back({int32_t(c), r.second});
+      }
+    }
+    finish_rows(out, rows);
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -342,6 +518,9 @@ std::string assemble_fine(HostLevel& L, int dim, int n, int p, const double* mu_
   L.n = n;
   L.p = p;
   L.b = b;
+  L.bs = b;
+  L.nf = 1;
+  L.gamma = 0;
   L.N = g.N;
   L.h = 1.0 / n;
   const double h = L.h;
@@ -429,66 +608,40 @@ std::string assemble_fine(HostLevel& L, int dim, int n, int p, const double* mu_
   }
 
   // --- penalty E = sum_faces tau_f int_f [u][v], tau_f = tau0 min(mu) / h ---
-  {
-    std::vector<std::vector<double>> lolo(dim), lohi(dim), hihi(dim), hilo(dim);
-    for (int a = 0; a < dim; ++a) {
-      lolo[a] = axis_op(outer(B.lo, B.lo), a, dim, q);
-      lohi[a] = axis_op(outer(B.lo, B.hi), a, dim, q);
-      hihi[a] = axis_op(outer(B.hi, B.hi), a, dim, q);
-      hilo[a] = axis_op(outer(B.hi, B.lo), a, dim, q);
-    }
-    L.E = PBSR();
-    L.E.pool.b = b;
-    std::vector<std::vector<std::pair<int32_t, uint32_t>>> rows(g.N);
-    Memo memo;  // key: per axis (flags, c_lo, c_up) -> encoded in a list of (col-role, id)
-    std::unordered_map<std::vector<uint64_t>, std::vector<std::pair<int, uint32_t>>, VecHash> rmemo;
-    for (int64_t e = 0; e < g.N; ++e) {
-      int64_t nb[3][2];
-      std::vector<uint64_t> key;
-      double clo[3], cup[3];
-      for (int a = 0; a < dim; ++a) {
-        nb[a][0] = g.shift(e, a, -1);
-        nb[a][1] = g.shift(e, a, +1);
-        clo[a] = tau0 * std::min(mu[nb[a][0]], mu[e]) / h * wface;
-        cup[a] = tau0 * std::min(mu[nb[a][1]], mu[e]) / h * wface;
-        key.push_back(uint64_t(nb[a][0] == e) | (uint64_t(nb[a][1] == e) << 1) |
-                      (uint64_t(nb[a][0] == nb[a][1]) << 2));
-        key.push_back(dbits(clo[a]));
-        key.push_back(dbits(cup[a]));
-      }
-      auto it = rmemo.find(key);
-      if (it == rmemo.end()) {
-        // distinct neighbour roles: 0 self, 1 + 2a lower of axis a, 2 + 2a upper
-        std::map<int, std::vector<double>> blk;
-        auto add = [&](int role, const std::vector<double>& M, double c) {
-          auto& v = blk[role];
-          if (v.empty()) v.assign(bb, 0.0);
-          for (size_t x = 0; x < bb; ++x) v[x] += c * M[x];
-        };
-        for (int a = 0; a < dim; ++a) {
-          const int rl = (nb[a][0] == e) ? 0 : 1 + 2 * a;
-          const int ru = (nb[a][1] == e) ? 0 : ((nb[a][1] == nb[a][0]) ? rl : 2 + 2 * a);
-          add(0, lolo[a], clo[a]);   // face (Lo, e): e is the upper element
-          add(rl, lohi[a], -clo[a]);
-          add(0, hihi[a], cup[a]);   // face (e, Up): e is the lower element
-          add(ru, hilo[a], -cup[a]);
-        }
-        std::vector<std::pair<int, uint32_t>> lst;
-        for (auto& kv : blk) lst.push_back({kv.first, L.E.pool.intern(kv.second.data())});
-        it = rmemo.emplace(key, lst).first;
-      }
-      for (auto& r : it->second) {
-        int64_t c = e;
-        if (r.first > 0) {
-          const int a = (r.first - 1) / 2;
-          c = nb[a][(r.first - 1) % 2];
-        }
-        rows[e].push_back({int32_t(c), r.second});
-      }
-    }
-    finish_rows(L.E, rows);
-  }
+  build_penalty(L.E, g, B, dim, b,
+                [&](int64_t x, int64_t e) { return tau0 * std::min(mu[x], mu[e]) / h * wface; });
   build_A(L);
+  return "";
+}
+
+double stokes_zeta(int gamma, int dim, int p) {
+  static const double z2[2][5] = {{0.0382, 0.131, 0.0990, 0.153, 0.142}, {0.118, 0.131, 0.0814, 0.123, 0.0745}};
+  static const double z3[2][3] = {{0.0462, 0.107, 0.113}, {0.0384, 0.0928, 0.0930}};
+  const int g = gamma ? 1 : 0;
+  if (dim == 2 && p >= 1 && p <= 5) return z2[g][p - 1];
+  if (dim == 3 && p >= 1 && p <= 3) return z3[g][p - 1];
+  return 0.1;
+}
+
+std::string assemble_stokes_fine(HostLevel& L, int dim, int n, int p, const double* mu_in, int gamma,
+                                 double tau0, double taup) {
+  if (gamma != 0 && gamma != 1) return "gamma must be 0 (standard form) or 1 (stress form)";
+  if (!(taup >= 0.0) || !std::isfinite(taup)) return "taup must be non-negative and finite";
+  std::string err = assemble_fine(L, dim, n, p, mu_in, tau0);
+  if (!err.empty()) return err;
+  const Basis1D B = make_basis(p);
+  Grid g{dim, n, L.N};
+  const double h = L.h, wface = std::pow(h / 2.0, dim - 1);
+  std::vector<double> mu(L.N, 1.0);
+  if (mu_in)
+    for (int64_t e = 0; e < L.N; ++e) mu[e] = mu_in[e];
+  // E_p = sum_faces tau_p int_f [p][q], tau_p = taup h / min(mu) (scaling E_p ~ h^d / mu, Sec. 3.3)
+  build_penalty(L.Ep, g, B, dim, L.bs,
+                [&](int64_t x, int64_t e) { return taup * h / std::min(mu[x], mu[e]) * wface; });
+  L.gamma = gamma;
+  L.nf = dim + 1;
+  L.b = L.nf * L.bs;
+  build_A_stokes(L);
   return "";
 }
 
@@ -560,7 +713,7 @@ static void coarsen_pbsr(const PBSR& F, PBSR& C, const Grid& gf, const Grid& gc,
 
 std::string coarsen(const HostLevel& F, HostLevel& C) {
   if (F.n % 2 != 0 || F.n < 2) return "cannot coarsen odd n";
-  const int d = F.dim, b = F.b, nch = 1 << d;
+  const int d = F.dim, b = F.bs, nch = 1 << d;
   const Basis1D B = make_basis(F.p);
   std::vector<std::vector<double>> Pc(nch);
   for (int s = 0; s < nch; ++s) Pc[s] = child_block(B, s, d);
@@ -568,11 +721,15 @@ std::string coarsen(const HostLevel& F, HostLevel& C) {
   C.dim = d;
   C.n = F.n / 2;
   C.p = F.p;
-  C.b = b;
+  C.b = F.b;
+  C.bs = b;
+  C.nf = F.nf;
+  C.gamma = F.gamma;
   C.N = gc.N;
   C.h = 2.0 * F.h;
   for (int a = 0; a < d; ++a) coarsen_pbsr(F.G[a], C.G[a], gf, gc, Pc, std::ldexp(1.0, -d), b);
   coarsen_pbsr(F.E, C.E, gf, gc, Pc, 0.5, b);
+  if (F.nf > 1) coarsen_pbsr(F.Ep, C.Ep, gf, gc, Pc, 2.0, b);
   // M_mu,c[C] = sum_c P_c^T M_mu,f[c] P_c
   C.mmu_pool = Pool();
   C.mmu_pool.b = b;
@@ -599,7 +756,8 @@ std::string coarsen(const HostLevel& F, HostLevel& C) {
     }
     C.mmu[Ce] = it->second;
   }
-  build_A(C);
+  if (C.nf > 1) build_A_stokes(C);
+  else build_A(C);
   return "";
 }
 
@@ -747,35 +905,68 @@ static bool householder_ls(std::vector<double>& M, int m, int nc, std::vector<do
 }
 
 // Minimum-norm least squares for a rank-deficient M (tiny periodic levels
-// where S(i) covers the whole mesh and the constants are a null vector):
-// X = (M^T M)^+ M^T Rhs with the pseudo-inverse from a symmetric
-// eigendecomposition, eigenvalues below 1e-10 of the largest dropped.
-static void minnorm_ls(const std::vector<double>& M, int m, int nc, const std::vector<double>& Rhs, int nr,
+// where S(i) covers the whole mesh and the kernel of A lies in its span):
+// X = V Sigma^+ U^T Rhs from a one-sided Jacobi SVD of M (Hestenes: plane
+// rotations of column pairs until all pairs are orthogonal to 1e-15), singular
+// values at or below 1e-12 of the largest treated as zero.
+static void minnorm_ls(const std::vector<double>& M0, int m, int nc, const std::vector<double>& Rhs, int nr,
                        std::vector<double>& X) {
-  std::vector<double> G(size_t(nc) * nc), H(size_t(nc) * nr), lam, V;
-  for (int i = 0; i < nc; ++i)
-    for (int j = 0; j < nc; ++j) {
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s += M[size_t(i) * m + k] * M[size_t(j) * m + k];
-      G[size_t(i) * nc + j] = s;
-    }
-  for (int i = 0; i < nc; ++i)
-    for (int c = 0; c < nr; ++c) {
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s += M[size_t(i) * m + k] * Rhs[size_t(c) * m + k];
-      H[size_t(i) * nr + c] = s;
-    }
-  sym_eig_jacobi(G, nc, lam, V);
-  double lmax = 0.0;
-  for (double l : lam) lmax = std::max(lmax, std::fabs(l));
+  std::vector<double> W = M0;                       // m x nc column-major, becomes U Sigma
+  std::vector<double> V(size_t(nc) * nc, 0.0);      // nc x nc column-major
+  for (int i = 0; i < nc; ++i) V[size_t(i) * nc + i] = 1.0;
+  auto col = [&](std::vector<double>& A, int rows, int j) { return A.data() + size_t(j) * rows; };
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    bool rotated = false;
+    for (int i = 0; i < nc - 1; ++i)
+      for (int j = i + 1; j < nc; ++j) {
+        double* wi = col(W, m, i);
+        double* wj = col(W, m, j);
+        double a = 0.0, bq = 0.0, g = 0.0;
+        for (int k = 0; k < m; ++k) {
+          a += wi[k] * wi[k];
+          bq += wj[k] * wj[k];
+          g += wi[k] * wj[k];
+        }
+        if (!(std::fabs(g) > 1e-15 * std::sqrt(a * bq))) continue;
+        rotated = true;
+        const double zeta = (bq - a) / (2.0 * g);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+        for (int k = 0; k < m; ++k) {
+          const double x = wi[k], y = wj[k];
+          wi[k] = c * x - sn * y;
+          wj[k] = sn * x + c * y;
+        }
+        double* vi = col(V, nc, i);
+        double* vj = col(V, nc, j);
+        for (int k = 0; k < nc; ++k) {
+          const double x = vi[k], y = vj[k];
+          vi[k] = c * x - sn * y;
+          vj[k] = sn * x + c * y;
+        }
+      }
+    if (!rotated) break;
+  }
+  std::vector<double> sig(nc);
+  double smax = 0.0;
+  for (int j = 0; j < nc; ++j) {
+    double s2 = 0.0;
+    const double* wj = col(W, m, j);
+    for (int k = 0; k < m; ++k) s2 += wj[k] * wj[k];
+    sig[j] = std::sqrt(s2);
+    smax = std::max(smax, sig[j]);
+  }
   X.assign(size_t(nc) * nr, 0.0);  // column-major nc x nr
-  for (int k = 0; k < nc; ++k) {
-    if (!(std::fabs(lam[k]) > 1e-10 * lmax)) continue;
+  for (int j = 0; j < nc; ++j) {
+    if (!(sig[j] > 1e-12 * smax)) continue;
+    const double* wj = col(W, m, j);          // sigma_j u_j
+    const double* vj = col(V, nc, j);
     for (int c = 0; c < nr; ++c) {
+      const double* rc = Rhs.data() + size_t(c) * m;
       double proj = 0.0;
-      for (int i = 0; i < nc; ++i) proj += V[size_t(i) * nc + k] * H[size_t(i) * nr + c];
-      proj /= lam[k];
-      for (int i = 0; i < nc; ++i) X[size_t(c) * nc + i] += proj * V[size_t(i) * nc + k];
+      for (int k = 0; k < m; ++k) proj += wj[k] * rc[k];
+      proj /= sig[j] * sig[j];                // (u_j . r) / sigma_j
+      for (int i = 0; i < nc; ++i) X[size_t(c) * nc + i] += proj * vj[i];
     }
   }
 }
@@ -828,16 +1019,36 @@ std::string setup_smoother(HostLevel& L, const SetupParams& sp, int nthreads) {
   }
   if (sp.smoother != 1) return "unknown smoother";
   if (sp.sai_level < 0 || sp.sai_level > 2) return "sai_level must be 0, 1 or 2";
-  // balancing: alpha_i = ||A_ii||_F^{-1/2} (Sec. 2.3.3)
-  std::vector<double> alpha(N, 1.0);
+  // balancing, one value per dof (N x b): alpha = ||A_ii||_F^{-1/2} on every dof
+  // of element i (Sec. 2.3.3); for Stokes alpha_u = ||A_ii^uu||_F^{-1/2} on the
+  // velocity dofs and alpha_p = zeta ||A_ii^uu||_F^{1/2} ||D_ii||_F^{-1} on the
+  // pressure dofs, D_ii the divergence sub-block (Sec. 3.3).
+  std::vector<double> alpha(size_t(N) * b, 1.0);
   std::vector<uint32_t> diag_id(N);
+  const double zeta = sp.zeta > 0.0 ? sp.zeta : stokes_zeta(L.gamma, L.dim, L.p);
   for (int64_t i = 0; i < N; ++i) {
     diag_id[i] = A.find(i, int32_t(i));
-    if (sp.balance) {
-      const double* D = A.pool.get(diag_id[i]);
+    if (!sp.balance) continue;
+    const double* D = A.pool.get(diag_id[i]);
+    double* al = alpha.data() + size_t(i) * b;
+    if (L.nf == 1) {
       double f = 0.0;
       for (size_t x = 0; x < bb; ++x) f += D[x] * D[x];
-      alpha[i] = 1.0 / std::sqrt(std::sqrt(f));
+      const double a = 1.0 / std::sqrt(std::sqrt(f));
+      for (int r = 0; r < b; ++r) al[r] = a;
+    } else {
+      const int nu = L.dim * L.bs;
+      double fuu = 0.0, fpu = 0.0;
+      for (int r = 0; r < b; ++r)
+        for (int c = 0; c < nu; ++c) {
+          const double v = D[size_t(r) * b + c];
+          if (r < nu) fuu += v * v;
+          else fpu += v * v;
+        }
+      const double nuu = std::sqrt(fuu), npu = std::sqrt(fpu);
+      if (!(nuu > 0.0) || !(npu > 0.0)) return "Stokes balancing: zero viscous or divergence diagonal block";
+      const double au = 1.0 / std::sqrt(nuu), ap = zeta * std::sqrt(nuu) / npu;
+      for (int r = 0; r < b; ++r) al[r] = r < nu ? au : ap;
     }
   }
   Grid g{L.dim, L.n, N};
@@ -915,10 +1126,11 @@ std::string setup_smoother(HostLevel& L, const SetupParams& sp, int nthreads) {
         const uint32_t id = A.find(R[ri], S[kj]);
         if (id == UINT32_MAX) continue;
         const double* blk = A.pool.get(id);
-        const double s = alpha[R[ri]] * alpha[S[kj]];
+        const double* ar = alpha.data() + size_t(R[ri]) * b;
+        const double* ac = alpha.data() + size_t(S[kj]) * b;
         for (int c = 0; c < b; ++c) {
           double* dst = M.data() + size_t(kj * b + c) * m + ri * b;
-          for (int r = 0; r < b; ++r) dst[r] = s * blk[size_t(r) * b + c];
+          for (int r = 0; r < b; ++r) dst[r] = (ar[r] * ac[c]) * blk[size_t(r) * b + c];
         }
       }
     size_t pos = 0;
@@ -946,10 +1158,11 @@ std::string setup_smoother(HostLevel& L, const SetupParams& sp, int nthreads) {
       auto it = bmemo.find(mk);
       if (it == bmemo.end()) {
         const auto& X = sol[cols[i].key_id];
-        const double s = alpha[S[t]] * alpha[i];
+        const double* ar = alpha.data() + size_t(S[t]) * b;
+        const double* ac = alpha.data() + size_t(i) * b;
         for (int r = 0; r < b; ++r)
           for (int c = 0; c < b; ++c) {
-            const double v = s * X[size_t(c) * nc + t * b + r];
+            const double v = (ar[r] * ac[c]) * X[size_t(c) * nc + t * b + r];
             blk[size_t(r) * b + c] = v;
             blkT[size_t(c) * b + r] = v;
           }

@@ -49,14 +49,22 @@ struct PBSR {
 };
 
 struct HostLevel {
-  int dim = 0, n = 0, p = 0, b = 0;
+  int dim = 0, n = 0, p = 0;
+  int b = 0;                       // block size of the system A (nf * bs)
+  int bs = 0;                      // block size of one scalar field, (p+1)^dim
+  int nf = 1;                      // fields per element: 1 (scalar) or dim + 1 (Stokes)
+  int gamma = 0;                   // Stokes form: 0 standard, 1 stress
   int64_t N = 0;
   double h = 0.0;
+  // scalar pieces, block size bs
   PBSR G[3];                       // discrete gradient per axis
   std::vector<uint32_t> mmu;       // mu-weighted mass, one block per element
   Pool mmu_pool;
   PBSR E;                          // penalty
-  PBSR A;                          // sum_a G_a^T M_mu G_a + E
+  PBSR Ep;                         // Stokes pressure penalty (nf > 1 only)
+  // the system: sum_a G_a^T M_mu G_a + E (scalar), or the Stokes saddle-point
+  // operator with field order (u_1, .., u_dim, p) inside each block (Sec. 3.1)
+  PBSR A;
   // smoother
   PBSR B, BT;                      // SAI (BT holds the transposed blocks of B, row-wise)
   std::vector<uint32_t> dinv;      // Jacobi: pseudo-inverse of A_ii per element
@@ -67,13 +75,25 @@ struct SetupParams {
   int smoother = 1;                // 0 Jacobi, 1 SAI
   int sai_level = 1;
   int balance = 1;
+  double zeta = 0.0;               // Stokes balancing (Sec. 3.3); <= 0: Table tab:zeta
 };
+
+// Table tab:zeta: tuned Stokes balancing value for (gamma, dim, p); 0.1 where
+// the table has no entry.
+double stokes_zeta(int gamma, int dim, int p);
 
 // Fine-level assembly (Sec. 2.1).  mu: N values or nullptr for mu == 1.
 // Returns an empty string on success, else an error message.
 std::string assemble_fine(HostLevel& L, int dim, int n, int p, const double* mu, double tau0);
 
-// Operator coarsening of `fine` onto n/2 (Sec. 2.2).
+// Fine-level Stokes assembly (Sec. 3.1, Eq. components): the scalar pieces as
+// in assemble_fine, the pressure penalty E_p (tau_p = taup h / min(mu) per
+// face), and the saddle-point system with blocks of size (dim + 1) bs.
+std::string assemble_stokes_fine(HostLevel& L, int dim, int n, int p, const double* mu, int gamma,
+                                 double tau0, double taup);
+
+// Operator coarsening of `fine` onto n/2 (Sec. 2.2; per field for Stokes,
+// with E_p,c = 2 I^T E_p I because tau_p scales with h).
 std::string coarsen(const HostLevel& fine, HostLevel& coarse);
 
 // Coarse levels of `fine` (n/2, n/4, ... while n is even and > 1), appended

@@ -27,15 +27,18 @@ static ldgmg_status herr(ldgmg_status s, const std::string& m) {
 
 extern "C" {
 
-ldgmg_status ldgmg_host_build(const ldgmg_mesh* mesh, int p, const double* mu, double tau0,
-                              const ldgmg_setup_opts* o, ldgmg_host_hier** out) {
+}  // extern "C"
+
+template <class Assemble>
+static ldgmg_status host_build(const ldgmg_mesh* mesh, const ldgmg_setup_opts* o, ldgmg_host_hier** out,
+                               Assemble assemble) {
   if (!mesh || !o || !out) return herr(LDGMG_EINVAL, "null argument");
   *out = nullptr;
   if (!mesh->periodic) return herr(LDGMG_EUNSUPPORTED, "only periodic meshes are supported");
   auto* h = new ldgmg_host_hier();
   h->smoother = o->smoother;
   h->lv.emplace_back();
-  std::string err = assemble_fine(h->lv[0], mesh->dim, mesh->n, p, mu, tau0);
+  std::string err = assemble(h->lv[0]);
   if (!err.empty()) {
     delete h;
     return herr(LDGMG_EINVAL, err);
@@ -53,6 +56,7 @@ ldgmg_status ldgmg_host_build(const ldgmg_mesh* mesh, int p, const double* mu, d
   sp.smoother = o->smoother;
   sp.sai_level = o->sai_level;
   sp.balance = o->balance;
+  sp.zeta = o->zeta;
   const int nth = int(std::max(1u, std::thread::hardware_concurrency()));
   for (size_t l = 0; l + 1 < h->lv.size(); ++l) {
     err = setup_smoother(h->lv[l], sp, nth);
@@ -63,6 +67,20 @@ ldgmg_status ldgmg_host_build(const ldgmg_mesh* mesh, int p, const double* mu, d
   }
   *out = h;
   return LDGMG_OK;
+}
+
+extern "C" {
+
+ldgmg_status ldgmg_host_build(const ldgmg_mesh* mesh, int p, const double* mu, double tau0,
+                              const ldgmg_setup_opts* o, ldgmg_host_hier** out) {
+  return host_build(mesh, o, out, [&](HostLevel& L) { return assemble_fine(L, mesh->dim, mesh->n, p, mu, tau0); });
+}
+
+ldgmg_status ldgmg_host_build_stokes(const ldgmg_mesh* mesh, int p, const double* mu, int gamma, double tau0,
+                                     double taup, const ldgmg_setup_opts* o, ldgmg_host_hier** out) {
+  return host_build(mesh, o, out, [&](HostLevel& L) {
+    return assemble_stokes_fine(L, mesh->dim, mesh->n, p, mu, gamma, tau0, taup);
+  });
 }
 
 ldgmg_status ldgmg_host_level_info(const ldgmg_host_hier* h, int l, int* nlevels, int* n, int64_t* N,

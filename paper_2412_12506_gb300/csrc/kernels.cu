@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <mutex>
 
 namespace ldgmg {
 
@@ -166,17 +167,19 @@ static int64_t coarse_count(int d, int nf) {
   return r;
 }
 
-static cudaError_t xfer_config(int smem) {
-  static int configured = 0;
-  if (smem > 48 * 1024 && configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(xfer_kernel<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(xfer_kernel<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(xfer_kernel<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(xfer_kernel<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  return cudaSuccess;
+// The largest chunk needs 2 * max(kXferCap, 8 * 8^3) doubles = 64 KB of dynamic
+// shared memory; the opt-in is set once for every instance (thread safe).
+static cudaError_t xfer_config() {
+  static std::once_flag once;
+  static cudaError_t cfg = cudaSuccess;
+  std::call_once(once, [] {
+    const int smem = 2 * 4096 * int(sizeof(double));
+    cfg = cudaFuncSetAttribute(xfer_kernel<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cfg == cudaSuccess) cfg = cudaFuncSetAttribute(xfer_kernel<true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cfg == cudaSuccess) cfg = cudaFuncSetAttribute(xfer_kernel<false, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (cfg == cudaSuccess) cfg = cudaFuncSetAttribute(xfer_kernel<false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  return cfg;
 }
 
 template <bool RESTRICT>
@@ -187,8 +190,10 @@ static cudaError_t xfer_apply(int d, int q, int n_fine, const double* P, const v
   const int Rc = xfer_chunk(d, b, R);
   const int tot = (1 << d) * Rc * b;
   const int smem = 2 * tot * (vprec == 0 ? 8 : 4);
-  cudaError_t e = xfer_config(smem);
-  if (e != cudaSuccess) return e;
+  if (smem > 48 * 1024) {
+    cudaError_t e = xfer_config();
+    if (e != cudaSuccess) return e;
+  }
   const int threads = std::min(kXferMaxThreads, (tot + 31) / 32 * 32);
   const int64_t Nc = coarse_count(d, n_fine);
   if (vprec == 0)
@@ -307,7 +312,7 @@ __global__ void axpy_dev_kernel(int64_t n, const double* __restrict__ coef, doub
     y[t] += a * x[t];
 }
 
-__global__ void div_kernel(int64_t n, double s, const double* __restrict__ x, double* __restrict__ y) {
+__global__ void div_kernel(int64_t n, double s, const double* x, double* y) {   // x may alias y
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x)
     y[t] = x[t] / s;
 }

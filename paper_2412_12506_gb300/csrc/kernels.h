@@ -103,6 +103,13 @@ cudaError_t strided_sum(int64_t count, int64_t stride, const double* v, double* 
 cudaError_t strided_sub_mean(int64_t count, int64_t stride, double* v, const double* sum,
                              cudaStream_t st);
 
+// GMRES steps: y += sgn * coef[0] * x (coef on the device); y = x / s;
+// x += sum_{i<k} y[i] * Q[i*ldq ...] (y on the device, fixed summation order)
+cudaError_t axpy_dev(int64_t n, const double* coef, double sgn, const double* x, double* y, cudaStream_t st);
+cudaError_t vec_div(int64_t n, double s, const double* x, double* y, cudaStream_t st);
+cudaError_t vec_combine(int64_t n, int k, const double* Q, int64_t ldq, const double* y, double* x,
+                        cudaStream_t st);
+
 // per right-hand-side dots on [element][rhs][mode] vectors: out[r] = sum u_r v_r
 // (v may be null: sum of squares of u).  partials: kBatchDotBlocks * R doubles.
 constexpr int kBatchDotBlocks = 256;

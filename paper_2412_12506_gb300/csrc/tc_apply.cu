@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 namespace ldgmg {
 
@@ -369,25 +370,23 @@ template <int B, bool SPLIT>
 static cudaError_t launch_tc(const BatchArgs& a, cudaStream_t st) {
   typedef TcPlan<B, SPLIT> P;
   const int smem = int(P::total(a.R));
-  static int configured = 0;
-  static int per_sm[129] = {};     // CTAs per SM by R (occupancy), 0 = not computed
-  if (configured < smem) {
-    cudaError_t e = cudaFuncSetAttribute(bsr_tc_kernel<B, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(P::total(kTcM)));
-    if (e != cudaSuccess) return e;
-    configured = int(P::total(kTcM));
-  }
-  if (!per_sm[a.R]) {
-    // resident CTAs per SM from the kernel's own needs: shared memory (227 KB
-    // per SM, ~1 KB reserved per CTA), TMEM (512 columns), threads (2048)
-    const int by_smem = (227 * 1024) / (smem + 1024);
-    const int by_tmem = 512 / (B < 32 ? 32 : B);
-    const int by_threads = 2048 / kTcThreads;
-    per_sm[a.R] = std::max(1, std::min(by_smem, std::min(by_tmem, by_threads)));
-  }
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
-  const int64_t grid = std::min<int64_t>(a.nrows, int64_t(std::max(sms, 1)) * per_sm[a.R]);
+  static std::once_flag once;
+  static cudaError_t cfg = cudaSuccess;
+  std::call_once(once, [] {
+    cfg = cudaFuncSetAttribute(bsr_tc_kernel<B, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               int(P::total(kTcM)));
+  });
+  if (cfg != cudaSuccess) return cfg;
+  // resident CTAs per SM from the kernel's own needs: shared memory (227 KB
+  // per SM, ~1 KB reserved per CTA), TMEM (512 columns), threads (2048)
+  const int by_smem = (227 * 1024) / (smem + 1024);
+  const int by_tmem = 512 / (B < 32 ? 32 : B);
+  const int by_threads = 2048 / kTcThreads;
+  const int per_sm = std::max(1, std::min(by_smem, std::min(by_tmem, by_threads)));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t grid = std::min<int64_t>(a.nrows, int64_t(std::max(sms, 1)) * per_sm);
   if (grid <= 0) return cudaSuccess;
   bsr_tc_kernel<B, SPLIT><<<unsigned(grid), kTcThreads, smem, st>>>(a);
   return launched();

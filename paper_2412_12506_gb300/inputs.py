@@ -4,11 +4,13 @@ This module only draws random numbers and describes workload shapes.  It holds
 none of the method's arithmetic (no basis, no operator, no smoother), so both
 sides can take their inputs from it without sharing any numerical code.
 
-Workloads (shapes of the paper's experiments, Sec. 2.4.1 and Sec. 2.4.3):
+Workloads (shapes of the paper's experiments, Sec. 2.4.1, 2.4.3 and 3.4):
   * periodic Poisson on the unit square / cube, mu == 1 (Sec. 2.4.1);
-  * two-phase elliptic interface problem: mu = mu_in inside a seeded circle,
-    mu_out outside, decided per element by the sign of the circle's level set
-    at the element centroid (stand-in for the square inclusion of Sec. 2.4.3).
+  * two-phase elliptic interface problem: mu = mu_in inside the paper's
+    inclusion (1/4, 3/4)^d (Sec. 2.4.3) or inside a seeded circle, mu_out
+    outside, decided per element at the element centroid;
+  * steady two-phase Stokes (Sec. 3.4.3): viscosity contrast on the same
+    inclusion, body force a seeded smooth field of a few Fourier modes.
 
 Right-hand sides: the paper draws the coefficients of b independently at
 random (Sec. 2.4, footnote to Eq. (eta)); here they are N(0,1) per coefficient,
@@ -54,7 +56,12 @@ POISSON3D_48_P3 = Workload("poisson3d_n48_p3_sai1", 3, 48, 3, "sai", 3, 3)
 INTERFACE2D_256_P3 = Workload("interface2d_n256_p3_sai1_circle1e4", 2, 256, 3, "sai", 3, 3,
                               mu="circle", mu_in=1e4, mu_seed=0, nrhs=64)
 
-WORKLOADS = {w.name: w for w in (POISSON2D_16_P2, POISSON3D_48_P3, INTERFACE2D_256_P3)}
+# 2D steady two-phase Stokes, 128^2, p=2 (27 dofs/element: u, v, p), viscosity 1 / 1e3
+# on the square inclusion, 8-mode Fourier body force, Stokes-balanced SAI1, GMRES.
+STOKES2D_128_P2 = Workload("stokes2d_n128_p2_sai1_square1e3", 2, 128, 2, "sai", 3, 3, mu="square", mu_in=1e3,
+                           tol=1e-10, extra={"gamma": 1, "force_modes": 8, "force_seed": 0})
+
+WORKLOADS = {w.name: w for w in (POISSON2D_16_P2, POISSON3D_48_P3, INTERFACE2D_256_P3, STOKES2D_128_P2)}
 
 
 def circle_mu(dim: int, n: int, seed: int, mu_in: float = 1e4, mu_out: float = 1.0) -> np.ndarray:
@@ -109,3 +116,63 @@ def random_rhs(N: int, b: int, nrhs: int = 1, seed: int = 0) -> np.ndarray:
 def random_vector(size: int, seed: int) -> np.ndarray:
     """Generic N(0,1) test vector (operator-apply parity inputs)."""
     return np.random.default_rng(seed).standard_normal(size)
+
+
+def fourier_force_rhs(dim: int, n: int, p: int, seed: int, nmodes: int = 8) -> np.ndarray:
+    """Stokes right-hand side with a smooth seeded body force.
+
+    Each velocity component f_a(x) = sum_{m < nmodes} c_m sin(2 pi k_m . x + phi_m)
+    with integer wave vectors k_m, |k_m|_inf in 1..3 (so f_a has zero mean on
+    the periodic cell), c_m ~ N(0, 1), phi_m ~ U[0, 2 pi).  The value at each
+    element centroid is written into the element's constant mode (mode 0) of
+    that velocity field; all other modes and the pressure field are zero.
+    Layout: N blocks of (dim + 1) * (p + 1)^dim values, fields u_1..u_dim, p.
+    """
+    rng = np.random.default_rng(seed)
+    bs = (p + 1) ** dim
+    nf = dim + 1
+    N = n ** dim
+    c1 = (np.arange(n) + 0.5) / n
+    grids = np.meshgrid(*([c1] * dim), indexing="ij")
+    grids = [np.transpose(g, tuple(range(dim - 1, -1, -1))).reshape(-1) for g in grids]
+    out = np.zeros((N, nf, bs))
+    for a in range(dim):
+        field_a = np.zeros(N)
+        for _ in range(nmodes):
+            k = rng.integers(-3, 4, size=dim)
+            while not np.any(k):
+                k = rng.integers(-3, 4, size=dim)
+            amp = rng.standard_normal()
+            ph = rng.uniform(0.0, 2.0 * np.pi)
+            field_a += amp * np.sin(2.0 * np.pi * sum(k[t] * grids[t] for t in range(dim)) + ph)
+        out[:, a, 0] = field_a
+    return out.reshape(-1)
+
+
+def zero_mean_rhs(N: int, b: int, seed: int, nfields: int = 1) -> np.ndarray:
+    """N(0,1) coefficients (N blocks of nfields * b values) with the constant
+    mode of each field shifted to zero mean over the elements: the "N(0,1)
+    values projected to zero mean" of the workloads, consistent with the
+    periodic operators' constant kernel."""
+    v = np.random.default_rng(seed).standard_normal((N, nfields, b))
+    v[:, :, 0] -= v[:, :, 0].mean(axis=0)
+    return v.reshape(-1)
+
+
+def serving_requests(count: int, seed: int):
+    """Request mix of the serving workload: 2D Poisson or interface problems
+    (meshes 16^2..256^2, p = 1..4, interface contrast 1e2 or 1e4 on the
+    inclusion (1/4, 3/4)^2) and 3D Poisson (8^3..32^3, p = 1..3), drawn
+    uniformly per field.  Returns a list of dicts with dim, n, p, contrast
+    (1 = Poisson) and a right-hand-side seed."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        if rng.random() < 0.75:
+            dim, n, p = 2, int(rng.choice([16, 32, 64, 128, 256])), int(rng.integers(1, 5))
+            contrast = float(rng.choice([1.0, 1e2, 1e4]))
+        else:
+            dim, n, p = 3, int(rng.choice([8, 16, 32])), int(rng.integers(1, 4))
+            contrast = 1.0
+        out.append({"dim": dim, "n": n, "p": p, "contrast": contrast, "rhs_seed": int(rng.integers(1 << 31))})
+    return out

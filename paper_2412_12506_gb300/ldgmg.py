@@ -44,7 +44,33 @@ class SetupOpts(ctypes.Structure):
                 ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
                 ("pre_form", ctypes.c_int), ("post_form", ctypes.c_int),
                 ("vcycle_precision", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_rhs", ctypes.c_int),
-                ("outer_apply", ctypes.c_int)]
+                ("outer_apply", ctypes.c_int), ("krylov", ctypes.c_int), ("restart", ctypes.c_int),
+                ("zeta", ctypes.c_double)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("simulate", ctypes.c_int), ("simulate_solve_s", ctypes.c_double), ("setup", SetupOpts)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("p", ctypes.c_int), ("stokes", ctypes.c_int),
+                ("mu_host", ctypes.c_void_p), ("tau0", ctypes.c_double), ("taup", ctypes.c_double),
+                ("rhs_host", ctypes.c_void_p), ("x_host", ctypes.c_void_p), ("tol", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("relres", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("batch", ctypes.c_int), ("worker", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("builds", ctypes.c_uint64),
+                ("evictions", ctypes.c_uint64), ("build_failures", ctypes.c_uint64),
+                ("solve_calls", ctypes.c_uint64), ("max_batch_seen", ctypes.c_int),
+                ("classes_resident", ctypes.c_int), ("bytes_resident", ctypes.c_size_t),
+                ("bytes_peak", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t)]
 
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -52,7 +78,11 @@ _P = ctypes.POINTER
 _SIGS = {
     "ldgmg_default_opts": (None, [_P(SetupOpts)]),
     "ldgmg_assemble": (_i, [_P(Mesh), _i, _vp, _d, _P(_vp)]),
+    "ldgmg_assemble_stokes": (_i, [_P(Mesh), _i, _vp, _i, _d, _d, _P(_vp)]),
     "ldgmg_op_info": (_i, [_vp, _P(_i64), _P(_i), _P(_i64)]),
+    "ldgmg_op_fields": (_i, [_vp, _P(_i), _P(_i)]),
+    "ldgmg_op_device_bytes": (_i, [_vp, _P(ctypes.c_size_t)]),
+    "ldgmg_hier_device_bytes": (_i, [_vp, _P(ctypes.c_size_t)]),
     "ldgmg_apply": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ldgmg_project_kernel": (_i, [_vp, _vp, _i, _vp]),
     "ldgmg_setup": (_i, [_vp, _P(SetupOpts), _vp, _P(_vp)]),
@@ -72,10 +102,17 @@ _SIGS = {
     "ldgmg_kernel_launches": (ctypes.c_ulonglong, []),
     "ldgmg_project_kernel_noalloc": (_i, [_i64, _i, _vp, _vp]),
     "ldgmg_host_build": (_i, [_P(Mesh), _i, _vp, _d, _P(SetupOpts), _P(_vp)]),
+    "ldgmg_host_build_stokes": (_i, [_P(Mesh), _i, _vp, _i, _d, _d, _P(SetupOpts), _P(_vp)]),
     "ldgmg_host_level_info": (_i, [_vp, _i, _P(_i), _P(_i), _P(_i64), _P(_i), _P(_i64), _P(_i64),
                                    _P(_i64)]),
     "ldgmg_host_export": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "ldgmg_host_free": (None, [_vp]),
+    "ldgmg_server_create": (_i, [_P(ServerOpts), _P(_vp)]),
+    "ldgmg_server_submit": (_i, [_vp, _P(Request), _P(ctypes.c_uint64)]),
+    "ldgmg_server_wait": (_i, [_vp, ctypes.c_uint64, _P(Result)]),
+    "ldgmg_server_get_stats": (_i, [_vp, _P(ServerStats)]),
+    "ldgmg_server_clock": (_d, [_vp]),
+    "ldgmg_server_destroy": (None, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -106,10 +143,13 @@ def project_kernel_noalloc(v, N, b, stream=None):
 
 
 _OUTER = {"auto": 0, "fp64": 1, "df": 2}
+_KRYLOV = {"auto": 0, "cg": 1, "gmres": 2}
+TAUP = 0.05   # default Stokes pressure-penalty scale (tau_p = taup h / min mu)
 
 
 def make_opts(smoother="sai", sai_level=1, balance=True, nu1=3, nu2=3, omega=0.8, pre="B1", post="BT",
-              precision="fp64", max_iter=200, max_rhs=1, outer="auto") -> SetupOpts:
+              precision="fp64", max_iter=200, max_rhs=1, outer="auto", krylov="auto", restart=50,
+              zeta=0.0) -> SetupOpts:
     o = SetupOpts()
     _lib.ldgmg_default_opts(ctypes.byref(o))
     o.smoother = _SMOOTHER[smoother]
@@ -121,6 +161,9 @@ def make_opts(smoother="sai", sai_level=1, balance=True, nu1=3, nu2=3, omega=0.8
     o.max_iter = max_iter
     o.max_rhs = max_rhs
     o.outer_apply = _OUTER[outer]
+    o.krylov = _KRYLOV[krylov]
+    o.restart = restart
+    o.zeta = zeta
     return o
 
 
@@ -149,12 +192,17 @@ def _ptr(t):
 class HostHierarchy:
     """Host setup of ldgmg_setup without the device upload (include/ldgmg_host.h)."""
 
-    def __init__(self, dim, n, p, mu=None, tau0=1.0, **opts):
+    def __init__(self, dim, n, p, mu=None, tau0=1.0, stokes=None, taup=TAUP, **opts):
+        """stokes=None: scalar operator; stokes=0 / 1: Stokes standard / stress form."""
         keep, mp = _mu_ptr(mu)
         h = ctypes.c_void_p()
         o = make_opts(**opts)
-        _check(_lib.ldgmg_host_build(ctypes.byref(Mesh(dim, n, 1)), p, mp, tau0, ctypes.byref(o),
-                                     ctypes.byref(h)))
+        if stokes is None:
+            _check(_lib.ldgmg_host_build(ctypes.byref(Mesh(dim, n, 1)), p, mp, tau0, ctypes.byref(o),
+                                         ctypes.byref(h)))
+        else:
+            _check(_lib.ldgmg_host_build_stokes(ctypes.byref(Mesh(dim, n, 1)), p, mp, int(stokes), tau0, taup,
+                                                ctypes.byref(o), ctypes.byref(h)))
         self._h = h
         self.nlevels = self.info(0)["nlevels"]
 
@@ -189,18 +237,34 @@ class HostHierarchy:
 # ---------------------------------------------------------------------------
 
 class Operator:
-    """LDG operator A on the device (ldgmg_assemble)."""
+    """LDG operator A on the device: the scalar operator (ldgmg_assemble), or
+    with stokes=0 / 1 the Stokes saddle-point operator in standard / stress
+    form (ldgmg_assemble_stokes)."""
 
-    def __init__(self, dim, n, p, mu=None, tau0=1.0):
+    def __init__(self, dim, n, p, mu=None, tau0=1.0, stokes=None, taup=TAUP):
         keep, mp = _mu_ptr(mu)
         h = ctypes.c_void_p()
-        _check(_lib.ldgmg_assemble(ctypes.byref(Mesh(dim, n, 1)), p, mp, tau0, ctypes.byref(h)))
+        if stokes is None:
+            _check(_lib.ldgmg_assemble(ctypes.byref(Mesh(dim, n, 1)), p, mp, tau0, ctypes.byref(h)))
+        else:
+            _check(_lib.ldgmg_assemble_stokes(ctypes.byref(Mesh(dim, n, 1)), p, mp, int(stokes), tau0, taup,
+                                              ctypes.byref(h)))
         self._h = h
         N, b, nnz = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
         _check(_lib.ldgmg_op_info(h, ctypes.byref(N), ctypes.byref(b), ctypes.byref(nnz)))
+        nf, bs = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.ldgmg_op_fields(h, ctypes.byref(nf), ctypes.byref(bs)))
         self.dim, self.n, self.p = dim, n, p
         self.N, self.b, self.nnzb = N.value, b.value, nnz.value
+        self.nfields, self.field_b = nf.value, bs.value
+        self.stokes = stokes
         self.size = self.N * self.b
+
+    @property
+    def device_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _check(_lib.ldgmg_op_device_bytes(self._h, ctypes.byref(v)))
+        return v.value
 
     def _nrhs(self, t):
         n = t.numel() // self.size
@@ -238,6 +302,12 @@ class Hierarchy:
         self._h = h
         self.precision = opts.get("precision", "fp64")
         self.nlevels = self.info(0)["nlevels"]
+
+    @property
+    def device_bytes(self) -> int:
+        v = ctypes.c_size_t()
+        _check(_lib.ldgmg_hier_device_bytes(self._h, ctypes.byref(v)))
+        return v.value
 
     @property
     def vdtype(self):
@@ -347,3 +417,55 @@ def bsr_to_dense(rp, col, vals):
             j = col[z]
             D[i * b:(i + 1) * b, j * b:(j + 1) * b] += vals[z]
     return D
+
+
+# ---------------------------------------------------------------------------
+# serving engine (include/ldgmg_serve.h)
+# ---------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching solve server (ldgmg_server_*).  submit() copies the
+    inputs and returns a ticket; wait(ticket) returns (x, result dict)."""
+
+    def __init__(self, workers=4, max_batch=32, hbm_budget=0, simulate=False, simulate_solve_s=0.0, **opts):
+        o = ServerOpts()
+        o.hbm_budget, o.workers, o.max_batch = int(hbm_budget), workers, max_batch
+        o.simulate, o.simulate_solve_s = int(bool(simulate)), simulate_solve_s
+        o.setup = make_opts(**opts)
+        h = ctypes.c_void_p()
+        _check(_lib.ldgmg_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._live = {}
+
+    def submit(self, dim, n, p, rhs, mu=None, stokes=None, tau0=1.0, taup=TAUP, tol=1e-10):
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        x = np.zeros_like(rhs)
+        keep, mp = _mu_ptr(mu)
+        q = Request(dim, n, p, -1 if stokes is None else int(stokes), mp, tau0, taup,
+                    rhs.ctypes.data_as(_vp), x.ctypes.data_as(_vp), tol)
+        t = ctypes.c_uint64()
+        _check(_lib.ldgmg_server_submit(self._h, ctypes.byref(q), ctypes.byref(t)))
+        self._live[t.value] = x
+        return t.value
+
+    def wait(self, ticket):
+        r = Result()
+        _check(_lib.ldgmg_server_wait(self._h, ticket, ctypes.byref(r)))
+        x = self._live.pop(ticket)
+        return x, {k: getattr(r, k) for k, _ in Result._fields_}
+
+    def stats(self):
+        s = ServerStats()
+        _check(_lib.ldgmg_server_get_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def clock(self):
+        return _lib.ldgmg_server_clock(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ldgmg_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -130,3 +130,67 @@ def test_host_rejects_bad_arguments(lib):
         lib.HostHierarchy(2, 4, 1, mu=np.full(16, -1.0))
     with pytest.raises(lib.LdgmgError):
         lib.HostHierarchy(2, 4, 1, mu=np.full(16, np.nan))
+
+
+STOKES_CASES = [(2, 4, 1, 0, None), (2, 4, 2, 1, None), (2, 8, 2, 0, "circle"), (2, 6, 2, 1, "circle"),
+                (3, 2, 1, 0, None), (3, 4, 1, 1, None)]
+
+
+@pytest.mark.parametrize("d,n,p,gamma,mu_kind", STOKES_CASES)
+def test_host_stokes_operators_match_oracle(lib, d, n, p, gamma, mu_kind):
+    """Sec. 3.1 assembly and per-field coarsening: every level of the library's
+    Stokes hierarchy equals the oracle's, entry by entry and block pattern."""
+    from oracle import stokes as st
+    mu = circle_mu(d, n, seed=2, mu_in=1e3) if mu_kind else None
+    H = lib.HostHierarchy(d, n, p, mu, stokes=gamma, smoother="jacobi")
+    levels = st.build_stokes_levels(d, n, p, mu, gamma=gamma)
+    assert H.nlevels == len(levels)
+    for l, lv in enumerate(levels):
+        rp, col, vals = H.export(l, lib.MAT_A)
+        assert vals.shape[1] == (d + 1) * (p + 1) ** d
+        A = _dense(rp, col, vals)
+        Ao = lv.A.dense()
+        scale = np.abs(Ao).max()
+        assert np.abs(A - Ao).max() <= 1e-12 * scale, (l, np.abs(A - Ao).max() / scale)
+        assert np.array_equal(_pattern(rp, col, lv.op.N), lv.A.pat.toarray().astype(bool))
+
+
+@pytest.mark.parametrize("d,n,p,gamma,mu_kind", [(2, 8, 2, 0, None), (2, 4, 2, 1, None), (2, 8, 1, 1, "circle"),
+                                                 (3, 4, 1, 0, None)])
+def test_host_stokes_sai_matches_oracle(lib, d, n, p, gamma, mu_kind):
+    """Balanced Stokes SAI (Sec. 3.3, zeta of Table tab:zeta) equals the oracle's."""
+    from oracle import stokes as st
+    mu = circle_mu(d, n, seed=1, mu_in=1e3) if mu_kind else None
+    H = lib.HostHierarchy(d, n, p, mu, stokes=gamma, smoother="sai")
+    levels = st.build_stokes_levels(d, n, p, mu, gamma=gamma)
+    zeta = st.ZETA[(gamma, d)][p - 1]
+    for l, lv in enumerate(levels[:-1]):
+        alpha = st.stokes_alpha(lv.A, d, lv.op.bs, zeta)
+        sai = mg.SAI(lv.A, 1, alpha=alpha)
+        Bo = sai.B.dense()
+        rp, col, vals = H.export(l, lib.MAT_B)
+        B = _dense(rp, col, vals)
+        scale = np.abs(Bo).max()
+        assert np.abs(B - Bo).max() <= 1e-9 * scale, (l, np.abs(B - Bo).max() / scale)
+        assert np.array_equal(_pattern(rp, col, lv.op.N), sai.B.pat.toarray().astype(bool))
+        rpt, colt, valst = H.export(l, lib.MAT_BT)
+        assert np.array_equal(_dense(rpt, colt, valst), B.T)
+
+
+def test_host_stokes_jacobi_blocks_match_oracle(lib):
+    from oracle import stokes as st
+    H = lib.HostHierarchy(2, 8, 2, None, stokes=1, smoother="jacobi")
+    levels = st.build_stokes_levels(2, 8, 2, gamma=1)
+    for l, lv in enumerate(levels[:-1]):
+        jac = mg.Jacobi(lv.A)
+        _, _, vals = H.export(l, lib.MAT_D)
+        for i in range(lv.op.N):
+            ref = jac.Dinv[i]
+            assert np.abs(vals[i] - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_host_stokes_rejects_bad_arguments(lib):
+    with pytest.raises(lib.LdgmgError):
+        lib.HostHierarchy(2, 4, 1, stokes=2)
+    with pytest.raises(lib.LdgmgError):
+        lib.HostHierarchy(2, 4, 1, stokes=0, taup=-1.0)

@@ -251,3 +251,37 @@ def test_stokes_sai1_gmres_speed(gamma):
     x, it, hist = st.gmres(A.mat, V, b, tol=1e-10, max_iter=60)
     assert 0.4 <= krylov.eta(hist) <= 0.8, (it, krylov.eta(hist))
     assert np.linalg.norm(b - A.mat @ x) <= 1e-7 * np.linalg.norm(b)
+
+
+def test_fgmres_minimal_true_residual_over_preconditioned_space():
+    """FGMRES with a fixed linear V minimises ||b - A x|| over V K_k(A V, b)
+    (brute-force least squares) and reaches the solution."""
+    rng = np.random.default_rng(12)
+    n = 24
+    A = rng.standard_normal((n, n)) + 6 * np.eye(n)
+    Vm = np.eye(n) + 0.3 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    AV = A @ Vm
+    for k in range(1, 7):
+        x, it, hist = st.fgmres(A, lambda v: Vm @ v, b, tol=0.0, restart=50, max_iter=k)
+        Kb = np.empty((n, k))
+        v = b.copy()
+        for j in range(k):
+            Kb[:, j] = v
+            v = AV @ v
+        Qk, _ = np.linalg.qr(Kb)
+        y, *_ = np.linalg.lstsq(AV @ Qk, b, rcond=None)
+        best = np.linalg.norm(b - AV @ (Qk @ y))
+        got = np.linalg.norm(b - A @ x)
+        assert abs(got - best) <= 1e-10 * np.linalg.norm(b)
+        assert abs(hist[-1] - got) <= 1e-10 * np.linalg.norm(b)
+    # restarted: converges when A V has its field of values in the right half plane
+    A2 = rng.standard_normal((n, n)) + 12 * np.eye(n)
+    V2 = np.eye(n) + 0.05 * rng.standard_normal((n, n))
+    x, it, hist = st.fgmres(A2, lambda v: V2 @ v, b, tol=1e-12, restart=5, max_iter=400)
+    assert np.linalg.norm(b - A2 @ x) <= 1e-11 * np.linalg.norm(b)
+    assert all(hist[i + 1] <= hist[i] * (1 + 1e-12) for i in range(len(hist) - 1))
+    # with V = I both variants are plain GMRES and agree
+    x1, k1, h1 = st.gmres(A, lambda v: v, b, tol=1e-10, restart=50)
+    x2, k2, h2 = st.fgmres(A, lambda v: v, b, tol=1e-10, restart=50)
+    assert k1 == k2 and np.allclose(h1, h2, rtol=1e-10, atol=0)

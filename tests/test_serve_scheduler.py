@@ -1,0 +1,108 @@
+"""The serving engine's scheduler (include/ldgmg_serve.h) on the CPU.
+
+The server runs with simulate = 1: the real scheduler, builder and worker
+threads, class cache, admission, eviction and batching, with timed stand-ins
+for builds and solves (no device work, no results).  The GPU behaviour --
+real solves, alone-vs-mix equality -- is tested in test_gpu_serve.py.
+"""
+import numpy as np
+import pytest
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_12506_gb300 import ldgmg
+    return ldgmg
+
+
+def _rhs(dim, n, p, stokes=None):
+    b = (p + 1) ** dim * (1 if stokes is None else dim + 1)
+    return np.zeros(n ** dim * b)
+
+
+def test_all_requests_complete_and_batch_per_class(lib):
+    s = lib.Server(workers=2, max_batch=8, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.01,
+                   precision="fp32")
+    tickets = []
+    # b = 16 (2D p = 3) classes take batches; b = 9 (2D p = 2) and Stokes do not
+    for i in range(40):
+        if i % 3 == 0:
+            tickets.append(("batched", s.submit(2, 16, 3, _rhs(2, 16, 3))))
+        elif i % 3 == 1:
+            tickets.append(("single", s.submit(2, 16, 2, _rhs(2, 16, 2))))
+        else:
+            tickets.append(("stokes", s.submit(2, 8, 2, _rhs(2, 8, 2, 1), stokes=1)))
+    res = {kind: [] for kind in ("batched", "single", "stokes")}
+    for kind, t in tickets:
+        _, r = s.wait(t)
+        assert r["status"] == lib.OK and r["iters"] == 0 and np.isnan(r["relres"])
+        assert r["t_submit"] <= r["t_start"] <= r["t_end"]
+        res[kind].append(r)
+    st = s.stats()
+    assert st["submitted"] == st["completed"] == 40
+    assert st["builds"] == 3 and st["evictions"] == 0 and st["classes_resident"] == 3
+    assert all(r["batch"] == 1 for r in res["single"] + res["stokes"])
+    assert all(1 <= r["batch"] <= 8 for r in res["batched"])
+    assert max(r["batch"] for r in res["batched"]) > 1          # queued requests joined one call
+    assert st["solve_calls"] < 40
+    s.close()
+
+
+def test_admission_by_footprint_evicts_lru(lib):
+    # a budget that holds about one 2D 32^2 p = 2 class at a time
+    probe = lib.Server(workers=1, max_batch=1, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.0)
+    t = probe.submit(2, 32, 2, _rhs(2, 32, 2))
+    probe.wait(t)
+    one = probe.stats()["bytes_resident"]
+    probe.close()
+    budget = int(one * 1.5)
+    s = lib.Server(workers=1, max_batch=1, hbm_budget=budget, simulate=True, simulate_solve_s=0.002)
+    mus = [np.full(32 * 32, 1.0 + k) for k in range(4)]          # four classes of equal size
+    order = []
+    for rep in range(3):
+        for k in range(4):
+            order.append(s.submit(2, 32, 2, _rhs(2, 32, 2), mu=mus[k]))
+    for t in order:
+        _, r = s.wait(t)
+        assert r["status"] == lib.OK
+    st = s.stats()
+    assert st["completed"] == 12
+    assert st["bytes_peak"] <= budget
+    assert st["evictions"] >= 3 and st["builds"] == st["evictions"] + st["classes_resident"]
+    s.close()
+
+
+def test_fifo_across_classes_with_one_worker(lib):
+    s = lib.Server(workers=1, max_batch=1, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.003)
+    tickets = [s.submit(2, 8, 1 + (i % 3), _rhs(2, 8, 1 + (i % 3))) for i in range(15)]
+    starts = [s.wait(t)[1]["t_start"] for t in tickets]
+    assert starts == sorted(starts)
+    s.close()
+
+
+def test_oversized_class_is_admitted_alone(lib):
+    s = lib.Server(workers=1, max_batch=1, hbm_budget=1, simulate=True, simulate_solve_s=0.0)
+    t = s.submit(2, 16, 2, _rhs(2, 16, 2))
+    _, r = s.wait(t)
+    assert r["status"] == lib.OK
+    t2 = s.submit(2, 16, 1, _rhs(2, 16, 1))
+    _, r2 = s.wait(t2)
+    assert r2["status"] == lib.OK and s.stats()["evictions"] == 1
+    s.close()
+
+
+def test_bad_requests(lib):
+    s = lib.Server(workers=1, max_batch=1, hbm_budget=1 << 30, simulate=True)
+    with pytest.raises(lib.LdgmgError):
+        s.submit(4, 8, 1, np.zeros(10))
+    with pytest.raises(lib.LdgmgError):
+        s.submit(2, 8, 1, _rhs(2, 8, 1), stokes=3)
+    with pytest.raises(lib.LdgmgError):
+        s.submit(2, 8, 1, _rhs(2, 8, 1), tol=0.0)
+    with pytest.raises(lib.LdgmgError):
+        s.wait(12345)
+    s.close()
+    with pytest.raises(lib.LdgmgError):
+        lib.Server(workers=0, simulate=True)
+    with pytest.raises(lib.LdgmgError):
+        lib.Server(max_batch=65, simulate=True)
