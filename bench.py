@@ -44,7 +44,7 @@ METRIC = "1e-10 solves/s (mixed-precision V-cycle + FP64 CG)"
 # mean of 3 launches), scaled by rows to the launch timed here; valid only for
 # the kernel source it was taken on (sha256 prefix of bsr_apply.cu), else
 # reported as null.
-TRAFFIC_PER_ROW = {"fp16": (241.08e6 / 4096, "014095b3432c0255")}
+TRAFFIC_PER_ROW = {"fp16": (241.17e6 / 4096, "4dc1baae596e4602")}
 
 
 def kernel_source_hash():
@@ -74,6 +74,7 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=3)
     ap.add_argument("--stokes-n", type=int, default=128, help="0 disables the Stokes section")
     ap.add_argument("--stokes-steps", type=int, default=3)
+    ap.add_argument("--stokes-tol", type=float, default=1e-9)
     ap.add_argument("--serve-requests", type=int, default=10000, help="0 disables the serving section")
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-fp64-sample", type=int, default=200)
@@ -317,16 +318,22 @@ def run_stokes(args, ldgmg, torch, np, dev, stream, barrier):
     d, n, p, gamma = W.dim, args.stokes_n, W.p, W.extra["gamma"]
     t0 = time.time()
     op = ldgmg.Operator(d, n, p, square_mu(d, n, mu_in=W.mu_in), stokes=gamma)
-    H32 = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp32")
-    H64 = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp64")
+    # FGMRES stops on the true residual; 1e-10 lies below what FP64 reaches on
+    # this operator (~1e-9 with the 1e3 viscosity jump), so the mixed and FP64
+    # flexible solves both run to args.stokes_tol.  The paper's form (left
+    # GMRES, FP64 V, preconditioned residual 1e-10) is timed beside them.
+    H32 = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp32", krylov="fgmres")
+    H64 = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp64", krylov="fgmres")
+    HL = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp64", krylov="gmres")
     setup_s = time.time() - t0
     rhs = torch.tensor(fourier_force_rhs(d, n, p, W.extra["force_seed"], W.extra["force_modes"]),
                        dtype=torch.float64, device=dev)
     op.project_kernel(rhs)
 
-    def timed(H, steps):
+    def timed(H, steps, tol=None):
+        tol = args.stokes_tol if tol is None else tol
         x = torch.empty_like(rhs)
-        H.solve(rhs, args.tol, x=x)                      # warm-up
+        H.solve(rhs, tol, x=x)                           # warm-up
         torch.cuda.synchronize()
         barrier()
         ev, its = [], []
@@ -336,7 +343,7 @@ def run_stokes(args, ldgmg, torch, np, dev, stream, barrier):
         for _ in range(steps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, k, rr, _ = H.solve(rhs, args.tol, x=x)
+            _, k, rr, _ = H.solve(rhs, tol, x=x)
             e1.record(stream)
             ev.append((e0, e1))
             its.append((k, rr))
@@ -347,6 +354,7 @@ def run_stokes(args, ldgmg, torch, np, dev, stream, barrier):
 
     ms32, lat32, it32, x32, l32 = timed(H32, args.stokes_steps)
     ms64, lat64, it64, x64, _ = timed(H64, max(1, args.stokes_steps // 2))
+    msL, latL, itL, _, _ = timed(HL, max(1, args.stokes_steps // 2), tol=args.tol)
     xa = op.project_kernel(x32.clone())
     xb = op.project_kernel(x64.clone())
     err = float(torch.linalg.norm(xa - xb) / torch.linalg.norm(xb))
@@ -382,9 +390,16 @@ def run_stokes(args, ldgmg, torch, np, dev, stream, barrier):
         "latency_ms": {"p50": float(np.percentile(lat32, 50)), "p99": float(np.percentile(lat32, 99))},
         "iterations": sorted(set(k for k, _ in it32)), "final_relres": max(r for _, r in it32),
         "gpu_launches_per_solve": l32 / args.stokes_steps,
-        "krylov": "flexible GMRES(50) in FP64, FP32 V-cycle (balanced SAI1, zeta = 0.131)",
+        "krylov": f"FGMRES(50) in FP64 to a true relative residual of {args.stokes_tol:g}, FP32 V-cycle "
+                  "(balanced SAI1, zeta = 0.131)",
         "fp64": {"solves_per_s": len(lat64) / (ms64 / 1e3), "p50_ms": float(np.median(lat64)),
-                 "iterations": sorted(set(k for k, _ in it64)), "krylov": "left-preconditioned GMRES(50), FP64 V-cycle"},
+                 "iterations": sorted(set(k for k, _ in it64)), "final_relres": max(r for _, r in it64),
+                 "krylov": "FGMRES(50), FP64 V-cycle, same tolerance"},
+        "paper_form_fp64": {"solves_per_s": len(latL) / (msL / 1e3), "p50_ms": float(np.median(latL)),
+                            "iterations": sorted(set(k for k, _ in itL)),
+                            "true_relres": max(r for _, r in itL),
+                            "krylov": f"left-preconditioned GMRES(50), FP64 V-cycle, preconditioned residual "
+                                      f"{args.tol:g} (Sec. 3.4)"},
         "speedup_vs_fp64": (args.stokes_steps / (ms32 / 1e3)) / (len(lat64) / (ms64 / 1e3)),
         "rel_err_vs_fp64": err,
         "roofline": {"bound": "hbm", "kernel": "bsr_kernel<27, float> finest-level B apply",

@@ -54,12 +54,13 @@ typedef enum {
   LDGMG_EUNSUPPORTED = 6   /* valid request outside what this build implements */
 } ldgmg_status;
 
-enum { LDGMG_JACOBI = 0, LDGMG_SAI = 1 };                  /* smoother kind */
+enum { LDGMG_JACOBI = 0, LDGMG_SAI = 1, LDGMG_GS = 2 };   /* smoother kind */
 enum { LDGMG_FORM_B1 = 0, LDGMG_FORM_BT = 1 };            /* SAI smoother form, Eqs. B1 / BT */
 enum { LDGMG_FP64 = 0, LDGMG_FP32 = 1, LDGMG_BF16 = 2, LDGMG_FP16 = 3 };   /* V-cycle precision */
 enum { LDGMG_MAT_A = 0, LDGMG_MAT_B = 1, LDGMG_MAT_BT = 2, LDGMG_MAT_D = 3 }; /* level matrices */
 enum { LDGMG_OUTER_AUTO = 0, LDGMG_OUTER_FP64 = 1, LDGMG_OUTER_DF = 2 };  /* batched outer apply */
-enum { LDGMG_KRYLOV_AUTO = 0, LDGMG_KRYLOV_CG = 1, LDGMG_KRYLOV_GMRES = 2 }; /* outer Krylov method */
+enum { LDGMG_KRYLOV_AUTO = 0, LDGMG_KRYLOV_CG = 1, LDGMG_KRYLOV_GMRES = 2, LDGMG_KRYLOV_FGMRES = 3 };
+                                                          /* outer Krylov method */
 
 typedef struct {
   int dim;          /* 2 or 3 */
@@ -68,7 +69,10 @@ typedef struct {
 } ldgmg_mesh;
 
 typedef struct {
-  int smoother;          /* LDGMG_JACOBI (Sec. 2.3.1) or LDGMG_SAI (Sec. 2.3.3) */
+  int smoother;          /* LDGMG_JACOBI (Sec. 2.3.1), LDGMG_SAI (Sec. 2.3.3), or LDGMG_GS:
+                            multi-coloured block Gauss-Seidel, undamped, greedy colouring of
+                            A's block pattern (Sec. 2.3.2; pre_form / post_form B1 = forward,
+                            BT = backward colour order) */
   int sai_level;         /* ell: B has the block pattern of A^ell (Sec. 2.3.3); 0..2 */
   int balance;           /* 1: balanced SAI, alpha_i = ||A_ii||_F^{-1/2} (Sec. 2.3.3) */
   int nu1, nu2;          /* pre / post sweeps of Algorithm 1 (paper: 3 / 3, Sec. 2.2) */
@@ -79,10 +83,11 @@ typedef struct {
                             LDGMG_BF16, or LDGMG_FP16 (each level matrix scaled by a power of
                             two so its largest entry is in [2^14, 2^15)) */
   int max_iter;          /* Krylov iteration cap for ldgmg_solve */
-  int max_rhs;           /* right-hand sides per call, 1..128.  > 1 builds the batched
-                            hierarchy: b = 16 or 64, V-cycle block applies on tensor cores,
-                            vcycle_precision LDGMG_BF16 (BF16 blocks) or LDGMG_FP32 (FP32
-                            blocks split into two BF16 parts on the fly) */
+  int max_rhs;           /* right-hand sides per call, 1..128 (scalar operators; Stokes: 1).
+                            With b = 16 or 64, vcycle_precision LDGMG_BF16 (BF16 blocks) or
+                            LDGMG_FP32 (FP32 blocks split into two BF16 parts on the fly) and
+                            Jacobi or SAI, > 1 builds the batched tensor-core hierarchy; else
+                            the CUDA-core kernels run one grid row per right-hand side */
   int outer_apply;       /* operator apply of the outer CG of reduced-precision or batched
                             hierarchies with b = 16 or 64: LDGMG_OUTER_FP64, or
                             LDGMG_OUTER_DF = double-FP32 arithmetic (FP32 pairs, ~2^-44 of
@@ -91,8 +96,11 @@ typedef struct {
                             FP64 hierarchies always use FP64.  The final residual that
                             ldgmg_solve reports is always computed in FP64. */
   int krylov;            /* ldgmg_solve's method: LDGMG_KRYLOV_CG (SPD scalar problems),
-                            LDGMG_KRYLOV_GMRES (Stokes: A and V are symmetric indefinite,
-                            Sec. 3.4), or LDGMG_KRYLOV_AUTO = GMRES for Stokes, else CG */
+                            LDGMG_KRYLOV_GMRES (left preconditioned, the paper's form; Stokes:
+                            A and V are symmetric indefinite, Sec. 3.4), LDGMG_KRYLOV_FGMRES
+                            (flexible, right preconditioned, stops on the true residual), or
+                            LDGMG_KRYLOV_AUTO = CG for scalar operators; for Stokes GMRES with
+                            an FP64 V-cycle and FGMRES with a reduced-precision one */
   int restart;           /* GMRES restart length m, 1..200 (Krylov vectors kept on the device) */
   double zeta;           /* Stokes SAI balancing (Sec. 3.3); <= 0 takes Table tab:zeta for
                             (gamma, dim, p), 0.1 where the table has no entry */
@@ -194,11 +202,14 @@ ldgmg_status ldgmg_vcycle(ldgmg_hier* h, const double* b_dev, double* x_dev, int
  * nrhs <= max_rhs stacked right-hand sides at once (batched hierarchy when
  * nrhs > 1).  GMRES (Stokes, Sec. 3.4; nrhs = 1; restarted every `restart`
  * steps, modified Gram-Schmidt Arnoldi, Givens rotations, FP64 Krylov
- * vectors): with an FP64 V-cycle it is left preconditioned as in the paper and
- * stops when ||V (rhs - A x)||_2 <= tol ||V rhs||_2; with a reduced-precision
- * V-cycle, which is not an exactly linear operator, it is the flexible
- * right-preconditioned variant (preconditioned directions kept) and stops
- * when ||rhs - A x||_2 <= tol ||rhs||_2.  Every right-hand side keeps
+ * vectors) is left preconditioned as in the paper and stops when
+ * ||V (rhs - A x)||_2 <= tol ||V rhs||_2; with a reduced-precision V-cycle
+ * (linear only to its rounding) that test is confirmed on the recomputed
+ * preconditioned residual and the iteration restarts from it when it fails.
+ * FGMRES (right preconditioned, preconditioned directions kept) stops when
+ * ||rhs - A x||_2 <= tol ||rhs||_2.  With a coefficient jump the two tests
+ * differ by orders of magnitude (V weights the residual by about 1/mu);
+ * relres always reports the true residual.  Every right-hand side keeps
  * its own CG scalars and stops updating once it has converged, so its result
  * is the same whether it is solved alone or in a batch.  rhs and x may be
  * device pointers or host pointers (pinned or pageable); host buffers are
@@ -215,19 +226,19 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
  * Level vectors are in the hierarchy's working type: double for an FP64
  * hierarchy, float for FP32/BF16.  All pointers are device pointers. */
 
-/* y = M x for M in {A_l, B_l, B_l^T, D_l} (LDGMG_MAT_*). */
+/* y = M x for M in {A_l, B_l, B_l^T, D_l} (LDGMG_MAT_*; D_l for Jacobi and Gauss-Seidel). */
 ldgmg_status ldgmg_level_apply(ldgmg_hier* h, int level, int which, const void* x_dev,
                                void* y_dev, void* stream);
 
 /* Batched block-row apply on level l: y = M x for nrhs right-hand sides, float
  * vectors laid out [element][rhs][mode] (N*b*nrhs floats).  On a batched
- * hierarchy (max_rhs > 1) this is the tensor-core kernel; otherwise the
- * CUDA-core kernel (FP32/BF16 hierarchies only).  nrhs <= 128. */
+ * tensor-core hierarchy (see max_rhs) this is the tensor-core kernel;
+ * otherwise the CUDA-core kernel (FP32/BF16/FP16 hierarchies).  nrhs <= 128. */
 ldgmg_status ldgmg_level_apply_batched(ldgmg_hier* h, int level, int which, int nrhs, const float* x_dev,
                                        float* y_dev, void* stream);
 
 /* One smoother sweep on level l (Eq. Jsmooth, Eq. B1 or Eq. BT by `form`;
- * Jacobi ignores form).  x_out may equal x_in.  x_is_zero != 0 treats x_in as
+ * Gauss-Seidel: forward / backward colour order; Jacobi ignores form).  x_out may equal x_in.  x_is_zero != 0 treats x_in as
  * zero without reading it (first pre-sweep of a coarse level). */
 ldgmg_status ldgmg_level_smooth(ldgmg_hier* h, int level, int form, const void* rhs_dev,
                                 const void* x_in_dev, void* x_out_dev, int x_is_zero,

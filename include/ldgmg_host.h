@@ -47,6 +47,11 @@ ldgmg_status ldgmg_host_level_info(const ldgmg_host_hier* h, int level, int* nle
 ldgmg_status ldgmg_host_export(const ldgmg_host_hier* h, int level, int which, int64_t* row_ptr,
                                int32_t* col, double* vals);
 
+/* Multi-coloured Gauss-Seidel hierarchies (smoother LDGMG_GS): the colour of
+ * every element of level l (colour: N ints, may be NULL) and the number of
+ * colours.  EINVAL on the bottom level or for other smoothers. */
+ldgmg_status ldgmg_host_colours(const ldgmg_host_hier* h, int level, int* colour, int* ncolours);
+
 void ldgmg_host_free(ldgmg_host_hier* h);
 
 #ifdef __cplusplus

@@ -14,11 +14,12 @@
  *     of a class that does not fit yet wait in its queue.
  *   - Continuous batching.  Worker threads, each with its own CUDA stream,
  *     take the oldest waiting class that is built and not running, and solve
- *     as many of its queued requests as one call takes: up to max_batch
- *     right-hand sides on classes with a batched (tensor-core) hierarchy
- *     (scalar operators with b = 16 or 64 and a reduced-precision V-cycle),
- *     one otherwise.  Requests that arrive while a class is running join its
- *     next call.  Different classes run concurrently on different streams.
+ *     as many of its queued requests as one call takes: for scalar operators
+ *     up to max_batch right-hand sides (fewer for large classes: at most 2^22
+ *     dofs per call), on the tensor cores where the hierarchy supports them;
+ *     one for Stokes (GMRES).  Requests that arrive while a class is running
+ *     join its next call.  Different classes run concurrently on different
+ *     streams.
  *   - Determinism.  Every right-hand side of a batched solve keeps its own
  *     Krylov scalars and its arithmetic does not depend on the other
  *     right-hand sides (ldgmg_solve), so a request's result is the same

@@ -202,6 +202,8 @@ class StokesVCycle(mg.VCycle):
         for lv in levels[:-1]:
             if smoother == "jacobi":
                 lv.smoother = mg.Jacobi(lv.A, omega)
+            elif smoother == "gs":
+                lv.smoother = mg.GaussSeidel(lv.A)
             else:
                 alpha = stokes_alpha(lv.A, lv.op.d, lv.op.bs, zeta)
                 lv.smoother = mg.SAI(lv.A, ell, balance=True, pre=pre, post=post, alpha=alpha)
@@ -311,7 +313,7 @@ def fgmres(A, V, b: np.ndarray, tol: float = 1e-10, restart: int = 50, max_iter:
                 break
         y = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
         x = x + Z[:, :j_done] @ y
-        if abs(g[j_done]) <= tol * beta0:
-            break
         r = b - apply_A(x)
+        if abs(g[j_done]) <= tol * beta0 and np.linalg.norm(r) <= tol * beta0:
+            break            # the estimate is confirmed on the true residual
     return x, k, hist

@@ -60,6 +60,7 @@ template <class TA, class TV> struct BsrArgs {
   int64_t es, rs;   // vector entry (element e, rhs r, mode c) at e*es + r*rs + c; rhs = blockIdx.y
   int R;            // right-hand sides (grid y dimension)
   double inv_scale; // 1 / storage scale of the matrix (exact power of two)
+  const int* rows;  // null: block rows 0..nrows-1; else the nrows block rows listed
 };
 
 template <int TEAM> __device__ __forceinline__ void team_sync() {
@@ -83,14 +84,16 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
   const int team = threadIdx.x / TEAM, lt = threadIdx.x % TEAM;
   const int g = lt / LPC, rl = lt % LPC;
   const bool active = g < G;
-  const int64_t row = int64_t(blockIdx.x) * TEAMS + team;
+  const int64_t t = int64_t(blockIdx.x) * TEAMS + team;     // team's position in the row range / list
+  const bool live = t < a.nrows;
+  const int64_t row = (a.rows && live) ? int64_t(a.rows[t]) : t;
   const int64_t roff = int64_t(blockIdx.y) * a.rs;
-  if (TEAM == 32 && row >= a.nrows) return;   // whole warp leaves together
+  if (TEAM == 32 && !live) return;            // whole warp leaves together
   TACC acc[VEC];
 #pragma unroll
   for (int v = 0; v < VEC; ++v) acc[v] = TACC(0);
 
-  if (row < a.nrows) {
+  if (live) {
     const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
     // stage the neighbour vectors of up to KMAX blocks, then stream those
     // blocks with no barrier in between (many loads in flight per thread)
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
     for (int v = 0; v < VEC; ++v) red[team][g][rl * VEC + v] = acc[v];
   }
   team_sync<TEAM>();
-  if (row < a.nrows && lt < B) {
+  if (live && lt < B) {
     TACC sum = TACC(0);
 #pragma unroll
     for (int gg = 0; gg < G; ++gg) sum += red[team][gg][lt];
@@ -149,18 +152,20 @@ bool block_size_supported(int b) {
 template <int B, class TA, class TV>
 static cudaError_t launch_bsr_b(const DevMat& M, const BsrArgs<TA, TV>& a, cudaStream_t st) {
   constexpr int TEAMS = (B > 32) ? 1 : 8;
-  if (M.nrows == 0) return cudaSuccess;
-  const int64_t grid = (M.nrows + TEAMS - 1) / TEAMS;
+  (void)M;
+  if (a.nrows == 0) return cudaSuccess;
+  const int64_t grid = (a.nrows + TEAMS - 1) / TEAMS;
   bsr_kernel<B, TA, TV><<<dim3(unsigned(grid), unsigned(a.R)), 256, 0, st>>>(a);
   return launched();
 }
 
 template <class TA, class TV>
-static cudaError_t launch_bsr_t(const DevMat& M, int mode, const void* x, const void* rhs,
-                                const void* xin, void* y, double s, int R, int64_t es, int64_t rs,
-                                cudaStream_t st) {
+static cudaError_t launch_bsr_t(const DevMat& M, const int* rows, int64_t count, int mode, const void* x,
+                                const void* rhs, const void* xin, void* y, double s, int R, int64_t es,
+                                int64_t rs, cudaStream_t st) {
   BsrArgs<TA, TV> a;
-  a.nrows = M.nrows;
+  a.nrows = rows ? count : M.nrows;
+  a.rows = rows;
   a.row_ptr = M.row_ptr;
   a.col = M.col;
   a.vals = static_cast<const TA*>(M.vals);
@@ -190,16 +195,28 @@ static cudaError_t launch_bsr_t(const DevMat& M, int mode, const void* x, const 
   }
 }
 
-cudaError_t bsr_apply_strided(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
-                              void* y, double s, int R, int64_t es, int64_t rs, cudaStream_t st) {
-  if (M.row_major || R < 1) return cudaErrorInvalidValue;
+static cudaError_t bsr_dispatch(const DevMat& M, const int* rows, int64_t count, int mode, const void* x,
+                                const void* rhs, const void* xin, void* y, double s, int R, int64_t es, int64_t rs,
+                                cudaStream_t st) {
+  if (M.row_major || R < 1 || count < 0) return cudaErrorInvalidValue;
   switch (M.prec) {
-    case P_FP64: return launch_bsr_t<double, double>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
-    case P_FP32: return launch_bsr_t<float, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
-    case P_BF16: return launch_bsr_t<bf16, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
-    case P_FP16: return launch_bsr_t<f16, float>(M, mode, x, rhs, xin, y, s, R, es, rs, st);
+    case P_FP64: return launch_bsr_t<double, double>(M, rows, count, mode, x, rhs, xin, y, s, R, es, rs, st);
+    case P_FP32: return launch_bsr_t<float, float>(M, rows, count, mode, x, rhs, xin, y, s, R, es, rs, st);
+    case P_BF16: return launch_bsr_t<bf16, float>(M, rows, count, mode, x, rhs, xin, y, s, R, es, rs, st);
+    case P_FP16: return launch_bsr_t<f16, float>(M, rows, count, mode, x, rhs, xin, y, s, R, es, rs, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t bsr_apply_strided(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
+                              void* y, double s, int R, int64_t es, int64_t rs, cudaStream_t st) {
+  return bsr_dispatch(M, nullptr, M.nrows, mode, x, rhs, xin, y, s, R, es, rs, st);
+}
+
+cudaError_t bsr_apply_rows(const DevMat& M, const int* rows, int64_t count, int mode, const void* x, const void* rhs,
+                           const void* xin, void* y, double s, int R, int64_t es, int64_t rs, cudaStream_t st) {
+  if (!rows) return cudaErrorInvalidValue;
+  return bsr_dispatch(M, rows, count, mode, x, rhs, xin, y, s, R, es, rs, st);
 }
 
 cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <string>
 #include <thread>
 #include <vector>
@@ -149,6 +150,8 @@ struct DevLevel {
   int64_t N = 0;
   int b = 0;
   DevMat A, S, ST;       // A_l; smoother matrix (B_l or D_l); B_l^T (SAI only)
+  int* crows = nullptr;  // Gauss-Seidel: element indices grouped by colour
+  std::vector<int64_t> cptr;   // colour c = crows[cptr[c] .. cptr[c+1])
   bool own_A = true;
   void* rhs = nullptr;   // level vectors, room for max_rhs right-hand sides
   void* x = nullptr;
@@ -173,16 +176,27 @@ struct ldgmg_hier {
   double *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *bvec = nullptr, *xvec = nullptr;
   double *scal = nullptr, *partials = nullptr;
   double *stage_rhs = nullptr, *stage_x = nullptr;
-  int* active = nullptr;         // device per-RHS flags
+  int* active = nullptr;         // device per-RHS CG state: active[Rmax], it[Rmax], flag[Rmax]
   int* err = nullptr;            // device flag set by bounded waits
   double* hscal = nullptr;       // pinned host mirror of per-RHS scalars
-  int* hactive = nullptr;        // pinned host mirror of the flags
+  int* hactive = nullptr;        // pinned host mirror of that state
   // GMRES (single right-hand side): Krylov basis Q (restart + 1 vectors),
   // preconditioned directions Z (flexible variant, restart vectors), device
   // Hessenberg column / coefficients, pinned host mirror
   bool gmres = false;
   double *gq = nullptr, *gz = nullptr, *gs = nullptr, *hgs = nullptr;
   size_t dev_bytes = 0;          // device memory held by this handle
+  // CUDA graphs of the V-cycle body and of chunks of CG iterations, per
+  // right-hand-side count: the first run of each runs eagerly (it also
+  // performs one-time kernel configuration), the second is captured, later
+  // ones replay it.
+  struct VGraph {
+    int uses = 0;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+  };
+  std::map<int, VGraph> graphs;  // by (what, R, chunk): see run_graphed
+  cudaStream_t cap_stream = nullptr;
 };
 
 static const HostLevel& host_level(const ldgmg_hier* h, int l) {
@@ -368,6 +382,7 @@ void ldgmg_hier_free(ldgmg_hier* h) {
     if (L.own_A) free_mat(L.A);
     free_mat(L.S);
     free_mat(L.ST);
+    cudaFree(L.crows);
     cudaFree(L.rhs);
     cudaFree(L.x);
     cudaFree(L.r);
@@ -381,6 +396,9 @@ void ldgmg_hier_free(ldgmg_hier* h) {
   cudaFree(h->gq);
   cudaFree(h->gz);
   cudaFree(h->gs);
+  for (auto& kv : h->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->hgs) cudaFreeHost(h->hgs);
   if (h->hscal) cudaFreeHost(h->hscal);
   if (h->hactive) cudaFreeHost(h->hactive);
@@ -488,22 +506,24 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   g_err.clear();
   if (!op || !o || !out) return fail(LDGMG_EINVAL, "null argument");
   *out = nullptr;
-  if (o->smoother != LDGMG_JACOBI && o->smoother != LDGMG_SAI) return fail(LDGMG_EINVAL, "smoother");
+  if (o->smoother != LDGMG_JACOBI && o->smoother != LDGMG_SAI && o->smoother != LDGMG_GS)
+    return fail(LDGMG_EINVAL, "smoother");
   if (o->nu1 < 0 || o->nu2 < 0 || o->nu1 > 64 || o->nu2 > 64) return fail(LDGMG_EINVAL, "nu1/nu2");
   if (o->vcycle_precision < 0 || o->vcycle_precision > 3) return fail(LDGMG_EINVAL, "precision");
   if (o->max_iter < 1) return fail(LDGMG_EINVAL, "max_iter");
   if (o->max_rhs < 1 || o->max_rhs > 128) return fail(LDGMG_EINVAL, "max_rhs must be in 1..128");
   if (o->outer_apply < 0 || o->outer_apply > 2) return fail(LDGMG_EINVAL, "outer_apply");
   if (o->smoother == LDGMG_JACOBI && !(o->omega > 0.0 && o->omega < 2.0)) return fail(LDGMG_EINVAL, "omega");
-  if (o->krylov < 0 || o->krylov > 2) return fail(LDGMG_EINVAL, "krylov");
+  if (o->krylov < 0 || o->krylov > 3) return fail(LDGMG_EINVAL, "krylov");
   if (o->restart < 1 || o->restart > 200) return fail(LDGMG_EINVAL, "restart must be in 1..200");
   if (!std::isfinite(o->zeta)) return fail(LDGMG_EINVAL, "zeta");
-  const bool batched = o->max_rhs > 1;
-  if (batched && op->host.nf > 1) return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 is implemented for scalar operators");
-  if (batched && o->vcycle_precision != LDGMG_BF16 && o->vcycle_precision != LDGMG_FP32)
-    return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 needs vcycle_precision LDGMG_BF16 or LDGMG_FP32 (tensor-core path)");
-  if (batched && !tc_block_size_supported(op->host.b))
-    return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 needs b = 16 or 64 (p = 3)");
+  // Several right-hand sides: the tensor-core hierarchy where it applies
+  // (b = 16 / 64, BF16 or FP32 blocks, Jacobi or SAI), else the CUDA-core
+  // kernels with one grid row per right-hand side.
+  const bool multi_rhs = o->max_rhs > 1;
+  if (multi_rhs && op->host.nf > 1) return fail(LDGMG_EUNSUPPORTED, "max_rhs > 1 is implemented for scalar operators");
+  const bool batched = multi_rhs && tc_block_size_supported(op->host.b) && o->smoother != LDGMG_GS &&
+                       (o->vcycle_precision == LDGMG_BF16 || o->vcycle_precision == LDGMG_FP32);
   cudaStream_t st = (cudaStream_t)stream;
   ldgmg_hier* h = new (std::nothrow) ldgmg_hier();
   if (!h) return fail(LDGMG_ENOMEM, "host allocation");
@@ -571,6 +591,15 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
       } else {
         s = upload(jacobi_pbsr(L), L.b, h->prec, rm, D.S, st);
       }
+      if (s == LDGMG_OK && o->smoother == LDGMG_GS) {
+        D.cptr = L.colour_ptr;
+        s = dalloc(&D.crows, L.colour_rows.size() * sizeof(int));
+        if (s == LDGMG_OK &&
+            cudaMemcpyAsync(D.crows, L.colour_rows.data(), L.colour_rows.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, st) != cudaSuccess)
+          s = fail(LDGMG_ECUDA, "colour rows copy");
+        if (s == LDGMG_OK && cudaStreamSynchronize(st) != cudaSuccess) s = fail(LDGMG_ECUDA, "colour rows sync");
+      }
     }
     const size_t vb = size_t(L.N) * L.b * h->vsz * h->Rmax;
     if (s == LDGMG_OK) s = dalloc((char**)&D.rhs, vb);
@@ -603,17 +632,18 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   }
   if (dalloc(&h->scal, size_t(kCgSlots) * h->Rmax * sizeof(double)) != LDGMG_OK ||
       dalloc(&h->partials, size_t(std::max(kDotBlocks, kBatchDotBlocks)) * h->Rmax * sizeof(double)) != LDGMG_OK ||
-      dalloc(&h->active, size_t(h->Rmax) * sizeof(int)) != LDGMG_OK || dalloc(&h->err, sizeof(int)) != LDGMG_OK)
+      dalloc(&h->active, 3 * size_t(h->Rmax) * sizeof(int)) != LDGMG_OK || dalloc(&h->err, sizeof(int)) != LDGMG_OK)
     return bail(LDGMG_ENOMEM);
   if (cudaMallocHost((void**)&h->hscal, size_t(kCgSlots) * h->Rmax * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost((void**)&h->hactive, size_t(h->Rmax) * sizeof(int)) != cudaSuccess)
+      cudaMallocHost((void**)&h->hactive, 3 * size_t(h->Rmax) * sizeof(int)) != cudaSuccess)
     return bail(fail(LDGMG_ENOMEM, "cudaMallocHost"));
-  h->gmres = o->krylov == LDGMG_KRYLOV_GMRES || (o->krylov == LDGMG_KRYLOV_AUTO && op->host.nf > 1);
+  h->gmres = o->krylov == LDGMG_KRYLOV_GMRES || o->krylov == LDGMG_KRYLOV_FGMRES ||
+             (o->krylov == LDGMG_KRYLOV_AUTO && op->host.nf > 1);
   if (h->gmres) {
     const size_t nv = size_t(L0.N) * L0.b * sizeof(double);
     const int m = o->restart;
-    if (dalloc(&h->gq, nv * (m + 1)) != LDGMG_OK ||
-        (h->prec != P_FP64 && dalloc(&h->gz, nv * m) != LDGMG_OK) ||
+    const bool flexible = o->krylov == LDGMG_KRYLOV_FGMRES || (o->krylov == LDGMG_KRYLOV_AUTO && h->prec != P_FP64);
+    if (dalloc(&h->gq, nv * (m + 1)) != LDGMG_OK || (flexible && dalloc(&h->gz, nv * m) != LDGMG_OK) ||
         dalloc(&h->gs, size_t(m + 2) * sizeof(double)) != LDGMG_OK)
       return bail(LDGMG_ENOMEM);
     if (cudaMallocHost((void**)&h->hgs, size_t(m + 2) * sizeof(double)) != cudaSuccess)
@@ -646,6 +676,30 @@ ldgmg_status ldgmg_hier_info(const ldgmg_hier* h, int level, int* nlevels, int* 
 static ldgmg_status smooth(ldgmg_hier* h, int l, int form, const void* rhs, const void* xin, void* xout,
                            bool x_zero, int R, cudaStream_t st) {
   DevLevel& D = h->lv[l];
+  if (h->o.smoother == LDGMG_GS) {
+    // Multi-coloured block Gauss-Seidel (Sec. 2.3.2), omega = 1: colour by
+    // colour, x_i += A_ii^{-1} (b_i - sum_j A_ij x_j) on that colour's rows
+    // (the residual kernel reads the newest x of the other colours); forward
+    // colour order for form B1, backward for BT.  CUDA-core kernels only.
+    const int64_t b = D.b;
+    const int64_t es = R * b, rs = b;
+    const size_t bytes = size_t(D.N) * b * h->vsz * R;
+    if (x_zero) CK(cudaMemsetAsync(xout, 0, bytes, st));
+    else if (xin != xout) CK(cudaMemcpyAsync(xout, xin, bytes, cudaMemcpyDeviceToDevice, st));
+    const int nc = int(D.cptr.size()) - 1;
+    for (int k = 0; k < nc; ++k) {
+      const int c = form == LDGMG_FORM_BT ? nc - 1 - k : k;
+      const int* rows = D.crows + D.cptr[c];
+      const int64_t cnt = D.cptr[c + 1] - D.cptr[c];
+      if (x_zero && k == 0) {        // x = 0: the first colour's residual is b itself
+        CK(bsr_apply_rows(D.S, rows, cnt, M_SCALE, rhs, nullptr, nullptr, xout, 1.0, R, es, rs, st));
+        continue;
+      }
+      CK(bsr_apply_rows(D.A, rows, cnt, M_RES, xout, rhs, nullptr, D.r, 1.0, R, es, rs, st));
+      CK(bsr_apply_rows(D.S, rows, cnt, M_AXPY, D.r, nullptr, xout, xout, 1.0, R, es, rs, st));
+    }
+    return LDGMG_OK;
+  }
   if (h->o.smoother == LDGMG_JACOBI) {
     // Eq. Jsmooth written as x + omega D^{-1} (b - A x)
     if (x_zero) {
@@ -702,13 +756,71 @@ static ldgmg_status vcycle_level(ldgmg_hier* h, int l, int R, cudaStream_t st) {
   return LDGMG_OK;
 }
 
-// x = V b on R right-hand sides, FP64 device vectors [element][rhs][mode]
-static ldgmg_status apply_V(ldgmg_hier* h, const double* b, double* x, int R, cudaStream_t st) {
+}  // extern "C"
+
+// Runs fn(stream) eagerly the first time `key` is seen, captures it into a
+// CUDA graph the second time (on a private stream in thread-local capture
+// mode, ordered after the work already queued on st), and replays the graph
+// on st from then on.  fn must only enqueue work on the stream it is given
+// and only touch buffers owned by the hierarchy.
+template <class Fn>
+static ldgmg_status run_graphed(ldgmg_hier* h, int key, cudaStream_t st, Fn fn) {
+  auto& g = h->graphs[key];
+  if (g.exec) {
+    CK(cudaGraphLaunch(g.exec, st));
+    CK(launched(g.kernels));
+    return LDGMG_OK;
+  }
+  if (g.uses++ == 0) return fn(st);
+  if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(ev, st));
+  CK(cudaStreamWaitEvent(h->cap_stream, ev, 0));
+  CK(cudaEventDestroy(ev));
+  const unsigned long long k0 = launches();
+  CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  ldgmg_status s = fn(h->cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &graph);
+  if (s != LDGMG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return fail(LDGMG_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g.exec = nullptr;
+    return fail(LDGMG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  g.kernels = int(launches() - k0);
+  launched(-g.kernels);      // captured, not yet run
+  CK(cudaGraphLaunch(g.exec, st));
+  CK(launched(g.kernels));
+  return LDGMG_OK;
+}
+
+extern "C" {
+
+enum { G_VCYCLE = 1, G_CG = 2 };
+static int graph_key(int what, int R, int chunk) { return (what << 24) | (R << 8) | chunk; }
+
+// The V-cycle body on level 0's own buffers (lv[0].rhs -> lv[0].x)
+static ldgmg_status vcycle_body(ldgmg_hier* h, int R, cudaStream_t st) {
+  return run_graphed(h, graph_key(G_VCYCLE, R, 0), st, [&](cudaStream_t s) { return vcycle_level(h, 0, R, s); });
+}
+
+// x = V b on R right-hand sides, FP64 device vectors [element][rhs][mode];
+// graphed = false inlines the V-cycle kernels (inside a larger capture).
+static ldgmg_status apply_V(ldgmg_hier* h, const double* b, double* x, int R, cudaStream_t st,
+                            bool graphed = true) {
   DevLevel& D = h->lv[0];
   const int64_t n = D.N * D.b * R;
   if (h->vprec == 0) CK(cudaMemcpyAsync(D.rhs, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   else CK(cast_d2f(n, b, (float*)D.rhs, st));
-  CKS(vcycle_level(h, 0, R, st));
+  if (graphed) CKS(vcycle_body(h, R, st));
+  else CKS(vcycle_level(h, 0, R, st));
   if (h->vprec == 0) CK(cudaMemcpyAsync(x, D.x, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   else CK(cast_f2d(n, (const float*)D.x, x, st));
   return LDGMG_OK;
@@ -759,16 +871,24 @@ static ldgmg_status read_slot(ldgmg_hier* h, int slot, int R, cudaStream_t st) {
 // the outer solver for the symmetric indefinite Stokes system (Sec. 3.4).
 // Arnoldi by modified Gram-Schmidt (dots and updates on the device, the
 // Hessenberg column read back once per step), Givens rotations and the
-// least-squares update on the host.  With an FP64 V-cycle it is left
-// preconditioned (solves V A x = V b, tests ||V(b - A x)|| <= tol ||V b||);
-// with a reduced-precision V-cycle it is the flexible right-preconditioned
-// form (x = sum y_j z_j with z_j = V q_j kept, tests ||b - A x|| <= tol ||b||).
+// least-squares update on the host.
+//   left (LDGMG_KRYLOV_GMRES, the paper's form): solves V A x = V b, stops when
+//     ||V (b - A x)|| <= tol ||V b||.  With a reduced-precision V-cycle, V is
+//     linear only to its rounding, so the Givens estimate is confirmed on the
+//     recomputed preconditioned residual (FP64 residual, then V) before
+//     stopping, and the iteration restarts from it otherwise: iterative
+//     refinement with GMRES as the inner solver.
+//   flexible (LDGMG_KRYLOV_FGMRES): right preconditioned with z_j = V q_j kept,
+//     x = sum y_j z_j, stops when ||b - A x|| <= tol ||b|| (confirmed on the
+//     recomputed true residual).
 static ldgmg_status gmres_solve(ldgmg_hier* h, const double* b, double* x, double tol, int* iters,
                                 cudaStream_t st) {
   const HostLevel& L0 = h->op->host;
   const int64_t n = L0.N * L0.b;
   const int m = h->o.restart;
-  const bool flexible = h->prec != P_FP64;
+  const bool flexible = h->o.krylov == LDGMG_KRYLOV_FGMRES ||
+                        (h->o.krylov == LDGMG_KRYLOV_AUTO && h->prec != P_FP64);
+  const bool exact_V = h->prec == P_FP64;
   double* Q = h->gq;
   auto q = [&](int i) { return Q + int64_t(i) * n; };
   auto zv = [&](int i) { return h->gz + int64_t(i) * n; };
@@ -844,15 +964,24 @@ static ldgmg_status gmres_solve(ldgmg_hier* h, const double* b, double* x, doubl
     }
     CK(cudaMemcpyAsync(h->gs, y.data(), size_t(jd) * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(vec_combine(n, jd, flexible ? h->gz : Q, n, h->gs, x, st));
-    if (std::fabs(g[jd]) <= tol * beta0) {
+    const bool estimate_met = std::fabs(g[jd]) <= tol * beta0;
+    if (estimate_met && !flexible && exact_V) {
       converged = true;
       break;
     }
-    // restart from the true (preconditioned) residual
+    // restart from the recomputed (preconditioned) residual.  Where the
+    // Arnoldi relation holds only to a rounding level above tol (a
+    // reduced-precision V in left GMRES; the rounding of A Z = Q H in the
+    // flexible form) a met estimate is confirmed here, and the iteration
+    // continues from this residual if it is not.
     CK(bsr_apply_strided(h->op->A, M_RES, x, b, nullptr, h->r, 1.0, 1, L0.b, 0, st));
     if (flexible) CK(cudaMemcpyAsync(q(0), h->r, size_t(n) * sizeof(double), cudaMemcpyDeviceToDevice, st));
     else CKS(apply_V(h, h->r, q(0), 1, st));
     CKS(norm2(q(0), &beta));
+    if (beta <= tol * beta0) {
+      converged = true;
+      break;
+    }
     if (!(beta > 0.0)) {
       converged = beta == 0.0;
       break;
@@ -886,8 +1015,8 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     CK(stack_to_batch(N, R, int(bsz), src, h->bvec, st));
     b = h->bvec;
   }
-  double* xd = (R > 1) ? h->xvec : (host_x ? h->stage_x : x);
   if (h->gmres) {
+    double* xd = host_x ? h->stage_x : x;
     if (R != 1) return fail(LDGMG_EUNSUPPORTED, "GMRES solves take one right-hand side per call");
     int it = 0;
     double bn = 0.0;
@@ -908,6 +1037,9 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     if (result != LDGMG_OK) g_err = msg;
     return result;
   }
+  // CG.  The iterate lives in h->xvec (a fixed address, so chunks of
+  // iterations can be replayed as CUDA graphs) and is copied out at the end.
+  double* xg = h->xvec;
   const bool flexible = h->prec != P_FP64;
   double* S = h->scal;
   auto slot = [&](int s) { return S + size_t(s) * R; };
@@ -917,17 +1049,23 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
   std::vector<double> bb(hslot(S_BB), hslot(S_BB) + R);
   for (double v : bb)
     if (!std::isfinite(v)) return fail(LDGMG_EINVAL, "rhs contains NaN or Inf");
-  std::vector<int> it(R, 0);
-  std::vector<int> act(R);
+  // device state: active[R], it[R], flag[R] (one D2H copy per chunk)
+  int* dact = h->active;
+  int* dit = h->active + R;
+  int* dflag = h->active + 2 * R;
   int nact = 0;
   for (int r = 0; r < R; ++r) {
-    act[r] = bb[r] > 0.0;
-    nact += act[r];
+    h->hactive[r] = bb[r] > 0.0;
+    h->hactive[R + r] = 0;
+    h->hactive[2 * R + r] = 0;
+    nact += h->hactive[r];
+    h->hscal[S_TOL2 * R + r] = tol * tol;
   }
-  for (int r = 0; r < R; ++r) h->hactive[r] = act[r];
-  CK(cudaMemcpyAsync(h->active, h->hactive, R * sizeof(int), cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(xd, 0, nb, st));
+  CK(cudaMemcpyAsync(h->active, h->hactive, 3 * R * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(slot(S_TOL2), hslot(S_TOL2), R * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(xg, 0, nb, st));
   ldgmg_status result = LDGMG_OK;
+  std::vector<int> it(R, 0);
   int k = 0;
   if (nact > 0) {
     CK(cudaMemcpyAsync(h->r, b, nb, cudaMemcpyDeviceToDevice, st));
@@ -937,49 +1075,56 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     // Batched hierarchies apply A once per block row for all right-hand sides,
     // in double-FP32 (use_df) or FP64.  The arithmetic of each right-hand side
     // does not depend on R, so a right-hand side solved alone matches the batch.
-    const bool multi = h->batched && R <= 64;
+    // Multi-RHS hierarchies use the same outer apply for every R (so each
+    // right-hand side is bitwise the same alone and batched): the block-reuse
+    // kernels for b = 16 / 64, else the CUDA-core kernel.
+    const bool multi = (h->batched || h->Rmax > 1) && R <= 64 && tc_block_size_supported(int(bsz));
+    // One CG iteration (Sec. 2.2).  The stopping test runs on the device right
+    // after the residual norms (cg_check_b), so a converged right-hand side is
+    // frozen (alpha = beta = 0) at the same iteration as with a host test, and
+    // several iterations can run between host reads; work after the last
+    // right-hand side converged changes nothing.
+    auto body = [&](cudaStream_t s) -> ldgmg_status {
+      if (multi && h->use_df) CK(bsr_apply_df(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, R, s));
+      else if (multi) CK(bsr_apply_multi64(h->op->A, M_Y, h->p, nullptr, h->q, R, s));
+      else if (h->use_df && R == 1) CK(bsr_apply_df1(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, s));
+      else CK(bsr_apply_strided(h->op->A, M_Y, h->p, nullptr, nullptr, h->q, 1.0, R, R * bsz, bsz, s));
+      CK(dot_batched(N, R, int(bsz), h->p, h->q, h->partials, slot(S_PQ), s));
+      CK(cg_alpha_b(R, S, dact, s));
+      CK(cg_update_xr_b(N, R, int(bsz), xg, h->r, h->p, h->q, S, s));
+      CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_RR), s));
+      CK(cg_check_b(R, S, dact, dit, dflag, s));
+      if (flexible) CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZOLD), s));
+      CKS(apply_V(h, h->r, h->z, R, s, false));
+      CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZNEW), s));
+      CK(cg_beta_b(R, S, dact, flexible ? 1 : 0, s));
+      CK(cg_update_p_b(N, R, int(bsz), h->p, h->z, S, s));
+      return LDGMG_OK;
+    };
+    // Chunk length: one iteration per host check for large solves (an extra
+    // iteration after convergence would cost real time), four for small ones
+    // (launch and synchronisation bound).
+    const int chunk = n >= (int64_t(1) << 19) ? 1 : 4;
     while (nact > 0 && k < h->o.max_iter) {
-      if (multi && h->use_df) CK(bsr_apply_df(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, R, st));
-      else if (multi) CK(bsr_apply_multi64(h->op->A, M_Y, h->p, nullptr, h->q, R, st));
-      else if (h->use_df && R == 1) CK(bsr_apply_df1(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, st));
-      else CK(bsr_apply_strided(h->op->A, M_Y, h->p, nullptr, nullptr, h->q, 1.0, R, R * bsz, bsz, st));
-      CK(dot_batched(N, R, int(bsz), h->p, h->q, h->partials, slot(S_PQ), st));
-      CK(cg_alpha_b(R, S, h->active, st));
-      CK(cg_update_xr_b(N, R, int(bsz), xd, h->r, h->p, h->q, S, st));
-      CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_RR), st));
-      ++k;
-      CKS(read_slot(h, S_RR, R, st));
-      bool changed = false;
+      const int c = std::min(chunk, h->o.max_iter - k);
+      CKS(run_graphed(h, graph_key(G_CG, R, c), st, [&](cudaStream_t s) -> ldgmg_status {
+        for (int i = 0; i < c; ++i) CKS(body(s));
+        return LDGMG_OK;
+      }));
+      k += c;
+      CK(cudaMemcpyAsync(h->hactive, h->active, 3 * R * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      nact = 0;
       for (int r = 0; r < R; ++r) {
-        if (!act[r]) continue;
-        it[r] = k;
-        const double rr = hslot(S_RR)[r];
-        if (!std::isfinite(rr)) {
+        nact += h->hactive[r];
+        it[r] = h->hactive[R + r];
+        if (h->hactive[2 * R + r] && result == LDGMG_OK)
           result = fail(LDGMG_ENOTCONV, "CG breakdown (non-finite residual)");
-          act[r] = 0;
-          changed = true;
-        } else if (rr <= tol * tol * bb[r]) {
-          act[r] = 0;
-          changed = true;
-        }
       }
-      if (changed) {
-        nact = 0;
-        for (int r = 0; r < R; ++r) {
-          h->hactive[r] = act[r];
-          nact += act[r];
-        }
-        CK(cudaMemcpyAsync(h->active, h->hactive, R * sizeof(int), cudaMemcpyHostToDevice, st));
-      }
-      if (nact == 0) break;
-      if (flexible) CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZOLD), st));
-      CKS(apply_V(h, h->r, h->z, R, st));
-      CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZNEW), st));
-      CK(cg_beta_b(R, S, h->active, flexible ? 1 : 0, st));
-      CK(cg_update_p_b(N, R, int(bsz), h->p, h->z, S, st));
     }
     if (nact > 0 && result == LDGMG_OK) result = fail(LDGMG_ENOTCONV, "max_iter reached");
   }
+  double* xd = xg;
   // true residual of the returned iterates
   CK(bsr_apply_strided(h->op->A, M_RES, xd, b, nullptr, h->r, 1.0, R, R * bsz, bsz, st));
   CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_TMP), st));
@@ -988,8 +1133,8 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     double* dst = host_x ? h->stage_x : x;
     CK(batch_to_stack(N, R, int(bsz), xd, dst, st));
     if (host_x) CK(cudaMemcpyAsync(x, h->stage_x, nb, cudaMemcpyDeviceToHost, st));
-  } else if (host_x) {
-    CK(cudaMemcpyAsync(x, xd, nb, cudaMemcpyDeviceToHost, st));
+  } else {
+    CK(cudaMemcpyAsync(x, xd, nb, host_x ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
   }
   CK(cudaStreamSynchronize(st));
   for (int r = 0; r < R; ++r) {
@@ -1017,7 +1162,7 @@ static ldgmg_status check_level(ldgmg_hier* h, int l, bool need_smoother) {
 static const DevMat* level_mat(ldgmg_hier* h, int l, int which) {
   const DevLevel& D = h->lv[l];
   if (which == LDGMG_MAT_A) return &D.A;
-  if (which == LDGMG_MAT_D && h->o.smoother == LDGMG_JACOBI) return &D.S;
+  if (which == LDGMG_MAT_D && (h->o.smoother == LDGMG_JACOBI || h->o.smoother == LDGMG_GS)) return &D.S;
   if (which == LDGMG_MAT_B && h->o.smoother == LDGMG_SAI) return &D.S;
   if (which == LDGMG_MAT_BT && h->o.smoother == LDGMG_SAI) return &D.ST;
   return nullptr;

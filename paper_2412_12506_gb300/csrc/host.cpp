@@ -995,11 +995,51 @@ static void parallel_for(int64_t n, int nthreads, F&& f) {
 // Smoothers (Sec. 2.3)
 // --------------------------------------------------------------------------
 
+std::vector<int> greedy_colouring(const PBSR& A) {
+  const int64_t N = A.nrows;
+  std::vector<std::vector<int32_t>> nb(N);
+  for (int64_t i = 0; i < N; ++i)
+    for (int64_t z = A.row_ptr[i]; z < A.row_ptr[i + 1]; ++z) {
+      const int32_t j = A.col[z];
+      if (j == i) continue;
+      nb[i].push_back(j);
+      nb[j].push_back(int32_t(i));
+    }
+  std::vector<int> colour(N, -1);
+  std::vector<char> used;
+  for (int64_t i = 0; i < N; ++i) {
+    used.assign(nb[i].size() + 2, 0);
+    for (int32_t j : nb[i])
+      if (colour[j] >= 0 && colour[j] < int(used.size())) used[colour[j]] = 1;
+    int c = 0;
+    while (used[c]) ++c;
+    colour[i] = c;
+  }
+  return colour;
+}
+
 std::string setup_smoother(HostLevel& L, const SetupParams& sp, int nthreads) {
   const int b = L.b;
   const size_t bb = size_t(b) * b;
   const int64_t N = L.N;
   const PBSR& A = L.A;
+  if (sp.smoother == 2) {
+    // multi-coloured Gauss-Seidel: the Jacobi blocks plus the colour classes
+    SetupParams jp = sp;
+    jp.smoother = 0;
+    std::string err = setup_smoother(L, jp, nthreads);
+    if (!err.empty()) return err;
+    const std::vector<int> colour = greedy_colouring(A);
+    int nc = 0;
+    for (int c : colour) nc = std::max(nc, c + 1);
+    L.colour_ptr.assign(nc + 1, 0);
+    for (int c : colour) L.colour_ptr[c + 1]++;
+    for (int c = 0; c < nc; ++c) L.colour_ptr[c + 1] += L.colour_ptr[c];
+    L.colour_rows.assign(N, 0);
+    std::vector<int64_t> fill(L.colour_ptr.begin(), L.colour_ptr.end() - 1);
+    for (int64_t i = 0; i < N; ++i) L.colour_rows[fill[colour[i]]++] = int32_t(i);
+    return "";
+  }
   if (sp.smoother == 0) {
     // block Jacobi: pseudo-inverse of A_ii from a symmetric eigendecomposition (Eq. Jsmooth)
     L.dinv_pool = Pool();

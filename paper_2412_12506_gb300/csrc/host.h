@@ -67,12 +67,16 @@ struct HostLevel {
   PBSR A;
   // smoother
   PBSR B, BT;                      // SAI (BT holds the transposed blocks of B, row-wise)
-  std::vector<uint32_t> dinv;      // Jacobi: pseudo-inverse of A_ii per element
+  std::vector<uint32_t> dinv;      // Jacobi / Gauss-Seidel: pseudo-inverse of A_ii per element
   Pool dinv_pool;
+  // multi-coloured Gauss-Seidel: elements of colour c are
+  // colour_rows[colour_ptr[c] .. colour_ptr[c+1]), increasing
+  std::vector<int32_t> colour_rows;
+  std::vector<int64_t> colour_ptr;
 };
 
 struct SetupParams {
-  int smoother = 1;                // 0 Jacobi, 1 SAI
+  int smoother = 1;                // 0 Jacobi, 1 SAI, 2 multi-coloured Gauss-Seidel
   int sai_level = 1;
   int balance = 1;
   double zeta = 0.0;               // Stokes balancing (Sec. 3.3); <= 0: Table tab:zeta
@@ -100,7 +104,12 @@ std::string coarsen(const HostLevel& fine, HostLevel& coarse);
 // to `out` (which must not alias `fine`).
 std::string build_coarse_levels(const HostLevel& fine, std::vector<HostLevel>& out);
 
-// Smoother setup on one level (Jacobi blocks or balanced SAI, Sec. 2.3).
+// Greedy colouring of the (symmetrised) block pattern of A in element order
+// (Sec. 2.3.2): colour of each element; red-black on the 5 / 7-point stencil.
+std::vector<int> greedy_colouring(const PBSR& A);
+
+// Smoother setup on one level (Jacobi blocks, Gauss-Seidel blocks and
+// colours, or balanced SAI, Sec. 2.3).
 std::string setup_smoother(HostLevel& L, const SetupParams& sp, int nthreads);
 
 // Dense copy of A (row-major, (N*b)^2) for the bottom solver.

@@ -108,7 +108,7 @@ ldgmg_status ldgmg_host_export(const ldgmg_host_hier* h, int l, int which, int64
   const int b = L.b;
   const size_t bb = size_t(b) * b;
   if (which == LDGMG_MAT_D) {
-    if (bottom || h->smoother != LDGMG_JACOBI) return herr(LDGMG_EINVAL, "no Jacobi blocks on this level");
+    if (bottom || h->smoother == LDGMG_SAI) return herr(LDGMG_EINVAL, "no Jacobi blocks on this level");
     for (int64_t i = 0; i < L.N; ++i) {
       if (row_ptr) row_ptr[i] = i;
       if (col) col[i] = int32_t(i);
@@ -126,6 +126,19 @@ ldgmg_status ldgmg_host_export(const ldgmg_host_hier* h, int l, int which, int64
   if (col) std::copy(M->col.begin(), M->col.end(), col);
   if (vals)
     for (int64_t z = 0; z < M->nnzb(); ++z) std::memcpy(vals + z * bb, M->pool.get(M->id[z]), bb * sizeof(double));
+  return LDGMG_OK;
+}
+
+ldgmg_status ldgmg_host_colours(const ldgmg_host_hier* h, int l, int* colour, int* ncolours) {
+  if (!h) return herr(LDGMG_EINVAL, "null handle");
+  if (l < 0 || l + 1 >= int(h->lv.size())) return herr(LDGMG_EINVAL, "level out of range or bottom level");
+  const HostLevel& L = h->lv[l];
+  if (h->smoother != LDGMG_GS || L.colour_ptr.empty()) return herr(LDGMG_EINVAL, "not a Gauss-Seidel hierarchy");
+  const int nc = int(L.colour_ptr.size()) - 1;
+  if (ncolours) *ncolours = nc;
+  if (colour)
+    for (int c = 0; c < nc; ++c)
+      for (int64_t k = L.colour_ptr[c]; k < L.colour_ptr[c + 1]; ++k) colour[L.colour_rows[k]] = c;
   return LDGMG_OK;
 }
 

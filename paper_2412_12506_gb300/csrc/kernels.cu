@@ -477,6 +477,24 @@ __global__ void cg_update_p_b_kernel(int64_t n, int R, int b, double* p, const d
     p[i] = z[i] + s[S_BETA * R + (i / b) % R] * p[i];
 }
 
+__global__ void cg_check_b_kernel(int R, const double* s, int* active, int* it, int* flag) {
+  const int r = threadIdx.x + blockIdx.x * blockDim.x;
+  if (r >= R || !active[r]) return;
+  it[r] += 1;
+  const double rr = s[S_RR * R + r];
+  if (!isfinite(rr)) {
+    flag[r] = 1;
+    active[r] = 0;
+  } else if (rr <= s[S_TOL2 * R + r] * s[S_BB * R + r]) {
+    active[r] = 0;
+  }
+}
+
+cudaError_t cg_check_b(int R, const double* scal, int* active, int* it, int* flag, cudaStream_t st) {
+  cg_check_b_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, scal, active, it, flag);
+  return launched();
+}
+
 cudaError_t cg_alpha_b(int R, double* scal, const int* active, cudaStream_t st) {
   cg_alpha_b_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, scal, active);
   return launched();

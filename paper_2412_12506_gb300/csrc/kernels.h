@@ -43,6 +43,11 @@ cudaError_t bsr_apply(const DevMat& M, int mode, const void* x, const void* rhs,
 cudaError_t bsr_apply_strided(const DevMat& M, int mode, const void* x, const void* rhs, const void* xin,
                               void* y, double s, int R, int64_t es, int64_t rs, cudaStream_t st);
 
+// Same on the `count` block rows listed in `rows` (device int32; e.g. one
+// colour class of multi-coloured Gauss-Seidel); other rows of y are untouched.
+cudaError_t bsr_apply_rows(const DevMat& M, const int* rows, int64_t count, int mode, const void* x, const void* rhs,
+                           const void* xin, void* y, double s, int R, int64_t es, int64_t rs, cudaStream_t st);
+
 // Batched apply on tensor cores (tc_apply.cu): BF16 row-major blocks, FP32 vectors.
 struct BatchArgs {
   int64_t nrows;
@@ -118,7 +123,7 @@ cudaError_t dot_batched(int64_t N, int R, int b, const double* u, const double* 
 
 // CG scalar slots
 enum CgSlot { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZNEW = 3, S_RZOLD = 4, S_ALPHA = 5, S_BETA = 6,
-              S_BB = 7, S_TMP = 8, kCgSlots = 16 };
+              S_BB = 7, S_TMP = 8, S_TOL2 = 9, kCgSlots = 16 };
 cudaError_t cg_alpha(double* scal, cudaStream_t st);                    // alpha = rz / pq
 cudaError_t cg_update_xr(int64_t n, double* x, double* r, const double* p, const double* q,
                          const double* scal, cudaStream_t st);          // x += a p ; r -= a q
@@ -132,6 +137,10 @@ cudaError_t cg_update_xr_b(int64_t N, int R, int b, double* x, double* r, const 
 cudaError_t cg_beta_b(int R, double* scal, const int* active, int flexible, cudaStream_t st);
 cudaError_t cg_update_p_b(int64_t N, int R, int b, double* p, const double* z, const double* scal,
                           cudaStream_t st);
+// Device-side stopping test after the residual norms: for each active r,
+// it[r] += 1, then r stops when scal[S_RR] <= scal[S_TOL2] * scal[S_BB] (flag[r]
+// = 0) or when the norm is not finite (flag[r] = 1).
+cudaError_t cg_check_b(int R, const double* scal, int* active, int* it, int* flag, cudaStream_t st);
 // Double-FP32 operator apply (df_apply.cu): `pairs` holds A's FP64 entries as
 // (hi, lo) FP32 pairs in the layout of M (column-major blocks, b = 16 or 64);
 // x, rhs, y are FP64 [element][rhs][mode] with R <= 64 right-hand sides.

@@ -78,7 +78,7 @@ struct Class {
   ldgmg_status fail_status = LDGMG_OK;
   ldgmg_op* op = nullptr;
   ldgmg_hier* h = nullptr;
-  bool batched = false;
+  int rmax = 1;             // right-hand sides per solve call of this class
   bool busy = false;
   size_t est = 0, bytes = 0;
   double last_use = 0.0;
@@ -130,7 +130,7 @@ size_t estimate(const ldgmg_server_opts& o, const Class& c) {
   if (k.stokes == 1) per_row = d == 2 ? 7 : 13;   // stress form couples diagonal neighbours
   const int sai_rows = o.setup.sai_level == 2 ? (d == 2 ? 13 : 25) : per_row;
   const double es = double(esize(o.setup.vcycle_precision));
-  const int rmax = c.batched ? o.max_batch : 1;
+  const int rmax = c.rmax;
   const double vs = o.setup.vcycle_precision == LDGMG_FP64 ? 8.0 : 4.0;
   double total = 0.0;
   total += double(c.N) * per_row * b * b * 8.0 * 2.0;   // FP64 A (+ double-FP32 copy)
@@ -223,7 +223,7 @@ void plan(ldgmg_server* s) {
     if (!best) break;
     Job j;
     j.c = best;
-    const size_t cap = best->batched ? size_t(s->o.max_batch) : 1;
+    const size_t cap = size_t(best->rmax);
     const double tol = best->queue.front()->tol;
     while (!best->queue.empty() && j.reqs.size() < cap && best->queue.front()->tol == tol) {
       j.reqs.push_back(best->queue.front());
@@ -249,9 +249,8 @@ void builder_loop(ldgmg_server* s) {
     s->build_q.pop_front();
     const ClassKey k = c->key;
     const std::vector<double> mu = c->mu;
-    const bool batched = c->batched;
     ldgmg_setup_opts so = s->o.setup;
-    so.max_rhs = batched ? s->o.max_batch : 1;
+    so.max_rhs = c->rmax;
     const bool simulate = s->o.simulate != 0;
     lk.unlock();
     ldgmg_op* op = nullptr;
@@ -428,9 +427,11 @@ ldgmg_status ldgmg_server_submit(ldgmg_server* s, const ldgmg_request* q, uint64
     if (q->mu_host) c->mu.assign(q->mu_host, q->mu_host + N);
     c->b = b;
     c->N = N;
-    const int prec = s->o.setup.vcycle_precision;
-    c->batched = q->stokes < 0 && (b == 16 || b == 64) && (prec == LDGMG_FP32 || prec == LDGMG_BF16) &&
-                 s->o.max_batch > 1;
+    // Scalar classes take up to max_batch right-hand sides per call (tensor
+    // cores where the hierarchy supports them, else the CUDA-core kernels),
+    // capped so that a call holds at most 2^22 dofs; GMRES classes take one.
+    const int64_t cap = std::max<int64_t>(1, (int64_t(1) << 22) / (N * b));
+    c->rmax = q->stokes < 0 ? int(std::min<int64_t>(s->o.max_batch, cap)) : 1;
     it = s->classes.emplace(k, std::move(c)).first;
   }
   r->id = s->next_id++;

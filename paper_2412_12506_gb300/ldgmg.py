@@ -20,13 +20,13 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONV, ETIMEOUT, EUNSUPPORTED = range(7)
-JACOBI, SAI = 0, 1
+JACOBI, SAI, GS = 0, 1, 2
 FORM_B1, FORM_BT = 0, 1
 FP64, FP32, BF16, FP16 = 0, 1, 2, 3
 MAT_A, MAT_B, MAT_BT, MAT_D = 0, 1, 2, 3
 _PREC = {"fp64": FP64, "fp32": FP32, "bf16": BF16, "fp16": FP16}
 _FORM = {"B1": FORM_B1, "BT": FORM_BT}
-_SMOOTHER = {"jacobi": JACOBI, "sai": SAI}
+_SMOOTHER = {"jacobi": JACOBI, "sai": SAI, "gs": GS}
 
 
 class LdgmgError(RuntimeError):
@@ -106,6 +106,7 @@ _SIGS = {
     "ldgmg_host_level_info": (_i, [_vp, _i, _P(_i), _P(_i), _P(_i64), _P(_i), _P(_i64), _P(_i64),
                                    _P(_i64)]),
     "ldgmg_host_export": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
+    "ldgmg_host_colours": (_i, [_vp, _i, _vp, _P(_i)]),
     "ldgmg_host_free": (None, [_vp]),
     "ldgmg_server_create": (_i, [_P(ServerOpts), _P(_vp)]),
     "ldgmg_server_submit": (_i, [_vp, _P(Request), _P(ctypes.c_uint64)]),
@@ -143,7 +144,7 @@ def project_kernel_noalloc(v, N, b, stream=None):
 
 
 _OUTER = {"auto": 0, "fp64": 1, "df": 2}
-_KRYLOV = {"auto": 0, "cg": 1, "gmres": 2}
+_KRYLOV = {"auto": 0, "cg": 1, "gmres": 2, "fgmres": 3}
 TAUP = 0.05   # default Stokes pressure-penalty scale (tau_p = taup h / min mu)
 
 
@@ -225,6 +226,14 @@ class HostHierarchy:
         _check(_lib.ldgmg_host_export(self._h, level, which, rp.ctypes.data_as(_vp), col.ctypes.data_as(_vp),
                                       vals.ctypes.data_as(_vp)))
         return rp, col, vals
+
+    def colours(self, level):
+        """Colour of every element of a Gauss-Seidel level (ldgmg_host_colours)."""
+        N = self.info(level)["N"]
+        out = np.zeros(N, np.int32)
+        nc = ctypes.c_int()
+        _check(_lib.ldgmg_host_colours(self._h, level, out.ctypes.data_as(_vp), ctypes.byref(nc)))
+        return out, nc.value
 
     def __del__(self):
         if getattr(self, "_h", None):

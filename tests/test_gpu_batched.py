@@ -96,14 +96,27 @@ def test_batched_solve_equals_alone_and_oracle(lib, prec, d, n, p, mu_kind, oute
     print(f"\nbatched {prec} d={d} n={n} p={p} mu={mu_kind}: iterations {its}")
 
 
-def test_batched_setup_rejects_unsupported(lib):
-    op = lib.Operator(2, 8, 2)                         # b = 9: no tensor-core path
-    with pytest.raises(lib.LdgmgError) as e:
-        lib.Hierarchy(op, smoother="sai", precision="bf16", max_rhs=8)
-    assert e.value.status == lib.EUNSUPPORTED
+def test_multi_rhs_without_tensor_cores_and_limits(lib):
+    """max_rhs > 1 off the tensor-core path (b = 9; FP16 storage; Gauss-Seidel)
+    runs the CUDA-core kernels with one grid row per right-hand side: each
+    right-hand side is bitwise the same alone and in the batch.  nrhs above
+    max_rhs and Stokes operators with max_rhs > 1 are rejected."""
+    for d, n, p, kw in ((2, 8, 2, dict(smoother="sai", precision="bf16")),
+                        (2, 8, 3, dict(smoother="sai", precision="fp16")),
+                        (2, 8, 2, dict(smoother="gs", precision="fp32"))):
+        op = lib.Operator(d, n, p)
+        H = lib.Hierarchy(op, max_rhs=4, **kw)
+        N, b = n ** d, (p + 1) ** d
+        B = np.stack([ldg.project_out_constant(random_rhs(N, b, seed=60 + r), d, p, N) for r in range(3)])
+        Xb, kb, rb, st = H.solve(torch.tensor(B, device="cuda"), tol=1e-10)
+        assert st == lib.OK and max(rb) <= 1.05e-10
+        x1, k1, r1, s1 = H.solve(torch.tensor(B[1], device="cuda"), tol=1e-10)
+        assert s1 == lib.OK and k1 == kb[1]
+        assert np.array_equal(x1.cpu().numpy(), Xb[1].cpu().numpy())
     op3 = lib.Operator(2, 8, 3)
-    with pytest.raises(lib.LdgmgError):
-        lib.Hierarchy(op3, smoother="sai", precision="fp16", max_rhs=8)
     H = lib.Hierarchy(op3, smoother="sai", precision="bf16", max_rhs=2)
     with pytest.raises(lib.LdgmgError):
         H.solve(torch.zeros(3, op3.size, dtype=torch.float64, device="cuda"))
+    with pytest.raises(lib.LdgmgError) as e:
+        lib.Hierarchy(lib.Operator(2, 8, 2, stokes=0), precision="fp32", max_rhs=2)
+    assert e.value.status == lib.EUNSUPPORTED

@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 from oracle import krylov, ldg
+from oracle import krylov as krylov_mod
 from oracle import multigrid as mg
 from paper_2412_12506_gb300.inputs import circle_mu, random_rhs, random_vector, square_mu
 
@@ -305,3 +306,51 @@ def test_full_size_poisson3d_apply_sampled_rows(lib):
             j = mfull.index(tuple(ci[a] + off[a] for a in range(d)))
             acc += scale * Aref.block(0, int(jr)) @ xs[j * b:(j + 1) * b]
         assert rel(y[i * b:(i + 1) * b], acc) < 1e-12
+
+
+@pytest.mark.parametrize("prec,smoother,R", [("fp64", "sai", 1), ("fp32", "jacobi", 1), ("fp32", "gs", 3),
+                                             ("bf16", "sai", 4)])
+def test_vcycle_graph_replay_equals_eager(lib, prec, smoother, R):
+    """The first V-cycle with a given right-hand-side count runs eagerly, the
+    second is captured into a CUDA graph, later ones replay it: all bitwise equal."""
+    d, n, p = 2, 16, 3
+    op = lib.Operator(d, n, p)
+    H = lib.Hierarchy(op, smoother=smoother, precision=prec, max_rhs=R)
+    N, b = n * n, (p + 1) ** 2
+    B = np.stack([ldg.project_out_constant(random_rhs(N, b, seed=70 + r), d, p, N) for r in range(R)])
+    bt = cuda(B if R > 1 else B[0])
+    k0 = lib.kernel_launches()
+    outs = [H.vcycle(bt).cpu().numpy() for _ in range(4)]
+    per_cycle = (lib.kernel_launches() - k0) / 4
+    assert per_cycle > 10
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+@pytest.mark.parametrize("prec,pre,post,krylov", [("fp64", "B1", "BT", "cg"), ("fp32", "B1", "BT", "cg"),
+                                                  ("fp64", "B1", "B1", "gmres")])
+def test_sai2_solves_match_oracle(lib, prec, pre, post, krylov):
+    """SAI2 (pattern of A^2, Sec. 2.3.3; the paper's fastest-converging smoother)
+    with the symmetric pairing and CG, and the same-form pairing with GMRES."""
+    from oracle import stokes as st
+    d, n, p = 2, 16, 2
+    N, b = n * n, (p + 1) ** 2
+    levels = mg.build_levels(d, n, p)
+    V = mg.VCycle(levels, "sai", 3, 3, ell=2, pre=pre, post=post)
+    A = levels[0].A.mat
+    rhs = ldg.project_out_constant(random_rhs(N, b, seed=23), d, p, N)
+    if krylov == "cg":
+        _, ko, _ = krylov_mod.pcg(A, V, rhs, tol=1e-10)
+        xo, _, _ = krylov_mod.pcg(A, V, rhs, tol=1e-12)
+    else:
+        _, ko, _ = st.gmres(A, V, rhs, tol=1e-10)
+        xo, _, _ = st.gmres(A, V, rhs, tol=1e-12)
+    op = lib.Operator(d, n, p)
+    H = lib.Hierarchy(op, smoother="sai", sai_level=2, pre=pre, post=post, precision=prec, krylov=krylov)
+    assert H.info(0)["nnzb_S"] == 13 * N                       # Table tab:sizes: SAI2 stencil 13 blocks
+    x, k, rr, status = H.solve(cuda(rhs), tol=1e-10)
+    assert status == lib.OK
+    assert (abs(k - ko) <= 1) if prec == "fp64" else (k <= ko + 3), (k, ko)
+    xg = ldg.project_out_constant(x.cpu().numpy(), d, p, N)
+    err = np.linalg.norm(xg - ldg.project_out_constant(xo, d, p, N)) / np.linalg.norm(xo)
+    assert err <= (1e-8 if prec == "fp64" else 1e-7), err

@@ -13,9 +13,10 @@ Tolerances (relative, max-abs error over max-abs value unless stated):
     iteration count within one of the oracle's; solution within 1e-8 relative
     L2 of an oracle solve to 1e-12 after removing the kernel (both stop at a
     preconditioned residual of 1e-10; V A is well conditioned).
-  * Flexible GMRES with an FP32 V-cycle: true relative residual <= 1.05e-10,
-    error against the FP64 oracle solution below 1e-7, iterations within three
-    of the oracle's left-preconditioned count.
+  * Left GMRES with an FP32 V-cycle (iterative refinement): error against the
+    FP64 oracle solution below 1e-7, at most five times the oracle's iterations.
+  * Flexible GMRES: true relative residual <= 1.05e-10; iterations within one
+    (FP64 V) / three (FP32 V) of the oracle's FGMRES; solution within 1e-7.
 """
 import numpy as np
 import pytest
@@ -146,26 +147,52 @@ def test_stokes_gmres_fp64_matches_oracle(lib, d, n, p, gamma, mu_kind):
     assert rr <= (1e-8 if mu_kind is None else 1e-4), rr
 
 
-@pytest.mark.parametrize("gamma,mu_kind", [(0, None), (1, None), (1, "square")])
-def test_stokes_flexible_gmres_fp32(lib, gamma, mu_kind):
+@pytest.mark.parametrize("gamma,mu_kind", [(0, None), (1, "square")])
+def test_stokes_left_gmres_fp32_vcycle(lib, gamma, mu_kind):
+    """Left GMRES with an FP32 V-cycle: the preconditioned residual is confirmed
+    (FP64 residual, then V) before stopping and the iteration restarts from it
+    otherwise -- iterative refinement with GMRES inside.  It converges to the
+    FP64 oracle's solution, but the rounding of V breaks the Arnoldi relation at
+    ~1e-7 per cycle, so it needs several restarts; that is why
+    LDGMG_KRYLOV_AUTO picks FGMRES for reduced-precision V-cycles."""
     d, n, p = 2, 16, 2
     mu = mu_for(mu_kind, d, n)
     levels, V = oracle_stokes(d, n, p, gamma, mu_kind)
     rhs = _stokes_rhs(d, n, p, 12)
-    xo, ko, _ = st.gmres(levels[0].A.mat, V, rhs, tol=1e-12)
+    xo, _, _ = st.gmres(levels[0].A.mat, V, rhs, tol=1e-12)
     _, ko10, _ = st.gmres(levels[0].A.mat, V, rhs, tol=1e-10)
     op = lib.Operator(d, n, p, mu, stokes=gamma)
-    H = lib.Hierarchy(op, smoother="sai", precision="fp32")
+    H = lib.Hierarchy(op, smoother="sai", precision="fp32", krylov="gmres")
     x, k, rr, status = H.solve(cuda(rhs), tol=1e-10)
     assert status == lib.OK
-    assert rr <= 1.05e-10
     N = n ** d
     xg = st.project_out_kernel(x.cpu().numpy(), d, p, N)
     xo = st.project_out_kernel(xo, d, p, N)
     err = np.linalg.norm(xg - xo) / np.linalg.norm(xo)
-    print(f"\nstokes gamma={gamma} {mu_kind}: FGMRES fp32 iters {k} (oracle left GMRES {ko10}), err {err:.2e}")
+    print(f"\nstokes gamma={gamma} {mu_kind}: left GMRES, fp32 V: iters {k} (oracle fp64 V {ko10}), err {err:.2e}")
     assert err < 1e-7
-    assert k <= ko10 + 3
+    assert k <= 5 * ko10
+
+
+@pytest.mark.parametrize("prec,gamma,mu_kind", [("fp64", 1, None), ("fp64", 1, "square"), ("fp32", 0, None),
+                                                ("fp32", 1, "square")])
+def test_stokes_fgmres(lib, prec, gamma, mu_kind):
+    """Flexible GMRES stops on the true residual; with an FP64 V-cycle it follows
+    the oracle's FGMRES within one iteration, with FP32 within three."""
+    d, n, p = 2, 16, 2
+    mu = mu_for(mu_kind, d, n)
+    levels, V = oracle_stokes(d, n, p, gamma, mu_kind)
+    rhs = _stokes_rhs(d, n, p, 14)
+    xo, ko, _ = st.fgmres(levels[0].A.mat, V, rhs, tol=1e-10)
+    op = lib.Operator(d, n, p, mu, stokes=gamma)
+    H = lib.Hierarchy(op, smoother="sai", precision=prec, krylov="fgmres")
+    x, k, rr, status = H.solve(cuda(rhs), tol=1e-10)
+    assert status == lib.OK and rr <= 1.05e-10
+    assert abs(k - ko) <= 1 if prec == "fp64" else k <= ko + 3, (k, ko)
+    N = n ** d
+    xg = st.project_out_kernel(x.cpu().numpy(), d, p, N)
+    xo = st.project_out_kernel(xo, d, p, N)
+    assert np.linalg.norm(xg - xo) <= 1e-7 * np.linalg.norm(xo)
 
 
 def test_stokes_gmres_restart_and_host_buffers(lib):

@@ -194,3 +194,21 @@ def test_host_stokes_rejects_bad_arguments(lib):
         lib.HostHierarchy(2, 4, 1, stokes=2)
     with pytest.raises(lib.LdgmgError):
         lib.HostHierarchy(2, 4, 1, stokes=0, taup=-1.0)
+
+
+@pytest.mark.parametrize("d,n,p,stokes", [(2, 8, 2, None), (3, 4, 1, None), (2, 8, 1, 1), (2, 8, 2, 0)])
+def test_host_gauss_seidel_colours_and_blocks_match_oracle(lib, d, n, p, stokes):
+    """Sec. 2.3.2: the library's greedy colouring and inverse blocks equal the oracle's."""
+    from oracle import stokes as st
+    if stokes is None:
+        levels = mg.build_levels(d, n, p)
+    else:
+        levels = st.build_stokes_levels(d, n, p, gamma=stokes)
+    H = lib.HostHierarchy(d, n, p, stokes=stokes, smoother="gs")
+    for l, lv in enumerate(levels[:-1]):
+        gs = mg.GaussSeidel(lv.A)
+        col, nc = H.colours(l)
+        assert nc == gs.ncolours and np.array_equal(col, gs.colour)
+        _, _, vals = H.export(l, lib.MAT_D)
+        for i in range(lv.A.nblocks):
+            assert np.abs(vals[i] - gs.Dinv[i]).max() <= 1e-9 * np.abs(gs.Dinv[i]).max()

@@ -289,3 +289,85 @@ def test_interface_contrast_independence():
         _, k, _ = krylov.pcg(A.mat, V, rhs)
         ks.append(k)
     assert max(ks) - min(ks) <= 2 and max(ks) <= 12, ks
+
+
+# ---------------------------------------------------------------------------
+# multi-coloured block Gauss-Seidel (Sec. 2.3.2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,n,p", [(2, 8, 1), (2, 6, 2), (3, 4, 1), (2, 2, 1)])
+def test_colouring_is_red_black_on_the_block_stencil(d, n, p):
+    """Sec. 2.3.2: on Cartesian grids with one-sided fluxes the colouring of the
+    block pattern is the red-black colouring of the 5 / 7-point stencil."""
+    A = ldg.assemble(d, n, p).A
+    col = mg.greedy_colouring(A.pat)
+    assert col.max() == 1
+    P = A.pat.tocoo()
+    assert all(col[i] != col[j] for i, j in zip(P.row, P.col) if i != j)
+    mesh = ldg.Mesh(d, n)
+    parity = np.array([sum(mesh.coords(e)) % 2 for e in range(mesh.N)])
+    assert np.array_equal(col, parity)
+
+
+def _block_parts(A, order):
+    """Dense A permuted to `order` (block level) and split into D, strict lower L, strict upper U."""
+    b = A.b
+    perm = np.concatenate([np.arange(i * b, (i + 1) * b) for i in order])
+    Ad = A.dense()[np.ix_(perm, perm)]
+    N = len(order)
+    D = np.zeros_like(Ad)
+    L = np.zeros_like(Ad)
+    for I in range(N):
+        for J in range(N):
+            blk = Ad[I * b:(I + 1) * b, J * b:(J + 1) * b]
+            if I == J:
+                D[I * b:(I + 1) * b, J * b:(J + 1) * b] = blk
+            elif J < I:
+                L[I * b:(I + 1) * b, J * b:(J + 1) * b] = blk
+    return perm, D, L, Ad - D - L
+
+
+@pytest.mark.parametrize("mu_kind", [None, "circle"])
+def test_gauss_seidel_sweep_is_block_triangular_solve(mu_kind):
+    """A forward multi-coloured sweep equals textbook block Gauss-Seidel in the
+    colour-sorted element order, x' = (D + L)^{-1} (b - U x); the backward sweep
+    equals (D + U)^{-1} (b - L x) (Sec. 2.3.2, Sec. 2.4 pairings)."""
+    d, n, p = 2, 6, 2
+    mu = None if mu_kind is None else circle_mu(d, n, seed=1, mu_in=1e3)
+    A = ldg.assemble(d, n, p, mu).A
+    gs = mg.GaussSeidel(A)
+    order = np.argsort(gs.colour, kind="stable")
+    perm, D, L, U = _block_parts(A, order)
+    rng = np.random.default_rng(0)
+    x, rhs = rng.standard_normal(A.mat.shape[0]), rng.standard_normal(A.mat.shape[0])
+    fwd = np.empty_like(x)
+    fwd[perm] = np.linalg.solve(D + L, rhs[perm] - U @ x[perm])
+    bwd = np.empty_like(x)
+    bwd[perm] = np.linalg.solve(D + U, rhs[perm] - L @ x[perm])
+    assert np.abs(gs.sweep(x, rhs, "B1") - fwd).max() <= 1e-11 * np.abs(fwd).max()
+    assert np.abs(gs.sweep(x, rhs, "BT") - bwd).max() <= 1e-11 * np.abs(bwd).max()
+
+
+def test_gauss_seidel_vcycle_symmetry_and_pairing_speed():
+    """Forward pre / backward post gives a symmetric V-cycle (CG-usable); the
+    forward / forward pairing is asymmetric and, with GMRES, needs fewer
+    iterations (Sec. 2.4.1: GS with same-order sweeps is usually fastest)."""
+    d, n, p = 2, 4, 1
+    levels = mg.build_levels(d, n, p)
+    sym = mg.VCycle(levels, "gs", 2, 2, pre="B1", post="BT")
+    asym = mg.VCycle(levels, "gs", 2, 2, pre="B1", post="B1")
+    size = levels[0].A.mat.shape[0]
+    c = ldg.constant_vector(d, p, levels[0].N)
+    Pc = np.eye(size) - np.outer(c, c) / (c @ c)
+    Vs = Pc @ np.column_stack([sym(Pc @ e) for e in np.eye(size)])
+    Va = Pc @ np.column_stack([asym(Pc @ e) for e in np.eye(size)])
+    assert np.abs(Vs - Vs.T).max() <= 1e-11 * np.abs(Vs).max()
+    assert np.abs(Va - Va.T).max() > 1e-3 * np.abs(Va).max()
+    from oracle import stokes as st
+    for d, n, p in ((2, 16, 2), (2, 16, 3)):
+        levels = mg.build_levels(d, n, p)
+        A = levels[0].A
+        rhs = ldg.project_out_constant(np.random.default_rng(0).standard_normal(A.mat.shape[0]), d, p, A.nblocks)
+        _, k_oi, _ = st.gmres(A.mat, mg.VCycle(levels, "gs", 3, 3, pre="B1", post="BT"), rhs, tol=1e-10)
+        _, k_oo, _ = st.gmres(A.mat, mg.VCycle(levels, "gs", 3, 3, pre="B1", post="B1"), rhs, tol=1e-10)
+        assert k_oo < k_oi, (k_oo, k_oi)

@@ -24,27 +24,31 @@ def test_all_requests_complete_and_batch_per_class(lib):
     s = lib.Server(workers=2, max_batch=8, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.01,
                    precision="fp32")
     tickets = []
-    # b = 16 (2D p = 3) classes take batches; b = 9 (2D p = 2) and Stokes do not
-    for i in range(40):
-        if i % 3 == 0:
-            tickets.append(("batched", s.submit(2, 16, 3, _rhs(2, 16, 3))))
-        elif i % 3 == 1:
-            tickets.append(("single", s.submit(2, 16, 2, _rhs(2, 16, 2))))
-        else:
+    # scalar classes take batches (capped at 2^22 dofs per call: the 256^2 p = 4
+    # class takes at most 2); Stokes (GMRES) takes one right-hand side per call
+    for i in range(48):
+        if i % 4 == 0:
+            tickets.append(("b16", s.submit(2, 16, 3, _rhs(2, 16, 3))))
+        elif i % 4 == 1:
+            tickets.append(("b9", s.submit(2, 16, 2, _rhs(2, 16, 2))))
+        elif i % 4 == 2:
             tickets.append(("stokes", s.submit(2, 8, 2, _rhs(2, 8, 2, 1), stokes=1)))
-    res = {kind: [] for kind in ("batched", "single", "stokes")}
+        else:
+            tickets.append(("big", s.submit(2, 256, 4, _rhs(2, 256, 4))))
+    res = {kind: [] for kind in ("b16", "b9", "stokes", "big")}
     for kind, t in tickets:
         _, r = s.wait(t)
         assert r["status"] == lib.OK and r["iters"] == 0 and np.isnan(r["relres"])
         assert r["t_submit"] <= r["t_start"] <= r["t_end"]
         res[kind].append(r)
     st = s.stats()
-    assert st["submitted"] == st["completed"] == 40
-    assert st["builds"] == 3 and st["evictions"] == 0 and st["classes_resident"] == 3
-    assert all(r["batch"] == 1 for r in res["single"] + res["stokes"])
-    assert all(1 <= r["batch"] <= 8 for r in res["batched"])
-    assert max(r["batch"] for r in res["batched"]) > 1          # queued requests joined one call
-    assert st["solve_calls"] < 40
+    assert st["submitted"] == st["completed"] == 48
+    assert st["builds"] == 4 and st["evictions"] == 0 and st["classes_resident"] == 4
+    assert all(r["batch"] == 1 for r in res["stokes"])
+    assert all(1 <= r["batch"] <= 2 for r in res["big"])
+    assert all(1 <= r["batch"] <= 8 for r in res["b16"] + res["b9"])
+    assert max(r["batch"] for r in res["b16"]) > 1 and max(r["batch"] for r in res["b9"]) > 1
+    assert st["solve_calls"] < 48
     s.close()
 
 
