@@ -44,7 +44,7 @@ METRIC = "1e-10 solves/s (mixed-precision V-cycle + FP64 CG)"
 # mean of 3 launches), scaled by rows to the launch timed here; valid only for
 # the kernel source it was taken on (sha256 prefix of bsr_apply.cu), else
 # reported as null.
-TRAFFIC_PER_ROW = {"fp16": (241.17e6 / 4096, "4dc1baae596e4602")}
+TRAFFIC_PER_ROW = {"fp16": (241.00e6 / 4096, "64e8581caa4a6cb1")}
 
 
 def kernel_source_hash():
@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--stokes-n", type=int, default=128, help="0 disables the Stokes section")
     ap.add_argument("--stokes-steps", type=int, default=3)
     ap.add_argument("--stokes-tol", type=float, default=1e-9)
-    ap.add_argument("--serve-requests", type=int, default=10000, help="0 disables the serving section")
+    ap.add_argument("--serve-requests", type=int, default=3000, help="0 disables the serving section")
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-fp64-sample", type=int, default=200)
     ap.add_argument("--section", default="all", choices=["all", "batched", "stokes", "serve"],

@@ -238,9 +238,11 @@ class SAI:
     matrices with the block pattern of A^ell (Sec. 2.3.3)."""
 
     def __init__(self, A: BOp, ell: int = 1, balance: bool = True, pre: str = "B1",
-                 post: str = "BT", alpha=None):
+                 post: str = "BT", alpha=None, build: bool = True):
         """alpha: optional per-dof balancing vector (Sec. 3.3, Stokes); by default
-        alpha_i = ||A_ii||_F^{-1/2} on every dof of element i (Sec. 2.3.3)."""
+        alpha_i = ||A_ii||_F^{-1/2} on every dof of element i (Sec. 2.3.3).
+        build = False prepares the least-squares data without solving every
+        column (columns are then computed on demand by column(i))."""
         self.A, self.ell = A, ell
         self.pre, self.post = pre, post
         b, N = A.b, A.nblocks
@@ -260,6 +262,8 @@ class SAI:
         self._At = (Da @ A.mat @ Da).tocsc()
         self._Pc = pattern_power(A.pat, ell).tocsc()
         self._Ac = A.pat.tocsc()
+        if not build:
+            return
         blocks = {}
         for i in range(N):
             blocks.update(self.column(i))

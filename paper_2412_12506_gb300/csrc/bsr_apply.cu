@@ -70,16 +70,17 @@ template <int TEAM> __device__ __forceinline__ void team_sync() {
 template <int B, class TA, class TV>
 __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
   typedef typename AccOf<TA>::type TACC;
-  constexpr int VEC = vec_for<TA>(B);
+  constexpr int CS = (B + 3) / 4 * 4;      // column stride of the stored block (padding rows are zero)
+  constexpr int VEC = vec_for<TA>(CS);
   constexpr int TEAM = (B > 32) ? 256 : 32;
-  constexpr int LPC = B / VEC;             // threads per column
+  constexpr int LPC = CS / VEC;            // threads per column
   constexpr int G = TEAM / LPC;            // column groups per team
   constexpr int TEAMS = 256 / TEAM;        // block rows per CTA
   constexpr int STEPS = (B + G - 1) / G;   // load steps per block
   static_assert(G >= 1, "team too small");
   constexpr int KMAX = 16;                 // blocks whose x_j are staged at once
   __shared__ TACC xs[TEAMS][KMAX][B];
-  __shared__ TACC red[TEAMS][G][B];
+  __shared__ TACC red[TEAMS][G][CS];
 
   const int team = threadIdx.x / TEAM, lt = threadIdx.x % TEAM;
   const int g = lt / LPC, rl = lt % LPC;
@@ -107,12 +108,12 @@ __global__ void __launch_bounds__(256) bsr_kernel(BsrArgs<TA, TV> a) {
       team_sync<TEAM>();
       if (active) {
         for (int kk = 0; kk < nb; ++kk) {
-          const TA* blk = a.vals + int64_t(zb + kk) * (B * B) + rl * VEC;
+          const TA* blk = a.vals + int64_t(zb + kk) * (B * CS) + rl * VEC;
 #pragma unroll 4
           for (int st = 0; st < STEPS; ++st) {
             const int c = st * G + g;
             if (c < B) {
-              const VecT<TA, VEC> w = *reinterpret_cast<const VecT<TA, VEC>*>(blk + c * B);
+              const VecT<TA, VEC> w = *reinterpret_cast<const VecT<TA, VEC>*>(blk + c * CS);
               const TACC xc = xs[team][kk][c];
 #pragma unroll
               for (int v = 0; v < VEC; ++v) acc[v] += cvt<TACC>(w.v[v]) * xc;

@@ -108,10 +108,11 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat
   M.prec = prec;
   M.row_major = row_major;
   M.scale = storage_scale(H, prec);
+  M.cs = row_major ? b : col_stride(b);
   std::vector<int> rp(H.row_ptr.begin(), H.row_ptr.end());
   CKS(dalloc(&M.row_ptr, rp.size() * sizeof(int)));
   CKS(dalloc(&M.col, H.col.size() * sizeof(int)));
-  CKS(dalloc((char**)&M.vals, size_t(M.nnzb) * b * b * esize(prec)));
+  CKS(dalloc((char**)&M.vals, size_t(M.nnzb) * b * M.cs * esize(prec)));
   CK(cudaMemcpyAsync(M.row_ptr, rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   if (M.nnzb) CK(cudaMemcpyAsync(M.col, H.col.data(), H.col.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   uint32_t* d_ids = nullptr;
@@ -122,7 +123,7 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat
     CK(cudaMemcpyAsync(d_ids, H.id.data(), H.id.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_pool, H.pool.data.data(), H.pool.data.size() * sizeof(double),
                        cudaMemcpyHostToDevice, st));
-    CK(expand_blocks(M.nnzb, b, d_ids, d_pool, M.vals, prec, row_major, M.scale, st));
+    CK(expand_blocks(M.nnzb, b, M.cs, d_ids, d_pool, M.vals, prec, row_major, M.scale, st));
   }
   CK(cudaStreamSynchronize(st));
   cudaFree(d_ids);
@@ -1067,6 +1068,7 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
   ldgmg_status result = LDGMG_OK;
   std::vector<int> it(R, 0);
   int k = 0;
+  bool true_res_fresh = false;
   if (nact > 0) {
     CK(cudaMemcpyAsync(h->r, b, nb, cudaMemcpyDeviceToDevice, st));
     CKS(apply_V(h, h->r, h->z, R, st));
@@ -1105,30 +1107,58 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     // iteration after convergence would cost real time), four for small ones
     // (launch and synchronisation bound).
     const int chunk = n >= (int64_t(1) << 19) ? 1 : 4;
-    while (nact > 0 && k < h->o.max_iter) {
-      const int c = std::min(chunk, h->o.max_iter - k);
-      CKS(run_graphed(h, graph_key(G_CG, R, c), st, [&](cudaStream_t s) -> ldgmg_status {
-        for (int i = 0; i < c; ++i) CKS(body(s));
-        return LDGMG_OK;
-      }));
-      k += c;
-      CK(cudaMemcpyAsync(h->hactive, h->active, 3 * R * sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      nact = 0;
-      for (int r = 0; r < R; ++r) {
-        nact += h->hactive[r];
-        it[r] = h->hactive[R + r];
-        if (h->hactive[2 * R + r] && result == LDGMG_OK)
-          result = fail(LDGMG_ENOTCONV, "CG breakdown (non-finite residual)");
+    for (int round = 0;; ++round) {
+      while (nact > 0 && k < h->o.max_iter) {
+        const int c = std::min(chunk, h->o.max_iter - k);
+        CKS(run_graphed(h, graph_key(G_CG, R, c), st, [&](cudaStream_t s) -> ldgmg_status {
+          for (int i = 0; i < c; ++i) CKS(body(s));
+          return LDGMG_OK;
+        }));
+        k += c;
+        CK(cudaMemcpyAsync(h->hactive, h->active, 3 * R * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        nact = 0;
+        for (int r = 0; r < R; ++r) {
+          nact += h->hactive[r];
+          it[r] = h->hactive[R + r];
+          if (h->hactive[2 * R + r] && result == LDGMG_OK)
+            result = fail(LDGMG_ENOTCONV, "CG breakdown (non-finite residual)");
+        }
       }
+      // With a reduced-precision V-cycle the recurrence residual can drift from
+      // the true one (flexible CG, large coefficient jumps): confirm every
+      // right-hand side on its FP64 residual b - A x and restart the ones that
+      // miss tol from it (r = b - A x, z = V r, p = z).  Restarting touches
+      // r, z, p of every right-hand side, which frozen ones no longer read.
+      if (!flexible || nact > 0 || k >= h->o.max_iter || result != LDGMG_OK || round >= 8) break;
+      CK(bsr_apply_strided(h->op->A, M_RES, xg, b, nullptr, h->r, 1.0, R, R * bsz, bsz, st));
+      CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_TMP), st));
+      CKS(read_slot(h, S_TMP, R, st));
+      true_res_fresh = true;
+      int again = 0;
+      for (int r = 0; r < R; ++r) {
+        const bool miss = bb[r] > 0.0 && !(hslot(S_TMP)[r] <= tol * tol * bb[r]);
+        h->hactive[r] = miss;
+        again += miss;
+      }
+      if (again == 0) break;
+      true_res_fresh = false;
+      nact = again;
+      CK(cudaMemcpyAsync(h->active, h->hactive, R * sizeof(int), cudaMemcpyHostToDevice, st));
+      CKS(apply_V(h, h->r, h->z, R, st));
+      CK(cudaMemcpyAsync(h->p, h->z, nb, cudaMemcpyDeviceToDevice, st));
+      CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZ), st));
     }
     if (nact > 0 && result == LDGMG_OK) result = fail(LDGMG_ENOTCONV, "max_iter reached");
   }
   double* xd = xg;
-  // true residual of the returned iterates
-  CK(bsr_apply_strided(h->op->A, M_RES, xd, b, nullptr, h->r, 1.0, R, R * bsz, bsz, st));
-  CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_TMP), st));
-  CKS(read_slot(h, S_TMP, R, st));
+  // true residual of the returned iterates (already in S_TMP when the
+  // flexible confirmation just computed it for this x)
+  if (!true_res_fresh) {
+    CK(bsr_apply_strided(h->op->A, M_RES, xd, b, nullptr, h->r, 1.0, R, R * bsz, bsz, st));
+    CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_TMP), st));
+    CKS(read_slot(h, S_TMP, R, st));
+  }
   if (R > 1) {
     double* dst = host_x ? h->stage_x : x;
     CK(batch_to_stack(N, R, int(bsz), xd, dst, st));
@@ -1244,15 +1274,16 @@ ldgmg_status ldgmg_export_level(ldgmg_hier* h, int l, int which, int64_t* row_pt
   }
   if (col && M->nnzb) CK(cudaMemcpy(col, M->col, M->nnzb * sizeof(int), cudaMemcpyDeviceToHost));
   if (vals && M->nnzb) {
-    const int b = M->b;
-    const size_t cnt = size_t(M->nnzb) * b * b;
+    const int b = M->b, cs = M->cs;
+    const size_t cnt = size_t(M->nnzb) * b * cs;      // stored entries (padding included)
     std::vector<char> raw(cnt * esize(M->prec));
     CK(cudaMemcpy(raw.data(), M->vals, raw.size(), cudaMemcpyDeviceToHost));
     for (size_t t = 0; t < cnt; ++t) {
-      const size_t nz = t / (size_t(b) * b), e = t % (size_t(b) * b);
+      const size_t nz = t / (size_t(b) * cs), e = t % (size_t(b) * cs);
       size_t r, c;
-      if (M->row_major) { r = e / b; c = e % b; }
-      else { c = e / b; r = e % b; }
+      if (M->row_major) { r = e / cs; c = e % cs; }
+      else { c = e / cs; r = e % cs; }
+      if (r >= size_t(b) || c >= size_t(b)) continue;
       double v;
       if (M->prec == P_FP64) v = reinterpret_cast<const double*>(raw.data())[t];
       else if (M->prec == P_FP32) v = reinterpret_cast<const float*>(raw.data())[t];

@@ -9,11 +9,15 @@ namespace ldgmg {
 enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2, P_FP16 = 3 };
 
 // Block-CSR matrix resident on the device.  Block nz of row i is the dense
-// b x b block M_{i, col[nz]}, stored column-major: element (r, c) at
-// vals[nz*b*b + c*b + r], in the storage precision `prec`.
+// b x b block M_{i, col[nz]}, stored column-major with column stride
+// cs = col_stride(b) (b rounded up to a multiple of 4; rows b..cs-1 are zero)
+// so every column starts on a 16-byte boundary: element (r, c) at
+// vals[nz*b*cs + c*cs + r], in the storage precision `prec`.  Row-major
+// blocks (tensor-core path, b = 16 or 64) have cs = b.
+inline int col_stride(int b) { return (b + 3) / 4 * 4; }
 struct DevMat {
   int64_t nrows = 0, nnzb = 0;
-  int b = 0, prec = P_FP64;
+  int b = 0, cs = 0, prec = P_FP64;
   int row_major = 0;        // 1: blocks stored row-major (tensor-core batched path)
   double scale = 1.0;       // stored value = scale * entry (a power of two; FP16 storage only)
   int* row_ptr = nullptr;   // nrows + 1
@@ -69,8 +73,9 @@ bool tc_block_size_supported(int b);
 cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st);
 
 // vals[nz] = scale * pool[ids[nz]] converted to `prec`, stored column-major
-// (row_major = 0) or row-major (row_major = 1); pool blocks are row-major FP64
-cudaError_t expand_blocks(int64_t nnzb, int b, const uint32_t* ids, const double* pool, void* vals,
+// with column stride cs (row_major = 0; padding rows written as zero) or
+// row-major (row_major = 1, cs = b); pool blocks are row-major FP64
+cudaError_t expand_blocks(int64_t nnzb, int b, int cs, const uint32_t* ids, const double* pool, void* vals,
                           int prec, int row_major, double scale, cudaStream_t st);
 
 // P: device array of the 1D child-injection matrices P[s][i][j] (2*q*q doubles,
