@@ -56,6 +56,18 @@ def kernel_source_hash():
 UNIT = "solves/s"
 
 
+def eta_of(hist):
+    """Iterations per factor-10 residual reduction (Eq. eta), least-squares
+    slope of log10 of the residual history over its points above 1e3 eps."""
+    import numpy as np
+    h = np.asarray(hist, dtype=np.float64)
+    keep = h > 1e3 * np.finfo(np.float64).eps * h[0]
+    if keep.sum() < 2:
+        return None
+    slope = np.polyfit(np.arange(len(h))[keep], np.log10(h[keep]), 1)[0]
+    return float(-1.0 / slope) if slope < 0 else None
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -301,6 +313,7 @@ def run_batched(args, ldgmg, torch, np, dev, stream, barrier):
         "fp64_single": {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "iterations": sorted(set(it64))},
         "speedup_vs_fp64_single": (R * args.batched_steps / (ms / 1e3)) / (1e3 / ms64),
         "rel_err_vs_fp64": err,
+        "tc_autotuned_ctas_per_sm": Hb.tuning[0],
         "roofline": {"bound": "hbm", "kernel": "bsr_tc_kernel<16, fp32 split> finest-level B apply, 64 RHS",
                      "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                      "frac": bytes_ / (kms / 1e3) / 1e9 / hbm, "ms_per_launch": kms,
@@ -389,6 +402,7 @@ def run_stokes(args, ldgmg, torch, np, dev, stream, barrier):
         "solves_per_s": args.stokes_steps / (ms32 / 1e3),
         "latency_ms": {"p50": float(np.percentile(lat32, 50)), "p99": float(np.percentile(lat32, 99))},
         "iterations": sorted(set(k for k, _ in it32)), "final_relres": max(r for _, r in it32),
+        "eta": eta_of(H32.history()),
         "gpu_launches_per_solve": l32 / args.stokes_steps,
         "krylov": f"FGMRES(50) in FP64 to a true relative residual of {args.stokes_tol:g}, FP32 V-cycle "
                   "(balanced SAI1, zeta = 0.131)",
@@ -396,7 +410,7 @@ def run_stokes(args, ldgmg, torch, np, dev, stream, barrier):
                  "iterations": sorted(set(k for k, _ in it64)), "final_relres": max(r for _, r in it64),
                  "krylov": "FGMRES(50), FP64 V-cycle, same tolerance"},
         "paper_form_fp64": {"solves_per_s": len(latL) / (msL / 1e3), "p50_ms": float(np.median(latL)),
-                            "iterations": sorted(set(k for k, _ in itL)),
+                            "iterations": sorted(set(k for k, _ in itL)), "eta": eta_of(HL.history()),
                             "true_relres": max(r for _, r in itL),
                             "krylov": f"left-preconditioned GMRES(50), FP64 V-cycle, preconditioned residual "
                                       f"{args.tol:g} (Sec. 3.4)"},
@@ -707,6 +721,7 @@ def main():
                    "inputs": "larger than L2 (matrices ~ tens of GB)", "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "iterations": [k for k, _ in iters], "final_relres": max(rr for _, rr in iters),
+        "eta": eta_of(H.history()),
         "fp64_path": fp64,
         "spmv_fp64": {"ms": spmv_ms, "GB_per_s": spmv_bytes / (spmv_ms / 1e3) / 1e9,
                       "frac_of_hbm": spmv_bytes / (spmv_ms / 1e3) / 1e9 / peak},

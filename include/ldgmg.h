@@ -160,6 +160,12 @@ ldgmg_status ldgmg_op_info(const ldgmg_op* op, int64_t* N, int* b, int64_t* nnzb
 ldgmg_status ldgmg_op_device_bytes(const ldgmg_op* op, size_t* bytes);
 ldgmg_status ldgmg_hier_device_bytes(const ldgmg_hier* h, size_t* bytes);
 
+/* Launch shape chosen by the setup-time autotuner of the tensor-core apply
+ * (batched hierarchies): CTAs per SM (0 when not tuned) and the level-0
+ * smoother apply's time with max_rhs right-hand sides at that shape (ms).
+ * The apply's result does not depend on the shape. */
+ldgmg_status ldgmg_hier_tuning(const ldgmg_hier* h, int* tc_ctas_per_sm, double* tc_ms);
+
 /* Field structure: nfields = 1 (scalar) or dim + 1 (Stokes), field_b = (p+1)^dim
  * dofs per field and element (b = nfields * field_b). */
 ldgmg_status ldgmg_op_fields(const ldgmg_op* op, int* nfields, int* field_b);
@@ -221,6 +227,15 @@ ldgmg_status ldgmg_vcycle(ldgmg_hier* h, const double* b_dev, double* x_dev, int
  * non-finite rhs, ETIMEOUT if a bounded device wait gave up. */
 ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x, int nrhs,
                          int* iters, double* relres, void* stream);
+
+/* Residual history of the last ldgmg_solve on this hierarchy for right-hand
+ * side `rhs` (0-based): relres[k] for k = 0 .. count-1 (relres[0] = 1), the
+ * norm the method tests, relative to its value at x = 0 -- CG: the recurrence
+ * residual ||r_k|| / ||b||; GMRES: ||V r_k|| / ||V b|| (Givens estimate);
+ * FGMRES: ||r_k|| / ||b||.  This is the history the paper's speed
+ * eta = log 0.1 / log rho (Eq. eta) is measured on.  *count receives the
+ * length; at most cap values are written (relres may be NULL). */
+ldgmg_status ldgmg_solve_history(const ldgmg_hier* h, int rhs, double* relres, int cap, int* count);
 
 /* ---- per-level entry points (one step of the hot path each) --------------
  * Level vectors are in the hierarchy's working type: double for an FP64

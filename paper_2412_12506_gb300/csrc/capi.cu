@@ -14,6 +14,7 @@
 #include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -29,6 +30,12 @@
 using namespace ldgmg;
 
 static thread_local std::string g_err;
+
+// NVTX range over one C-ABI call (visible in Nsight tools; no cost without a tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 void ldgmg_set_error(const std::string& msg) { g_err = msg; }
 
@@ -187,6 +194,16 @@ struct ldgmg_hier {
   bool gmres = false;
   double *gq = nullptr, *gz = nullptr, *gs = nullptr, *hgs = nullptr;
   size_t dev_bytes = 0;          // device memory held by this handle
+  // autotuned launch shape of the tensor-core apply (CTAs per SM; 0 = all that fit)
+  int tc_ctas = 0;
+  double tc_ms = 0.0;            // its measured time on level 0 with max_rhs right-hand sides
+  // residual history of the last solve: ||r_k||^2 of right-hand side r at
+  // hist[k * R + r], k = 0..iters (device, CG) / host copy after the solve
+  double* hist = nullptr;
+  std::vector<double> hhist;
+  int hist_R = 0;
+  std::vector<int> hist_len;
+  std::vector<double> hist_b2;   // ||b||^2 per right-hand side
   // CUDA graphs of the V-cycle body and of chunks of CG iterations, per
   // right-hand-side count: the first run of each runs eagerly (it also
   // performs one-time kernel configuration), the second is captured, later
@@ -224,6 +241,7 @@ static ldgmg_status apply_mat(ldgmg_hier* h, const DevMat& M, int mode, const vo
     a.es = R * b;
     a.rs = b;
     a.err = h ? h->err : nullptr;
+    a.ctas_per_sm = h ? h->tc_ctas : 0;
     CK(bsr_apply_tc(a, M.b, M.prec, st));
     return LDGMG_OK;
   }
@@ -331,6 +349,26 @@ ldgmg_status ldgmg_op_device_bytes(const ldgmg_op* op, size_t* bytes) {
   return LDGMG_OK;
 }
 
+ldgmg_status ldgmg_solve_history(const ldgmg_hier* h, int rhs, double* relres, int cap, int* count) {
+  if (!h || !count) return fail(LDGMG_EINVAL, "null argument");
+  if (rhs < 0 || rhs >= h->hist_R) return fail(LDGMG_EINVAL, "no history for this right-hand side");
+  const int len = h->hist_len[rhs];
+  *count = len;
+  const double b2 = h->hist_b2[rhs];
+  for (int k = 0; k < len && k < cap && relres; ++k) {
+    const double v = h->hhist[size_t(k) * h->hist_R + rhs];
+    relres[k] = b2 > 0.0 ? std::sqrt(v / b2) : 0.0;
+  }
+  return LDGMG_OK;
+}
+
+ldgmg_status ldgmg_hier_tuning(const ldgmg_hier* h, int* tc_ctas_per_sm, double* tc_ms) {
+  if (!h) return fail(LDGMG_EINVAL, "null hierarchy");
+  if (tc_ctas_per_sm) *tc_ctas_per_sm = h->tc_ctas;
+  if (tc_ms) *tc_ms = h->tc_ms;
+  return LDGMG_OK;
+}
+
 ldgmg_status ldgmg_hier_device_bytes(const ldgmg_hier* h, size_t* bytes) {
   if (!h || !bytes) return fail(LDGMG_EINVAL, "null argument");
   *bytes = h->dev_bytes;
@@ -394,6 +432,7 @@ void ldgmg_hier_free(ldgmg_hier* h) {
     cudaFree(v);
   cudaFree(h->active);
   cudaFree(h->err);
+  cudaFree(h->hist);
   cudaFree(h->gq);
   cudaFree(h->gz);
   cudaFree(h->gs);
@@ -503,7 +542,59 @@ static PBSR jacobi_pbsr(const HostLevel& L) {
   return D;
 }
 
+static ldgmg_status check_err_flag(ldgmg_hier* h, cudaStream_t st);
+
+// Autotuner of the tensor-core apply's launch shape: times the level-0
+// smoother apply with max_rhs right-hand sides (on zeroed level vectors) for
+// every CTAs-per-SM count that fits and keeps the fastest (median of 3).
+// The result of the kernel does not depend on the launch shape.
+static ldgmg_status tune_tc(ldgmg_hier* h, cudaStream_t st) {
+  DevLevel& D = h->lv[0];
+  if (h->lv.size() < 2 || !D.S.row_major) return LDGMG_OK;
+  const int R = h->Rmax;
+  const int fit = tc_max_ctas_per_sm(D.b, h->prec, R);
+  if (fit <= 1) return LDGMG_OK;
+  const size_t bytes = size_t(D.N) * D.b * h->vsz * R;
+  CK(cudaMemsetAsync(D.rhs, 0, bytes, st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e30;
+  int best_c = 0;
+  ldgmg_status status = LDGMG_OK;
+  for (int c = 1; c <= fit && status == LDGMG_OK; ++c) {
+    h->tc_ctas = c;
+    std::vector<float> t;
+    for (int rep = 0; rep < 4 && status == LDGMG_OK; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) { status = fail(LDGMG_ECUDA, "tuner event"); break; }
+      status = apply_mat(h, D.S, M_Y, D.rhs, nullptr, nullptr, D.x, 1.0, R, st);
+      if (status != LDGMG_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        status = fail(LDGMG_ECUDA, "tuner timing");
+        break;
+      }
+      if (rep > 0) t.push_back(ms);       // the first launch warms caches
+    }
+    if (status != LDGMG_OK) break;
+    std::sort(t.begin(), t.end());
+    const double med = t[t.size() / 2];
+    if (med < best) {
+      best = med;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tc_ctas = best_c;
+  h->tc_ms = best;
+  if (status == LDGMG_OK) status = check_err_flag(h, st);
+  return status;
+}
+
 ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, ldgmg_hier** out) {
+  NvtxRange nvtx_("ldgmg_setup");
   g_err.clear();
   if (!op || !o || !out) return fail(LDGMG_EINVAL, "null argument");
   *out = nullptr;
@@ -631,7 +722,8 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
     ldgmg_status s = dalloc(v, n0);
     if (s != LDGMG_OK) return bail(s);
   }
-  if (dalloc(&h->scal, size_t(kCgSlots) * h->Rmax * sizeof(double)) != LDGMG_OK ||
+  if (dalloc(&h->hist, size_t(o->max_iter + 1) * h->Rmax * sizeof(double)) != LDGMG_OK ||
+      dalloc(&h->scal, size_t(kCgSlots) * h->Rmax * sizeof(double)) != LDGMG_OK ||
       dalloc(&h->partials, size_t(std::max(kDotBlocks, kBatchDotBlocks)) * h->Rmax * sizeof(double)) != LDGMG_OK ||
       dalloc(&h->active, 3 * size_t(h->Rmax) * sizeof(int)) != LDGMG_OK || dalloc(&h->err, sizeof(int)) != LDGMG_OK)
     return bail(LDGMG_ENOMEM);
@@ -652,6 +744,10 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   }
   if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "memset"));
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "setup sync"));
+  if (batched) {
+    ldgmg_status s = tune_tc(h, st);
+    if (s != LDGMG_OK) return bail(s);
+  }
   *out = h;
   return LDGMG_OK;
 }
@@ -836,6 +932,7 @@ static ldgmg_status check_err_flag(ldgmg_hier* h, cudaStream_t st) {
 }
 
 ldgmg_status ldgmg_vcycle(ldgmg_hier* h, const double* b, double* x, int nrhs, void* stream) {
+  NvtxRange nvtx_("ldgmg_vcycle");
   if (!h || !b || !x) return fail(LDGMG_EINVAL, "null argument");
   if (nrhs < 1 || nrhs > h->Rmax) return fail(LDGMG_EINVAL, "nrhs must be in 1..max_rhs");
   cudaStream_t st = (cudaStream_t)stream;
@@ -908,6 +1005,10 @@ static ldgmg_status gmres_solve(ldgmg_hier* h, const double* b, double* x, doubl
   CKS(norm2(q(0), &beta0));
   if (iters) *iters = 0;
   if (!std::isfinite(beta0)) return fail(LDGMG_EINVAL, "rhs contains NaN or Inf");
+  h->hist_R = 1;
+  h->hist_b2.assign(1, beta0 * beta0);
+  h->hhist.assign(1, beta0 * beta0);
+  h->hist_len.assign(1, 1);
   if (beta0 == 0.0) return LDGMG_OK;
   std::vector<double> H(size_t(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
   auto Hij = [&](int i, int j) -> double& { return H[size_t(i) * m + j]; };
@@ -955,6 +1056,8 @@ static ldgmg_status gmres_solve(ldgmg_hier* h, const double* b, double* x, doubl
       g[j] = cs[j] * g[j];
       ++k;
       jd = j + 1;
+      h->hhist.push_back(g[j + 1] * g[j + 1]);
+      h->hist_len[0] = int(h->hhist.size());
       if (std::fabs(g[j + 1]) <= tol * beta0) break;
     }
     // y = R^{-1} g (upper triangular), x += Q y (left) or Z y (flexible)
@@ -994,6 +1097,7 @@ static ldgmg_status gmres_solve(ldgmg_hier* h, const double* b, double* x, doubl
 
 ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x, int nrhs, int* iters,
                          double* relres, void* stream) {
+  NvtxRange nvtx_("ldgmg_solve");
   g_err.clear();
   if (!h || !rhs || !x) return fail(LDGMG_EINVAL, "null argument");
   if (nrhs < 1 || nrhs > h->Rmax) return fail(LDGMG_EINVAL, "nrhs must be in 1..max_rhs of the setup");
@@ -1086,7 +1190,8 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     // frozen (alpha = beta = 0) at the same iteration as with a host test, and
     // several iterations can run between host reads; work after the last
     // right-hand side converged changes nothing.
-    auto body = [&](cudaStream_t s) -> ldgmg_status {
+    // part 1: q = A p, alpha, x and r updates, residual norms, stopping test
+    auto step = [&](cudaStream_t s) -> ldgmg_status {
       if (multi && h->use_df) CK(bsr_apply_df(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, R, s));
       else if (multi) CK(bsr_apply_multi64(h->op->A, M_Y, h->p, nullptr, h->q, R, s));
       else if (h->use_df && R == 1) CK(bsr_apply_df1(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, s));
@@ -1095,7 +1200,11 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
       CK(cg_alpha_b(R, S, dact, s));
       CK(cg_update_xr_b(N, R, int(bsz), xg, h->r, h->p, h->q, S, s));
       CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_RR), s));
-      CK(cg_check_b(R, S, dact, dit, dflag, s));
+      CK(cg_check_b(R, S, dact, dit, dflag, h->hist, h->o.max_iter + 1, s));
+      return LDGMG_OK;
+    };
+    // part 2: z = V r, beta, new direction p
+    auto precondition = [&](cudaStream_t s) -> ldgmg_status {
       if (flexible) CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZOLD), s));
       CKS(apply_V(h, h->r, h->z, R, s, false));
       CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZNEW), s));
@@ -1103,27 +1212,44 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
       CK(cg_update_p_b(N, R, int(bsz), h->p, h->z, S, s));
       return LDGMG_OK;
     };
-    // Chunk length: one iteration per host check for large solves (an extra
-    // iteration after convergence would cost real time), four for small ones
-    // (launch and synchronisation bound).
+    auto body = [&](cudaStream_t s) -> ldgmg_status {
+      CKS(step(s));
+      return precondition(s);
+    };
+    // Chunk length: large solves read the stopping state after every
+    // iteration's residual norms (as a host test would) and run the V-cycle
+    // part only while something is active: two graphs per iteration.  Small
+    // solves (launch and synchronisation bound) run four whole iterations per
+    // read; the work after the last right-hand side converged changes nothing.
     const int chunk = n >= (int64_t(1) << 19) ? 1 : 4;
+    auto read_state = [&]() -> ldgmg_status {
+      CK(cudaMemcpyAsync(h->hactive, h->active, 3 * R * sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      nact = 0;
+      for (int r = 0; r < R; ++r) {
+        nact += h->hactive[r];
+        it[r] = h->hactive[R + r];
+        if (h->hactive[2 * R + r] && result == LDGMG_OK)
+          result = fail(LDGMG_ENOTCONV, "CG breakdown (non-finite residual)");
+      }
+      return LDGMG_OK;
+    };
     for (int round = 0;; ++round) {
       while (nact > 0 && k < h->o.max_iter) {
+        if (chunk == 1) {
+          CKS(run_graphed(h, graph_key(G_CG, R, 0), st, step));
+          ++k;
+          CKS(read_state());
+          if (nact > 0 && k < h->o.max_iter) CKS(run_graphed(h, graph_key(G_CG, R, 8), st, precondition));
+          continue;
+        }
         const int c = std::min(chunk, h->o.max_iter - k);
         CKS(run_graphed(h, graph_key(G_CG, R, c), st, [&](cudaStream_t s) -> ldgmg_status {
           for (int i = 0; i < c; ++i) CKS(body(s));
           return LDGMG_OK;
         }));
         k += c;
-        CK(cudaMemcpyAsync(h->hactive, h->active, 3 * R * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        nact = 0;
-        for (int r = 0; r < R; ++r) {
-          nact += h->hactive[r];
-          it[r] = h->hactive[R + r];
-          if (h->hactive[2 * R + r] && result == LDGMG_OK)
-            result = fail(LDGMG_ENOTCONV, "CG breakdown (non-finite residual)");
-        }
+        CKS(read_state());
       }
       // With a reduced-precision V-cycle the recurrence residual can drift from
       // the true one (flexible CG, large coefficient jumps): confirm every
@@ -1150,6 +1276,22 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
       CK(dot_batched(N, R, int(bsz), h->r, h->z, h->partials, slot(S_RZ), st));
     }
     if (nact > 0 && result == LDGMG_OK) result = fail(LDGMG_ENOTCONV, "max_iter reached");
+  }
+  // residual history of this solve (host copy for ldgmg_solve_history)
+  {
+    const int kmax = std::min(k, h->o.max_iter);
+    h->hist_R = R;
+    h->hhist.assign(size_t(kmax + 1) * R, 0.0);
+    if (kmax > 0)
+      CK(cudaMemcpyAsync(h->hhist.data() + R, h->hist + R, size_t(kmax) * R * sizeof(double),
+                         cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h->hist_len.assign(R, 1);
+    h->hist_b2 = bb;
+    for (int r = 0; r < R; ++r) {
+      h->hhist[r] = bb[r];
+      h->hist_len[r] = std::min(it[r], kmax) + 1;
+    }
   }
   double* xd = xg;
   // true residual of the returned iterates (already in S_TMP when the

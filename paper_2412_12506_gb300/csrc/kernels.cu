@@ -478,11 +478,13 @@ __global__ void cg_update_p_b_kernel(int64_t n, int R, int b, double* p, const d
     p[i] = z[i] + s[S_BETA * R + (i / b) % R] * p[i];
 }
 
-__global__ void cg_check_b_kernel(int R, const double* s, int* active, int* it, int* flag) {
+__global__ void cg_check_b_kernel(int R, const double* s, int* active, int* it, int* flag, double* hist,
+                                  int hist_cap) {
   const int r = threadIdx.x + blockIdx.x * blockDim.x;
   if (r >= R || !active[r]) return;
   it[r] += 1;
   const double rr = s[S_RR * R + r];
+  if (hist && it[r] < hist_cap) hist[int64_t(it[r]) * R + r] = rr;
   if (!isfinite(rr)) {
     flag[r] = 1;
     active[r] = 0;
@@ -491,8 +493,9 @@ __global__ void cg_check_b_kernel(int R, const double* s, int* active, int* it, 
   }
 }
 
-cudaError_t cg_check_b(int R, const double* scal, int* active, int* it, int* flag, cudaStream_t st) {
-  cg_check_b_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, scal, active, it, flag);
+cudaError_t cg_check_b(int R, const double* scal, int* active, int* it, int* flag, double* hist, int hist_cap,
+                       cudaStream_t st) {
+  cg_check_b_kernel<<<(R + 127) / 128, 128, 0, st>>>(R, scal, active, it, flag, hist, hist_cap);
   return launched();
 }
 

@@ -67,8 +67,12 @@ struct BatchArgs {
   int R;                  // right-hand sides, 1..128
   int64_t es, rs;         // element and right-hand-side strides of the vectors (floats)
   int* err;               // set to 1 if a bounded wait gave up (may be null)
+  int ctas_per_sm = 0;    // resident CTAs per SM to launch (0: as many as fit); the
+                          // result does not depend on it (a block row is one CTA's work)
 };
 bool tc_block_size_supported(int b);
+// most CTAs of the tensor-core kernel that fit on one SM for (b, prec, R)
+int tc_max_ctas_per_sm(int b, int prec, int R);
 // prec: P_BF16 (2 MMAs per K step) or P_FP32 (3 MMAs: A_hi x_hi + A_hi x_lo + A_lo x_hi)
 cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st);
 
@@ -143,9 +147,11 @@ cudaError_t cg_beta_b(int R, double* scal, const int* active, int flexible, cuda
 cudaError_t cg_update_p_b(int64_t N, int R, int b, double* p, const double* z, const double* scal,
                           cudaStream_t st);
 // Device-side stopping test after the residual norms: for each active r,
-// it[r] += 1, then r stops when scal[S_RR] <= scal[S_TOL2] * scal[S_BB] (flag[r]
-// = 0) or when the norm is not finite (flag[r] = 1).
-cudaError_t cg_check_b(int R, const double* scal, int* active, int* it, int* flag, cudaStream_t st);
+// it[r] += 1 and hist[it[r] * R + r] = ||r||^2 (while it[r] < hist_cap; hist may
+// be null), then r stops when scal[S_RR] <= scal[S_TOL2] * scal[S_BB]
+// (flag[r] = 0) or when the norm is not finite (flag[r] = 1).
+cudaError_t cg_check_b(int R, const double* scal, int* active, int* it, int* flag, double* hist, int hist_cap,
+                       cudaStream_t st);
 // Double-FP32 operator apply (df_apply.cu): `pairs` holds A's FP64 entries as
 // (hi, lo) FP32 pairs in the layout of M (column-major blocks, b = 16 or 64);
 // x, rhs, y are FP64 [element][rhs][mode] with R <= 64 right-hand sides.

@@ -10,8 +10,9 @@
 // as the CUDA-core path that multiplies BF16-stored blocks by FP32 vectors.
 // With FP32-stored blocks the matrix is split the same way while it is staged
 // and three products are accumulated (A_hi x_hi + A_hi x_lo + A_lo x_hi;
-// A_lo x_lo is below 2^-16 of the result), which gives FP32-like accuracy on
-// the BF16 tensor cores.
+// A_lo x_lo is below 2^-16 of the result): both factors then carry about 17
+// significant bits (|x - x_hi - x_lo| <= 2^-18 |x|), between BF16 (8) and
+// FP32 (24), with FP32 accumulation.
 //
 // Operands are staged into shared memory in the canonical K-major,
 // no-swizzle layout: 8-row x 16-byte core matrices, rows 16 B apart, core
@@ -366,6 +367,25 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
 
 bool tc_block_size_supported(int b) { return b == 16 || b == 64; }
 
+// resident CTAs per SM from the kernel's own needs: shared memory (227 KB
+// per SM, ~1 KB reserved per CTA), TMEM (512 columns), threads (2048)
+template <int B, bool SPLIT>
+static int max_ctas(int R) {
+  typedef TcPlan<B, SPLIT> P;
+  const int smem = int(P::total(R));
+  const int by_smem = (227 * 1024) / (smem + 1024);
+  const int by_tmem = 512 / (B < 32 ? 32 : B);
+  const int by_threads = 2048 / kTcThreads;
+  return std::max(1, std::min(by_smem, std::min(by_tmem, by_threads)));
+}
+
+int tc_max_ctas_per_sm(int b, int prec, int R) {
+  const bool split = prec == P_FP32;
+  if (b == 16) return split ? max_ctas<16, true>(R) : max_ctas<16, false>(R);
+  if (b == 64) return split ? max_ctas<64, true>(R) : max_ctas<64, false>(R);
+  return 0;
+}
+
 template <int B, bool SPLIT>
 static cudaError_t launch_tc(const BatchArgs& a, cudaStream_t st) {
   typedef TcPlan<B, SPLIT> P;
@@ -377,12 +397,8 @@ static cudaError_t launch_tc(const BatchArgs& a, cudaStream_t st) {
                                int(P::total(kTcM)));
   });
   if (cfg != cudaSuccess) return cfg;
-  // resident CTAs per SM from the kernel's own needs: shared memory (227 KB
-  // per SM, ~1 KB reserved per CTA), TMEM (512 columns), threads (2048)
-  const int by_smem = (227 * 1024) / (smem + 1024);
-  const int by_tmem = 512 / (B < 32 ? 32 : B);
-  const int by_threads = 2048 / kTcThreads;
-  const int per_sm = std::max(1, std::min(by_smem, std::min(by_tmem, by_threads)));
+  const int fit = max_ctas<B, SPLIT>(a.R);
+  const int per_sm = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, fit) : fit;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

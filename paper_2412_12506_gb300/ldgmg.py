@@ -83,6 +83,8 @@ _SIGS = {
     "ldgmg_op_fields": (_i, [_vp, _P(_i), _P(_i)]),
     "ldgmg_op_device_bytes": (_i, [_vp, _P(ctypes.c_size_t)]),
     "ldgmg_hier_device_bytes": (_i, [_vp, _P(ctypes.c_size_t)]),
+    "ldgmg_hier_tuning": (_i, [_vp, _P(_i), _P(_d)]),
+    "ldgmg_solve_history": (_i, [_vp, _i, _vp, _i, _P(_i)]),
     "ldgmg_apply": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ldgmg_project_kernel": (_i, [_vp, _vp, _i, _vp]),
     "ldgmg_setup": (_i, [_vp, _P(SetupOpts), _vp, _P(_vp)]),
@@ -317,6 +319,21 @@ class Hierarchy:
         v = ctypes.c_size_t()
         _check(_lib.ldgmg_hier_device_bytes(self._h, ctypes.byref(v)))
         return v.value
+
+    def history(self, rhs=0):
+        """Relative residual history of the last solve (ldgmg_solve_history)."""
+        n = ctypes.c_int()
+        _check(_lib.ldgmg_solve_history(self._h, rhs, None, 0, ctypes.byref(n)))
+        out = np.zeros(n.value)
+        _check(_lib.ldgmg_solve_history(self._h, rhs, out.ctypes.data_as(_vp), n.value, ctypes.byref(n)))
+        return out
+
+    @property
+    def tuning(self):
+        """Autotuned tensor-core launch shape: (CTAs per SM, ms of the level-0 apply)."""
+        c, t = ctypes.c_int(), ctypes.c_double()
+        _check(_lib.ldgmg_hier_tuning(self._h, ctypes.byref(c), ctypes.byref(t)))
+        return c.value, t.value
 
     @property
     def vdtype(self):

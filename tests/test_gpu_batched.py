@@ -120,3 +120,20 @@ def test_multi_rhs_without_tensor_cores_and_limits(lib):
     with pytest.raises(lib.LdgmgError) as e:
         lib.Hierarchy(lib.Operator(2, 8, 2, stokes=0), precision="fp32", max_rhs=2)
     assert e.value.status == lib.EUNSUPPORTED
+
+def test_autotuned_launch_shape_does_not_change_results(lib):
+    """The setup-time autotuner picks the tensor-core apply's CTAs per SM by
+    timing; the apply's result does not depend on it, so two hierarchies that
+    may have tuned differently give bitwise equal solves."""
+    d, n, p, R = 2, 32, 3, 16
+    N, b = n * n, (p + 1) ** 2
+    op = lib.Operator(d, n, p)
+    H1 = lib.Hierarchy(op, smoother="sai", precision="fp32", max_rhs=R)
+    H2 = lib.Hierarchy(op, smoother="sai", precision="fp32", max_rhs=R)
+    c1, t1 = H1.tuning
+    assert c1 >= 1 and t1 > 0.0
+    rhs = np.stack([ldg.project_out_constant(random_rhs(N, b, seed=80 + r), d, p, N) for r in range(R)])
+    X1, k1, _, s1 = H1.solve(torch.tensor(rhs, device="cuda"))
+    X2, k2, _, s2 = H2.solve(torch.tensor(rhs, device="cuda"))
+    assert s1 == s2 == lib.OK and k1 == k2 and torch.equal(X1, X2)
+    print(f"\ntuned CTAs per SM: {H1.tuning} / {H2.tuning}")

@@ -354,3 +354,34 @@ def test_sai2_solves_match_oracle(lib, prec, pre, post, krylov):
     xg = ldg.project_out_constant(x.cpu().numpy(), d, p, N)
     err = np.linalg.norm(xg - ldg.project_out_constant(xo, d, p, N)) / np.linalg.norm(xo)
     assert err <= (1e-8 if prec == "fp64" else 1e-7), err
+
+
+def test_residual_history_and_eta_match_oracle(lib):
+    """ldgmg_solve_history returns the residual norms the method tests; for
+    FP64 CG (the 16^2, p = 2 block-Jacobi workload) and FP64 left GMRES (Stokes)
+    they follow the oracle's histories, and so does the speed eta of Eq. eta."""
+    from oracle import stokes as st
+    d, n, p = 2, 16, 2
+    N, b = n * n, (p + 1) ** 2
+    levels = mg.build_levels(d, n, p)
+    V = mg.VCycle(levels, "jacobi", 2, 2)
+    rhs = ldg.project_out_constant(random_rhs(N, b, seed=31), d, p, N)
+    _, ko, ho = krylov.pcg(levels[0].A.mat, V, rhs, tol=1e-10)
+    H = lib.Hierarchy(lib.Operator(d, n, p), smoother="jacobi", nu1=2, nu2=2)
+    _, k, _, status = H.solve(cuda(rhs), tol=1e-10)
+    hist = H.history()
+    assert status == lib.OK and k == ko and len(hist) == k + 1 and hist[0] == 1.0
+    ho = np.asarray(ho) / ho[0]
+    assert np.abs(np.log10(hist) - np.log10(ho)).max() < 1e-6
+    assert abs(krylov.eta(hist) - krylov.eta(ho)) < 1e-3 * krylov.eta(ho)
+    # left GMRES on Stokes: the Givens estimates of ||V r_k||
+    ls = st.build_stokes_levels(d, 8, p, gamma=1)
+    Vs = st.StokesVCycle(ls, "sai", 3, 3, zeta=st.ZETA[(1, d)][p - 1])
+    rs = st.project_out_kernel(random_rhs(64, 27, seed=32), d, p, 64)
+    _, kso, hso = st.gmres(ls[0].A.mat, Vs, rs, tol=1e-10)
+    Hs = lib.Hierarchy(lib.Operator(d, 8, p, stokes=1), smoother="sai")
+    _, ks, _, ss = Hs.solve(cuda(rs), tol=1e-10)
+    hs = Hs.history()
+    assert ss == lib.OK and ks == kso and len(hs) == ks + 1
+    hso = np.asarray(hso) / hso[0]
+    assert np.abs(np.log10(hs) - np.log10(hso)).max() < 1e-5
