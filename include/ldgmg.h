@@ -302,6 +302,13 @@ void ldgmg_hier_free(ldgmg_hier* h);
 #define LDGMG_NOALLOC_MAX_ELEMENTS 16777216
 ldgmg_status ldgmg_project_kernel_noalloc(int64_t N, int b, double* v_dev, void* stream);
 
+/* Self-test of the error path of the library's bounded device waits (the
+ * paper has no counterpart): one kernel waits on an mbarrier that nothing
+ * arrives on, with the spin limit of the tensor-core kernel's waits, then
+ * records the timeout and returns.  Returns LDGMG_ETIMEOUT when the wait gave
+ * up as designed (the context stays usable), ECUDA on a CUDA error. */
+ldgmg_status ldgmg_selftest_bounded_wait(void* stream);
+
 /* Number of CUDA kernels this library has enqueued since it was loaded (all
  * handles, streams and devices; setup-only kernels included).  For counting
  * the launches of a timed region: read before and after it. */

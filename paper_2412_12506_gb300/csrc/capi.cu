@@ -362,6 +362,21 @@ ldgmg_status ldgmg_solve_history(const ldgmg_hier* h, int rhs, double* relres, i
   return LDGMG_OK;
 }
 
+ldgmg_status ldgmg_selftest_bounded_wait(void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int* d_err = nullptr;
+  CK(cudaMalloc((void**)&d_err, sizeof(int)));
+  int e = 0;
+  cudaError_t c = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+  if (c == cudaSuccess) c = bounded_wait_probe(d_err, st);
+  if (c == cudaSuccess) c = cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (c == cudaSuccess) c = cudaStreamSynchronize(st);
+  cudaFree(d_err);
+  if (c != cudaSuccess) return fail(LDGMG_ECUDA, std::string("bounded-wait self-test: ") + cudaGetErrorString(c));
+  if (e) return fail(LDGMG_ETIMEOUT, "bounded device wait gave up (self-test: expected)");
+  return LDGMG_OK;
+}
+
 ldgmg_status ldgmg_hier_tuning(const ldgmg_hier* h, int* tc_ctas_per_sm, double* tc_ms) {
   if (!h) return fail(LDGMG_EINVAL, "null hierarchy");
   if (tc_ctas_per_sm) *tc_ctas_per_sm = h->tc_ctas;

@@ -71,6 +71,8 @@ struct BatchArgs {
                           // result does not depend on it (a block row is one CTA's work)
 };
 bool tc_block_size_supported(int b);
+// one bounded wait on an mbarrier that never completes; sets *err = 1 when it gives up
+cudaError_t bounded_wait_probe(int* err, cudaStream_t st);
 // most CTAs of the tensor-core kernel that fit on one SM for (b, prec, R)
 int tc_max_ctas_per_sm(int b, int prec, int R);
 // prec: P_BF16 (2 MMAs per K step) or P_FP32 (3 MMAs: A_hi x_hi + A_hi x_lo + A_lo x_hi)

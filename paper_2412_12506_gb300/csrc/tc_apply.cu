@@ -63,14 +63,16 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// One potentially blocking test of an mbarrier phase; the suspend-time hint
+// caps each call at about 1 us, so kSpinLimit calls bound a wait to ~1 s.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
       : "memory");
   return ok != 0;
 }
@@ -363,7 +365,24 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
 }
 
+// Self-test of the bounded-wait error path: one thread waits on an mbarrier
+// that nothing arrives on, with the same bounded spin as the tensor-core
+// kernel; when the spin limit runs out it records the timeout and returns.
+__global__ void bounded_wait_probe_kernel(int* err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait_bounded(&bar, 0u)) *err = 1;
+  }
+}
+
 }  // namespace
+
+cudaError_t bounded_wait_probe(int* err, cudaStream_t st) {
+  bounded_wait_probe_kernel<<<1, 32, 0, st>>>(err);
+  return launched();
+}
 
 bool tc_block_size_supported(int b) { return b == 16 || b == 64; }
 

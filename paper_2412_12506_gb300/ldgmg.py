@@ -102,6 +102,7 @@ _SIGS = {
     "ldgmg_hier_free": (None, [_vp]),
     "ldgmg_last_error": (ctypes.c_char_p, []),
     "ldgmg_kernel_launches": (ctypes.c_ulonglong, []),
+    "ldgmg_selftest_bounded_wait": (_i, [_vp]),
     "ldgmg_project_kernel_noalloc": (_i, [_i64, _i, _vp, _vp]),
     "ldgmg_host_build": (_i, [_P(Mesh), _i, _vp, _d, _P(SetupOpts), _P(_vp)]),
     "ldgmg_host_build_stokes": (_i, [_P(Mesh), _i, _vp, _i, _d, _d, _P(SetupOpts), _P(_vp)]),
@@ -133,6 +134,11 @@ def _check(status: int):
 def kernel_launches() -> int:
     """Kernels enqueued by the library so far (ldgmg_kernel_launches)."""
     return int(_lib.ldgmg_kernel_launches())
+
+
+def selftest_bounded_wait(stream=None) -> int:
+    """ldgmg_selftest_bounded_wait: status of a device wait that must give up (ETIMEOUT)."""
+    return int(_lib.ldgmg_selftest_bounded_wait(_stream(stream)))
 
 
 NOALLOC_MAX_ELEMENTS = 16777216

@@ -137,3 +137,18 @@ def test_autotuned_launch_shape_does_not_change_results(lib):
     X2, k2, _, s2 = H2.solve(torch.tensor(rhs, device="cuda"))
     assert s1 == s2 == lib.OK and k1 == k2 and torch.equal(X1, X2)
     print(f"\ntuned CTAs per SM: {H1.tuning} / {H2.tuning}")
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(lib):
+    """A device wait on an mbarrier that nothing arrives on gives up after the
+    tensor-core kernel's spin limit (each try capped at ~1 us) and reports
+    ETIMEOUT; the CUDA context stays usable afterwards."""
+    import time
+    t0 = time.time()
+    assert lib.selftest_bounded_wait() == lib.ETIMEOUT
+    assert time.time() - t0 < 30.0
+    op = lib.Operator(2, 4, 1)
+    x = torch.randn(op.size, dtype=torch.float64, device="cuda")
+    y = op.apply(x)
+    ref = op.apply(x.clone())
+    assert torch.equal(y, ref) and torch.isfinite(y).all()
