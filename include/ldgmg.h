@@ -91,10 +91,13 @@ typedef struct {
   int outer_apply;       /* operator apply of the outer CG of reduced-precision or batched
                             hierarchies with b = 16 or 64: LDGMG_OUTER_FP64, or
                             LDGMG_OUTER_DF = double-FP32 arithmetic (FP32 pairs, ~2^-44 of
-                            sum |a x|: ~100x FP64's rounding, on the fast FP32 pipes), or
-                            LDGMG_OUTER_AUTO = DF when max mu / min mu <= 10, else FP64.
-                            FP64 hierarchies always use FP64.  The final residual that
-                            ldgmg_solve reports is always computed in FP64. */
+                            sum |a x|, on the fast FP32 pipes), or LDGMG_OUTER_AUTO = DF.
+                            With DF and max mu / min mu > 10 (cancellation across the jump
+                            costs DF accuracy) CG runs to 1e-8 of the residual it starts
+                            from and is restarted from the FP64 residual b - A x until tol
+                            is met (iterative refinement).  FP64 hierarchies always use
+                            FP64.  The final residual that ldgmg_solve reports is always
+                            computed in FP64. */
   int krylov;            /* ldgmg_solve's method: LDGMG_KRYLOV_CG (SPD scalar problems),
                             LDGMG_KRYLOV_GMRES (left preconditioned, the paper's form; Stokes:
                             A and V are symmetric indefinite, Sec. 3.4), LDGMG_KRYLOV_FGMRES

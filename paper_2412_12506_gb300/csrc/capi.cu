@@ -722,7 +722,7 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   // right-hand-side mixed-precision path for b = 16 / 64; the plain FP64
   // hierarchy always keeps the FP64 apply
   h->use_df = (batched || h->prec != P_FP64) && tc_block_size_supported(op->host.b) &&
-              (o->outer_apply == LDGMG_OUTER_DF || (o->outer_apply == LDGMG_OUTER_AUTO && op->mu_contrast <= 10.0));
+              (o->outer_apply == LDGMG_OUTER_DF || o->outer_apply == LDGMG_OUTER_AUTO);
   if (h->use_df && !op->A_pairs) {
     // FP32-pair copy of the FP64 operator for the batched outer apply (df_apply.cu)
     const int64_t cnt = op->A.nnzb * int64_t(op->A.b) * op->A.b;
@@ -1179,10 +1179,22 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     h->hactive[R + r] = 0;
     h->hactive[2 * R + r] = 0;
     nact += h->hactive[r];
-    h->hscal[S_TOL2 * R + r] = tol * tol;
   }
+  // Inner tolerance.  With the double-FP32 outer apply and a coefficient jump
+  // (cancellation costs it accuracy) CG runs to a relative 1e-8 of the residual
+  // it starts from, and the FP64 confirmation below restarts it from the true
+  // residual until tol is met: iterative refinement with a cheap inner apply.
+  const double inner = (h->use_df && h->op->mu_contrast > 10.0) ? 1e-8 : 0.0;
+  auto set_tol = [&](const double* start_rr) -> ldgmg_status {
+    for (int r = 0; r < R; ++r) {
+      const double t2 = tol * tol, i2 = inner * inner * (start_rr[r] / (bb[r] > 0.0 ? bb[r] : 1.0));
+      h->hscal[S_TOL2 * R + r] = std::max(t2, i2);
+    }
+    CK(cudaMemcpyAsync(slot(S_TOL2), hslot(S_TOL2), R * sizeof(double), cudaMemcpyHostToDevice, st));
+    return LDGMG_OK;
+  };
   CK(cudaMemcpyAsync(h->active, h->hactive, 3 * R * sizeof(int), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(slot(S_TOL2), hslot(S_TOL2), R * sizeof(double), cudaMemcpyHostToDevice, st));
+  CKS(set_tol(bb.data()));
   CK(cudaMemsetAsync(xg, 0, nb, st));
   ldgmg_status result = LDGMG_OK;
   std::vector<int> it(R, 0);
@@ -1271,7 +1283,7 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
       // right-hand side on its FP64 residual b - A x and restart the ones that
       // miss tol from it (r = b - A x, z = V r, p = z).  Restarting touches
       // r, z, p of every right-hand side, which frozen ones no longer read.
-      if (!flexible || nact > 0 || k >= h->o.max_iter || result != LDGMG_OK || round >= 8) break;
+      if (!flexible || nact > 0 || k >= h->o.max_iter || result != LDGMG_OK || round >= 16) break;
       CK(bsr_apply_strided(h->op->A, M_RES, xg, b, nullptr, h->r, 1.0, R, R * bsz, bsz, st));
       CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_TMP), st));
       CKS(read_slot(h, S_TMP, R, st));
@@ -1285,6 +1297,7 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
       if (again == 0) break;
       true_res_fresh = false;
       nact = again;
+      CKS(set_tol(hslot(S_TMP)));
       CK(cudaMemcpyAsync(h->active, h->hactive, R * sizeof(int), cudaMemcpyHostToDevice, st));
       CKS(apply_V(h, h->r, h->z, R, st));
       CK(cudaMemcpyAsync(h->p, h->z, nb, cudaMemcpyDeviceToDevice, st));
