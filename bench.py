@@ -90,8 +90,9 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=3000, help="0 disables the serving section")
     ap.add_argument("--serve-workers", type=int, default=4)
     ap.add_argument("--serve-fp64-sample", type=int, default=200)
-    ap.add_argument("--section", default="all", choices=["all", "batched", "stokes", "serve"],
-                    help="batched / stokes / serve: run only that section and print its object (profiling)")
+    ap.add_argument("--section", default="all", choices=["all", "batched", "stokes", "serve", "tcapply"],
+                    help="batched / stokes / serve: run only that section and print its object (profiling); "
+                         "tcapply: only the batched section's dominant-kernel timing")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--oracle-n", type=int, default=8)
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
@@ -240,6 +241,46 @@ class Clocks:
 # batched right-hand sides on the tensor-core path
 # ---------------------------------------------------------------------------
 
+def tc_apply_roofline(Hb, op, R, ldgmg, torch, dev, stream, reps=20):
+    """The batched section's dominant kernel: the finest-level SAI B apply on the
+    tensor cores (3 untimed launches, then `reps` timed back to back)."""
+    b = op.b
+    xv = torch.randn(op.size * R, dtype=torch.float32, device=dev)
+    yv = torch.empty_like(xv)
+    for _ in range(3):
+        Hb.level_apply_batched(0, ldgmg.MAT_B, xv, R, yv)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        Hb.level_apply_batched(0, ldgmg.MAT_B, xv, R, yv)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    kms = k0.elapsed_time(k1) / reps
+    nnzb = Hb.info(0)["nnzb_S"]
+    flops = 2.0 * nnzb * b * b * R                      # useful multiply-adds of Y = B X
+    bytes_ = nnzb * b * b * 4 + 2 * op.size * R * 4     # FP32 blocks (hi + lo images) once, X and Y once
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tc_peak = peaks.get("bf16_tflops", 1900.0)
+    return {"bound": "hbm", "kernel": f"bsr_tc_kernel<{b}, fp32 split> finest-level B apply, {R} RHS",
+            "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": bytes_ / (kms / 1e3) / 1e9 / hbm, "ms_per_launch": kms, "bytes_per_launch": bytes_,
+            "tensor_TFLOPs": flops / (kms / 1e3) / 1e12, "tensor_peak_TFLOPs": tc_peak,
+            "tc_ctas_per_sm": Hb.tuning[0]}
+
+
+def run_tcapply(args, ldgmg, torch, np, dev, stream, barrier):
+    """Only the batched section's hierarchy and its dominant-kernel timing (for
+    profiling: the setup autotuner's launches, then 3 + 20 applies)."""
+    from paper_2412_12506_gb300.inputs import square_mu
+    d, n, p, R = 2, args.batched_n, 3, args.batched_rhs
+    op = ldgmg.Operator(d, n, p, square_mu(d, n, mu_in=1e4))
+    Hb = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision="fp32", max_rhs=R)
+    return {"workload": f"interface2d_n{n}_p{p}_square1e4_sai1_{R}rhs",
+            "roofline": tc_apply_roofline(Hb, op, R, ldgmg, torch, dev, stream)}
+
+
 def run_batched(args, ldgmg, torch, np, dev, stream, barrier):
     from paper_2412_12506_gb300.inputs import square_mu
     d, n, p, R = 2, args.batched_n, 3, args.batched_rhs
@@ -282,28 +323,7 @@ def run_batched(args, ldgmg, torch, np, dev, stream, barrier):
     xr = op.project_kernel(X[7].clone())
     x64p = op.project_kernel(x64.clone())
     err = float(torch.linalg.norm(xr - x64p) / torch.linalg.norm(x64p))
-    # dominant kernel: batched finest-level B apply on the tensor cores
-    inf = Hb.info(0)
-    b = op.b
-    xv = torch.randn(op.size * R, dtype=torch.float32, device=dev)
-    yv = torch.empty_like(xv)
-    for _ in range(3):
-        Hb.level_apply_batched(0, ldgmg.MAT_B, xv, R, yv)
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 20
-    k0.record(stream)
-    for _ in range(reps):
-        Hb.level_apply_batched(0, ldgmg.MAT_B, xv, R, yv)
-    k1.record(stream)
-    torch.cuda.synchronize()
-    kms = k0.elapsed_time(k1) / reps
-    nnzb = inf["nnzb_S"]
-    flops = 2.0 * nnzb * b * b * R                      # useful multiply-adds of Y = B X
-    bytes_ = nnzb * b * b * 4 + 2 * op.size * R * 4     # FP32 blocks once, X and Y once
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    tc_peak = peaks.get("bf16_tflops", 1900.0)
+    roof = tc_apply_roofline(Hb, op, R, ldgmg, torch, dev, stream)
     return {
         "workload": f"interface2d_n{n}_p{p}_square1e4_sai1_{R}rhs", "rhs_per_call": R,
         "solves_per_s": R * args.batched_steps / (ms / 1e3),
@@ -314,10 +334,7 @@ def run_batched(args, ldgmg, torch, np, dev, stream, barrier):
         "speedup_vs_fp64_single": (R * args.batched_steps / (ms / 1e3)) / (1e3 / ms64),
         "rel_err_vs_fp64": err,
         "tc_autotuned_ctas_per_sm": Hb.tuning[0],
-        "roofline": {"bound": "hbm", "kernel": "bsr_tc_kernel<16, fp32 split> finest-level B apply, 64 RHS",
-                     "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                     "frac": bytes_ / (kms / 1e3) / 1e9 / hbm, "ms_per_launch": kms,
-                     "tensor_TFLOPs": flops / (kms / 1e3) / 1e12, "tensor_peak_TFLOPs": tc_peak},
+        "roofline": roof,
     }
 
 
@@ -559,13 +576,13 @@ def main():
             "e2e": {"value": s["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
-    if args.section in ("batched", "stokes", "serve"):
+    if args.section in ("batched", "stokes", "serve", "tcapply"):
         import numpy as np
         import torch
         torch.cuda.set_device(local_rank)
         from paper_2412_12506_gb300 import ldgmg
         dev = torch.device("cuda", local_rank)
-        fn = {"batched": run_batched, "stokes": run_stokes, "serve": run_serve}[args.section]
+        fn = {"batched": run_batched, "stokes": run_stokes, "serve": run_serve, "tcapply": run_tcapply}[args.section]
         out = fn(args, ldgmg, torch, np, dev, torch.cuda.current_stream(), lambda: None)
         print(json.dumps(out))
         return

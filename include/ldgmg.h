@@ -274,7 +274,9 @@ ldgmg_status ldgmg_level_prolong(ldgmg_hier* h, int level, const void* xc_dev, v
 ldgmg_status ldgmg_bottom_solve(ldgmg_hier* h, const void* rhs_dev, void* x_dev, void* stream);
 
 /* Copy a level matrix to host memory as FP64 block-CSR (values as stored on the
- * device, converted to double and divided by the storage scale).  row_ptr: N+1 int64, col: nnzb int32, vals:
+ * device, converted to double and divided by the storage scale; FP32 levels of
+ * a tensor-core hierarchy are stored as BF16 pairs hi + lo, |a - hi - lo| <=
+ * 2^-17 |a|, and exported as hi + lo).  row_ptr: N+1 int64, col: nnzb int32, vals:
  * nnzb*b*b doubles, block (r, c) at vals[nz*b*b + r*b + c].  Any of the three
  * may be NULL to skip it.  Test/inspection entry point. */
 ldgmg_status ldgmg_export_level(ldgmg_hier* h, int level, int which, int64_t* row_ptr,

@@ -199,7 +199,7 @@ static cudaError_t launch_bsr_t(const DevMat& M, const int* rows, int64_t count,
 static cudaError_t bsr_dispatch(const DevMat& M, const int* rows, int64_t count, int mode, const void* x,
                                 const void* rhs, const void* xin, void* y, double s, int R, int64_t es, int64_t rs,
                                 cudaStream_t st) {
-  if (M.row_major || R < 1 || count < 0) return cudaErrorInvalidValue;
+  if (M.tc_image || R < 1 || count < 0) return cudaErrorInvalidValue;
   switch (M.prec) {
     case P_FP64: return launch_bsr_t<double, double>(M, rows, count, mode, x, rhs, xin, y, s, R, es, rs, st);
     case P_FP32: return launch_bsr_t<float, float>(M, rows, count, mode, x, rhs, xin, y, s, R, es, rs, st);

@@ -107,15 +107,15 @@ static void free_mat(DevMat& M) {
 }
 
 // Expand a pooled host matrix into an explicit device block-CSR.
-static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat& M, cudaStream_t st) {
+static ldgmg_status upload(const PBSR& H, int b, int prec, int tc_image, DevMat& M, cudaStream_t st) {
   if (H.nnzb() >= (int64_t(1) << 31)) return fail(LDGMG_EUNSUPPORTED, "more than 2^31 blocks");
   M.nrows = H.nrows;
   M.nnzb = H.nnzb();
   M.b = b;
   M.prec = prec;
-  M.row_major = row_major;
+  M.tc_image = tc_image;
   M.scale = storage_scale(H, prec);
-  M.cs = row_major ? b : col_stride(b);
+  M.cs = tc_image ? b : col_stride(b);
   std::vector<int> rp(H.row_ptr.begin(), H.row_ptr.end());
   CKS(dalloc(&M.row_ptr, rp.size() * sizeof(int)));
   CKS(dalloc(&M.col, H.col.size() * sizeof(int)));
@@ -130,7 +130,7 @@ static ldgmg_status upload(const PBSR& H, int b, int prec, int row_major, DevMat
     CK(cudaMemcpyAsync(d_ids, H.id.data(), H.id.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(d_pool, H.pool.data.data(), H.pool.data.size() * sizeof(double),
                        cudaMemcpyHostToDevice, st));
-    CK(expand_blocks(M.nnzb, b, M.cs, d_ids, d_pool, M.vals, prec, row_major, M.scale, st));
+    CK(expand_blocks(M.nnzb, b, M.cs, d_ids, d_pool, M.vals, prec, tc_image, M.scale, st));
   }
   CK(cudaStreamSynchronize(st));
   cudaFree(d_ids);
@@ -225,7 +225,7 @@ static const HostLevel& host_level(const ldgmg_hier* h, int l) {
 static ldgmg_status apply_mat(ldgmg_hier* h, const DevMat& M, int mode, const void* x, const void* rhs,
                               const void* xin, void* y, double s, int R, cudaStream_t st) {
   const int64_t b = M.b;
-  if (M.row_major) {
+  if (M.tc_image) {
     BatchArgs a;
     a.nrows = M.nrows;
     a.row_ptr = M.row_ptr;
@@ -565,7 +565,7 @@ static ldgmg_status check_err_flag(ldgmg_hier* h, cudaStream_t st);
 // The result of the kernel does not depend on the launch shape.
 static ldgmg_status tune_tc(ldgmg_hier* h, cudaStream_t st) {
   DevLevel& D = h->lv[0];
-  if (h->lv.size() < 2 || !D.S.row_major) return LDGMG_OK;
+  if (h->lv.size() < 2 || !D.S.tc_image) return LDGMG_OK;
   const int R = h->Rmax;
   const int fit = tc_max_ctas_per_sm(D.b, h->prec, R);
   if (fit <= 1) return LDGMG_OK;
@@ -1448,12 +1448,29 @@ ldgmg_status ldgmg_export_level(ldgmg_hier* h, int l, int which, int64_t* row_pt
     const size_t cnt = size_t(M->nnzb) * b * cs;      // stored entries (padding included)
     std::vector<char> raw(cnt * esize(M->prec));
     CK(cudaMemcpy(raw.data(), M->vals, raw.size(), cudaMemcpyDeviceToHost));
+    if (M->tc_image) {
+      // operand images: BF16 hi (+ lo for FP32 storage); the stored value is hi + lo
+      const size_t img = size_t(b) * b * 2, per = M->prec == P_FP32 ? 2 * img : img;
+      for (size_t nz = 0; nz < size_t(M->nnzb); ++nz)
+        for (int r = 0; r < b; ++r)
+          for (int c = 0; c < b; ++c) {
+            const char* blk = raw.data() + nz * per;
+            const uint32_t off = tc_image_offset(b, r, c);
+            uint16_t u;
+            std::memcpy(&u, blk + off, 2);
+            double v = bf16_to_float(u);
+            if (M->prec == P_FP32) {
+              std::memcpy(&u, blk + img + off, 2);
+              v = double(float(v) + bf16_to_float(u));
+            }
+            vals[nz * b * b + r * b + c] = v / M->scale;
+          }
+      return LDGMG_OK;
+    }
     for (size_t t = 0; t < cnt; ++t) {
       const size_t nz = t / (size_t(b) * cs), e = t % (size_t(b) * cs);
-      size_t r, c;
-      if (M->row_major) { r = e / cs; c = e % cs; }
-      else { c = e / cs; r = e % cs; }
-      if (r >= size_t(b) || c >= size_t(b)) continue;
+      const size_t c = e / cs, r = e % cs;
+      if (r >= size_t(b)) continue;
       double v;
       if (M->prec == P_FP64) v = reinterpret_cast<const double*>(raw.data())[t];
       else if (M->prec == P_FP32) v = reinterpret_cast<const float*>(raw.data())[t];

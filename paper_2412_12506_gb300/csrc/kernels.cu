@@ -36,29 +36,60 @@ template <> __device__ __forceinline__ f16 from_d<f16>(double v) { return __doub
 
 template <class T>
 __global__ void expand_kernel(int64_t total, int b, int cs, const uint32_t* __restrict__ ids,
-                              const double* __restrict__ pool, T* __restrict__ vals, int row_major, double scale) {
+                              const double* __restrict__ pool, T* __restrict__ vals, double scale) {
   const int64_t bb = int64_t(b) * b, bs = int64_t(b) * cs;   // pool block, stored block
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
        t += int64_t(gridDim.x) * blockDim.x) {
     const int64_t nz = t / bs, e = t % bs;
-    int r, c;
-    if (row_major) { r = int(e / cs); c = int(e % cs); }
-    else { c = int(e / cs); r = int(e % cs); }
-    const bool pad = row_major ? (c >= b) : (r >= b);
-    vals[t] = pad ? from_d<T>(0.0) : from_d<T>(scale * pool[int64_t(ids[nz]) * bb + int64_t(r) * b + c]);
+    const int c = int(e / cs), r = int(e % cs);
+    vals[t] = r >= b ? from_d<T>(0.0) : from_d<T>(scale * pool[int64_t(ids[nz]) * bb + int64_t(r) * b + c]);
+  }
+}
+
+// tensor-core operand images: one thread per block entry (r, c)
+template <bool SPLIT>
+__global__ void expand_tc_kernel(int64_t total, int b, const uint32_t* __restrict__ ids,
+                                 const double* __restrict__ pool, unsigned char* __restrict__ vals, double scale) {
+  const int64_t bb = int64_t(b) * b;
+  const int64_t img = bb * 2;                          // bytes of one BF16 image
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t nz = t / bb, e = t % bb;
+    const int r = int(e / b), c = int(e % b);
+    const double v = scale * pool[int64_t(ids[nz]) * bb + e];
+    unsigned char* blk = vals + nz * img * (SPLIT ? 2 : 1);
+    const uint32_t off = tc_image_offset(b, r, c);
+    if (SPLIT) {
+      const float a = float(v);
+      const bf16 hi = __float2bfloat16_rn(a);
+      const bf16 lo = __float2bfloat16_rn(a - __bfloat162float(hi));
+      *reinterpret_cast<bf16*>(blk + off) = hi;
+      *reinterpret_cast<bf16*>(blk + img + off) = lo;
+    } else {
+      *reinterpret_cast<bf16*>(blk + off) = __double2bfloat16(v);
+    }
   }
 }
 
 cudaError_t expand_blocks(int64_t nnzb, int b, int cs, const uint32_t* ids, const double* pool, void* vals,
-                          int prec, int row_major, double scale, cudaStream_t st) {
+                          int prec, int tc_image, double scale, cudaStream_t st) {
+  if (tc_image) {
+    if (cs != b || (b != 16 && b != 64) || (prec != P_BF16 && prec != P_FP32)) return cudaErrorInvalidValue;
+    const int64_t total = nnzb * b * b;
+    if (total == 0) return cudaSuccess;
+    const int grid = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
+    if (prec == P_FP32) expand_tc_kernel<true><<<grid, 256, 0, st>>>(total, b, ids, pool, (unsigned char*)vals, scale);
+    else expand_tc_kernel<false><<<grid, 256, 0, st>>>(total, b, ids, pool, (unsigned char*)vals, scale);
+    return launched();
+  }
   const int64_t total = nnzb * b * cs;
   if (total == 0) return cudaSuccess;
   const int grid = int(std::min<int64_t>((total + 255) / 256, 152 * 64));
   switch (prec) {
-    case P_FP64: expand_kernel<double><<<grid, 256, 0, st>>>(total, b, cs, ids, pool, (double*)vals, row_major, scale); break;
-    case P_FP32: expand_kernel<float><<<grid, 256, 0, st>>>(total, b, cs, ids, pool, (float*)vals, row_major, scale); break;
-    case P_BF16: expand_kernel<bf16><<<grid, 256, 0, st>>>(total, b, cs, ids, pool, (bf16*)vals, row_major, scale); break;
-    case P_FP16: expand_kernel<f16><<<grid, 256, 0, st>>>(total, b, cs, ids, pool, (f16*)vals, row_major, scale); break;
+    case P_FP64: expand_kernel<double><<<grid, 256, 0, st>>>(total, b, cs, ids, pool, (double*)vals, scale); break;
+    case P_FP32: expand_kernel<float><<<grid, 256, 0, st>>>(total, b, cs, ids, pool, (float*)vals, scale); break;
+    case P_BF16: expand_kernel<bf16><<<grid, 256, 0, st>>>(total, b, cs, ids, pool, (bf16*)vals, scale); break;
+    case P_FP16: expand_kernel<f16><<<grid, 256, 0, st>>>(total, b, cs, ids, pool, (f16*)vals, scale); break;
     default: return cudaErrorInvalidValue;
   }
   return launched();

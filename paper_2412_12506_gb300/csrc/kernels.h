@@ -12,13 +12,14 @@ enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2, P_FP16 = 3 };
 // b x b block M_{i, col[nz]}, stored column-major with column stride
 // cs = col_stride(b) (b rounded up to a multiple of 4; rows b..cs-1 are zero)
 // so every column starts on a 16-byte boundary: element (r, c) at
-// vals[nz*b*cs + c*cs + r], in the storage precision `prec`.  Row-major
-// blocks (tensor-core path, b = 16 or 64) have cs = b.
+// vals[nz*b*cs + c*cs + r], in the storage precision `prec`.  Blocks of the
+// tensor-core path (b = 16 or 64, tc_image = 1) have cs = b and are stored as
+// the BF16 operand images the tensor cores read (tc_image_offset below).
 inline int col_stride(int b) { return (b + 3) / 4 * 4; }
 struct DevMat {
   int64_t nrows = 0, nnzb = 0;
   int b = 0, cs = 0, prec = P_FP64;
-  int row_major = 0;        // 1: blocks stored row-major (tensor-core batched path)
+  int tc_image = 0;         // 1: blocks stored as tensor-core operand images (batched path)
   double scale = 1.0;       // stored value = scale * entry (a power of two; FP16 storage only)
   int* row_ptr = nullptr;   // nrows + 1
   int* col = nullptr;       // nnzb
@@ -57,7 +58,7 @@ struct BatchArgs {
   int64_t nrows;
   const int* row_ptr;
   const int* col;
-  const void* vals;       // row-major blocks, BF16 or FP32 (split into hi/lo BF16 while staging)
+  const void* vals;       // block operand images (BF16, or BF16 hi + lo for FP32 storage)
   const float* x;
   const float* rhs;
   const float* xin;
@@ -79,10 +80,21 @@ int tc_max_ctas_per_sm(int b, int prec, int R);
 cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st);
 
 // vals[nz] = scale * pool[ids[nz]] converted to `prec`, stored column-major
-// with column stride cs (row_major = 0; padding rows written as zero) or
-// row-major (row_major = 1, cs = b); pool blocks are row-major FP64
+// with column stride cs (tc_image = 0; padding rows written as zero) or as
+// tensor-core operand images (tc_image = 1, cs = b, prec P_BF16 or P_FP32);
+// pool blocks are row-major FP64
 cudaError_t expand_blocks(int64_t nnzb, int b, int cs, const uint32_t* ids, const double* pool, void* vals,
-                          int prec, int row_major, double scale, cudaStream_t st);
+                          int prec, int tc_image, double scale, cudaStream_t st);
+
+// Tensor-core operand image of a b x b block (b = 16 or 64): entry (r, c) --
+// output mode r, input mode c -- in the K-major, no-swizzle core-matrix
+// layout (8 rows x 16 bytes per core matrix, b/8 core matrices along K),
+// BF16.  P_BF16 storage holds one image (2 b^2 bytes); P_FP32 storage holds
+// the image of hi = bf16(a) followed by that of lo = bf16(a - hi), a the FP32
+// entry (4 b^2 bytes, the same as FP32).  Byte offset within one image:
+__host__ __device__ inline uint32_t tc_image_offset(int b, int r, int c) {
+  return uint32_t(((r >> 3) * (b >> 3) + (c >> 3)) * 128 + (r & 7) * 16 + (c & 7) * 2);
+}
 
 // P: device array of the 1D child-injection matrices P[s][i][j] (2*q*q doubles,
 // q = p + 1 <= 8).  Level vectors are double (vprec 0) or float (vprec 1).

@@ -11,20 +11,34 @@
 // With FP32-stored blocks the matrix is split the same way while it is staged
 // and three products are accumulated (A_hi x_hi + A_hi x_lo + A_lo x_hi;
 // A_lo x_lo is below 2^-16 of the result): both factors then carry about 17
-// significant bits (|x - x_hi - x_lo| <= 2^-18 |x|), between BF16 (8) and
+// significant bits (|x - x_hi - x_lo| <= 2^-17 |x|), between BF16 (8) and
 // FP32 (24), with FP32 accumulation.
 //
-// Operands are staged into shared memory in the canonical K-major,
-// no-swizzle layout: 8-row x 16-byte core matrices, rows 16 B apart, core
-// matrices adjacent in K 128 B apart (LBO) and adjacent in M/N
-// (b/8)*128 B apart (SBO).  Matrix blocks are stored row-major in HBM for
-// this path, so a block row of 8 BF16 values is one 16-byte copy.
+// Operands live in shared memory in the canonical K-major, no-swizzle
+// layout: 8-row x 16-byte core matrices, rows 16 B apart, core matrices
+// adjacent in K 128 B apart (LBO) and adjacent in M/N (b/8)*128 B apart
+// (SBO).  Matrix blocks are stored in HBM already as these operand images
+// (setup splits FP32 blocks into hi / lo), so they are staged by one bulk
+// copy each and never touched by the CTA's threads; the X_j slabs arrive as
+// FP32 and are split into the hi / lo images in shared memory.
 //
-// One CTA of 128 threads (4 warps) owns one block row at a time; thread 0
-// issues the MMAs and commits them to an mbarrier; all threads wait on it
-// with a bounded spin, then warp w reads TMEM lanes 32w..32w+31 (one right-
-// hand side per lane) and applies the fused epilogue.  Several CTAs share an
-// SM (TMEM 32 or 64 columns each), which overlaps staging with MMAs.
+// One CTA has three roles that hand work on through mbarriers only (no CTA
+// barrier inside the loop):
+//   warp 0 (one thread)   bulk-copies the X_j slab and A_ij image of each
+//                         (block row, block) item into a deep ring of raw
+//                         stages;
+//   warp 1 (one thread)   issues the MMAs of an item once its X operand is
+//                         converted, commits its raw and operand stages back,
+//                         and at the end of a block row commits the row's
+//                         accumulator (two accumulators in TMEM alternate);
+//   warps 2..5            convert each item's X_j slab to the hi / lo BF16
+//                         operands (a 2-deep operand ring), and -- one block
+//                         row behind -- read the finished accumulator from
+//                         TMEM (warp w: lanes 32*(w%4)..+31, one right-hand
+//                         side per lane) and apply the fused epilogue.
+// Every wait is bounded; a role that gives up raises the CTA's abort flag,
+// the others see it in their own waits, and the CTA drains its own copies
+// and MMAs (bounded) before it frees TMEM and exits with the error flag set.
 #include "kernels.h"
 
 #include <cuda_bf16.h>
@@ -37,8 +51,11 @@ namespace ldgmg {
 
 namespace {
 
-constexpr int kTcThreads = 128;
 constexpr int kTcM = 128;
+constexpr int kConvThreads = 128;                   // warps 2..5: conversion and epilogue
+constexpr int kTcThreads = 64 + kConvThreads;       // + copy warp 0 and MMA warp 1
+constexpr uint32_t kCtrlBytes = 256;                // 24 mbarriers, TMEM address, abort flag
+constexpr uint32_t kSmemCap = 227 * 1024;           // dynamic shared memory per CTA
 constexpr unsigned kSpinLimit = 1u << 20;   // bounded waits: error flag instead of a hang
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -124,6 +141,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // 1D bulk copy global -> shared, completion counted on `bar` (16-byte aligned, size % 16 == 0)
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -140,55 +161,98 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+// bounded wait that also gives up as soon as another role of the CTA has;
+// giving up raises the CTA's abort flag and the caller-visible error flag
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (++spins > kSpinLimit) {
+      *abort_flag = 1;
+      if (err) atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
 __host__ __device__ __forceinline__ uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
 
-// Shared-memory plan of one CTA for b = B, R right-hand sides.
+// Shared-memory plan of one CTA for b = B, R right-hand sides:
+//   NO operand stages   [X hi | X lo]          (BF16, M = 128 rows each)
+//   NR raw stages       [raw X_j slab | A_ij image(s)]
+//   control words       mbarriers, TMEM address, abort flag
+// Raw stages are cheap, so there are many of them (the copies in flight hide
+// HBM latency); a raw stage is held until the MMAs that read its A image are
+// done.  b = 16 CTAs are sized so that four fit on an SM.
 template <int B, bool SPLIT>
 struct TcPlan {
   static constexpr int KQ = B / 8;
-  static constexpr uint32_t A_BYTES = kTcM * B * 2;             // one BF16 part of X^T
-  static constexpr uint32_t B_BYTES = B * B * 2;                // one BF16 part of A_ij
-  static constexpr uint32_t OP_BYTES = 2 * A_BYTES + (SPLIT ? 2 : 1) * B_BYTES;
-  static constexpr uint32_t RAWA_BYTES = B * B * (SPLIT ? 4 : 2);
+  static constexpr int NO = 2;
+  static constexpr int kMaxRaw = 8;
+  static constexpr uint32_t OPX_BYTES = kTcM * B * 2;                  // one BF16 part of X^T (M = 128 rows)
+  static constexpr uint32_t OP_BYTES = 2 * OPX_BYTES;
+  static constexpr uint32_t IMG1 = B * B * 2;                          // one BF16 image of A_ij
+  static constexpr uint32_t IMG_BYTES = IMG1 * (SPLIT ? 2 : 1);        // as stored in HBM
+  static constexpr uint32_t BUDGET = B == 16 ? kSmemCap / 4 - 1024 : kSmemCap - 1024;
   __host__ __device__ static uint32_t rawx_bytes(int R) { return round128(uint32_t(R) * B * 4); }
+  __host__ __device__ static uint32_t raw_bytes(int R) { return rawx_bytes(R) + round128(IMG_BYTES); }
+  __host__ __device__ static int raw_stages(int R) {
+    const uint32_t fit = (BUDGET - kCtrlBytes - NO * OP_BYTES) / raw_bytes(R);
+    return int(fit < 2 ? 2 : (fit > uint32_t(kMaxRaw) ? uint32_t(kMaxRaw) : fit));
+  }
   __host__ __device__ static uint32_t total(int R) {
-    return 2 * OP_BYTES + 2 * RAWA_BYTES + 2 * rawx_bytes(R) + 128;
+    return NO * OP_BYTES + uint32_t(raw_stages(R)) * raw_bytes(R) + kCtrlBytes;
   }
 };
 
-// Software pipeline over the flattened sequence of (block row, block) items of
-// this CTA: thread 0 keeps the raw X_j slab and matrix block of the next two
-// items in flight with bulk copies (raw buffers 0/1), all threads convert the
-// current item into BF16 core-matrix operands (operand buffers 0/1) while the
-// tensor cores still work on the previous item, and thread 0 issues the MMAs.
+// ring position: stage index and the parity of its current use
+struct Ring {
+  int s = 0;
+  uint32_t ph = 0;
+  __device__ __forceinline__ void next(int n) {
+    if (++s == n) { s = 0; ph ^= 1u; }
+  }
+};
+
 template <int B, bool SPLIT>
 __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   static_assert(B == 16 || B == 64, "tensor-core path supports b = 16 and b = 64");
   typedef TcPlan<B, SPLIT> P;
   constexpr int KQ = P::KQ;
+  constexpr int NO = P::NO;
   constexpr int KSTEPS = B / 16;
-  constexpr uint32_t NCOLS = B < 32 ? 32 : B;
+  constexpr uint32_t NACC = B < 32 ? 32 : B;     // TMEM columns of one accumulator
+  constexpr uint32_t NCOLS = 2 * NACC;
   constexpr uint32_t IDESC = make_idesc(kTcM, B);
   constexpr uint32_t SBO = KQ * 128;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int R = a.R;
-  const uint32_t rawx_bytes = P::rawx_bytes(R);
-  // operand buffer bf at smem + bf*OP_BYTES; raw buffers after them
-  auto op = [&](int bf) { return smem + bf * P::OP_BYTES; };
-  auto rawa = [&](int bf) { return smem + 2 * P::OP_BYTES + bf * P::RAWA_BYTES; };
-  auto rawx = [&](int bf) { return smem + 2 * P::OP_BYTES + 2 * P::RAWA_BYTES + bf * rawx_bytes; };
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + P::total(R) - 128);   // full[0..1], mma[2..3]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  const int NR = P::raw_stages(R);
+  const uint32_t raw_b = P::raw_bytes(R);
+  const uint32_t xbytes = uint32_t(R) * B * 4;
+  auto opx = [&](int s) { return smem + s * P::OP_BYTES; };                       // X hi; X lo at + OPX_BYTES
+  auto rawx = [&](int s) { return smem + NO * P::OP_BYTES + s * raw_b; };
+  auto img = [&](int s) { return smem + NO * P::OP_BYTES + s * raw_b + P::rawx_bytes(R); };
+  unsigned char* ctrl = smem + NO * P::OP_BYTES + NR * raw_b;
+  uint64_t* rfull = reinterpret_cast<uint64_t*>(ctrl);   // raw stage landed (transaction count)
+  uint64_t* rempty = rfull + P::kMaxRaw;                   // MMAs reading the raw stage's A image done (commit)
+  uint64_t* ofull = rempty + P::kMaxRaw;                   // X operand converted (kConvThreads arrivals)
+  uint64_t* oempty = ofull + NO;                           // MMAs reading the operand stage done (commit)
+  uint64_t* accfull = oempty + NO;                         // a block row's products complete (commit)
+  uint64_t* accempty = accfull + 2;                        // accumulator read out (kConvThreads arrivals)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + 224);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctrl + 228);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // rows of absent right-hand sides stay zero in both operand buffers
-  for (int t = tid; t < kTcM * KQ; t += kTcThreads) {
-    const int m = t / KQ, kq = t % KQ;
-    if (m >= R)
-      for (int bf = 0; bf < 2; ++bf) {
-        *reinterpret_cast<uint4*>(op(bf) + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4*>(op(bf) + P::A_BYTES + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
-      }
+  // rows of absent right-hand sides stay zero in every operand stage
+  for (int t = tid; t < NO * kTcM * KQ; t += kTcThreads) {
+    const int s = t / (kTcM * KQ), e = t % (kTcM * KQ);
+    const int m = e / KQ, kq = e % KQ;
+    if (m >= R) {
+      *reinterpret_cast<uint4*>(opx(s) + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(opx(s) + P::OPX_BYTES + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
+    }
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -197,7 +261,19 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(bars + i, 1);
+    for (int i = 0; i < P::kMaxRaw; ++i) {
+      mbar_init(rfull + i, 1);
+      mbar_init(rempty + i, 1);
+    }
+    for (int i = 0; i < NO; ++i) {
+      mbar_init(ofull + i, kConvThreads);
+      mbar_init(oempty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(accfull + i, 1);
+      mbar_init(accempty + i, kConvThreads);
+    }
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   fence_proxy_async();
@@ -206,163 +282,177 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // lookahead iterator over items (only thread 0 advances it)
-  int64_t la_row = blockIdx.x;
-  int la_nz = 0, la_z1 = 0;
-  if (la_row < a.nrows) { la_nz = a.row_ptr[la_row]; la_z1 = a.row_ptr[la_row + 1]; }
-  auto la_skip_empty = [&]() {
-    while (la_row < a.nrows && la_nz >= la_z1) {
-      la_row += gridDim.x;
-      if (la_row < a.nrows) { la_nz = a.row_ptr[la_row]; la_z1 = a.row_ptr[la_row + 1]; }
-    }
-  };
-  const uint32_t item_bytes = uint32_t(R) * B * 4 + P::RAWA_BYTES;
-  auto issue = [&](int bf) {     // thread 0: copies of the lookahead item into raw buffer bf
-    la_skip_empty();
-    if (la_row >= a.nrows) return false;
-    const int64_t j = a.col[la_nz];
-    mbar_arrive_expect_tx(bars + bf, item_bytes);
-    bulk_g2s(rawx(bf), a.x + j * a.es, uint32_t(R) * B * 4, bars + bf);
-    bulk_g2s(rawa(bf), static_cast<const unsigned char*>(a.vals) + int64_t(la_nz) * P::RAWA_BYTES, P::RAWA_BYTES,
-             bars + bf);
-    ++la_nz;
-    return true;
-  };
-  int issued = 0;                // items whose copies were issued (thread 0's count)
-  if (tid == 0) {
-    if (issue(0)) ++issued;
-    if (issue(1)) ++issued;
-  }
-
-  // per buffer: bit bf of fph / mph = phase parity to wait for; bit bf of pend = MMA outstanding
-  uint32_t fph = 0, mph = 0, pend = 0;
-  int consumed = 0;              // items converted so far
-  bool timed_out = false;
-
-  for (int64_t row = blockIdx.x; row < a.nrows && !timed_out; row += gridDim.x) {
-    const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
-    for (int nz = z0; nz < z1; ++nz) {
-      const int bf = consumed & 1;
-      bool ok = mbar_wait_bounded(bars + bf, (fph >> bf) & 1u);                        // raw data of this item
-      if (ok && ((pend >> bf) & 1u)) ok = mbar_wait_bounded(bars + 2 + bf, (mph >> bf) & 1u);   // operands free
-      if (__syncthreads_or(!ok)) { timed_out = true; break; }
-      fph ^= 1u << bf;
-      if ((pend >> bf) & 1u) { mph ^= 1u << bf; pend &= ~(1u << bf); }
-      // convert: X_j^T -> hi/lo BF16 (A operand), A_ij -> BF16 (hi [, lo]) (B operand)
-      unsigned char* o = op(bf);
-      const float* xr = reinterpret_cast<const float*>(rawx(bf));
-      // one float4 (4 modes of one right-hand side) per thread: consecutive
-      // 16-byte reads, 8-byte stores that tile the core matrices without conflicts
-      for (int t = tid; t < R * (B / 4); t += kTcThreads) {
-        const int m = t / (B / 4), q4 = t % (B / 4);
-        const float4 v = *reinterpret_cast<const float4*>(xr + m * B + q4 * 4);
-        const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
-        const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
-        const uint32_t off = core_off(m, q4 >> 1, KQ) + (q4 & 1) * 8;
-        *reinterpret_cast<uint2*>(o + off) =
-            make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
-        *reinterpret_cast<uint2*>(o + P::A_BYTES + off) =
-            make_uint2(pack_bf16(v.x - f0.x, v.y - f0.y), pack_bf16(v.z - f1.x, v.w - f1.y));
-      }
-      unsigned char* bo = o + 2 * P::A_BYTES;
-      if (!SPLIT) {
-        const uint4* ra = reinterpret_cast<const uint4*>(rawa(bf));
-        for (int t = tid; t < B * KQ; t += kTcThreads) {
-          const int r = t / KQ, kq = t % KQ;
-          *reinterpret_cast<uint4*>(bo + core_off(r, kq, KQ)) = ra[t];
+  if (warp == 0) {
+    // ---- copier: item k goes to raw stage k % NR once the MMAs of item k - NR are done
+    if (lane == 0) {
+      int64_t k = 0;
+      Ring r;
+      bool ok = true;
+      for (int64_t row = blockIdx.x; row < a.nrows && ok; row += gridDim.x) {
+        const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
+        for (int nz = z0; nz < z1; ++nz, ++k) {
+          if (k >= NR && !wait_or_abort(rempty + r.s, r.ph ^ 1u, abort_flag, a.err)) { ok = false; break; }
+          mbar_arrive_expect_tx(rfull + r.s, xbytes + P::IMG_BYTES);
+          bulk_g2s(rawx(r.s), a.x + int64_t(a.col[nz]) * a.es, xbytes, rfull + r.s);
+          bulk_g2s(img(r.s), static_cast<const unsigned char*>(a.vals) + int64_t(nz) * P::IMG_BYTES, P::IMG_BYTES,
+                   rfull + r.s);
+          r.next(NR);
         }
-      } else {
-        const float4* ra = reinterpret_cast<const float4*>(rawa(bf));
-        for (int t = tid; t < B * (B / 4); t += kTcThreads) {
-          const int r = t / (B / 4), q4 = t % (B / 4);
-          const float4 v = ra[t];
+      }
+      if (!ok || *abort_flag) {
+        // bounded drain of this CTA's copies in flight before shared memory goes away
+        for (int s = 0; s < NR && s < k; ++s) {
+          const int64_t cnt = k / NR + (s < k % NR ? 1 : 0);     // copies issued into stage s
+          mbar_wait_bounded(rfull + s, uint32_t(cnt - 1) & 1u);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: Y_i^T += X_j^T A_ij^T per item, accumulator t % 2 for the t-th non-empty row
+    if (lane == 0) {
+      int64_t t = 0;
+      Ring r, o, last;
+      bool ok = true, any = false;
+      for (int64_t row = blockIdx.x; row < a.nrows && ok; row += gridDim.x) {
+        const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
+        if (z0 == z1) continue;
+        const int acc = int(t & 1);
+        if (t >= 2 && !wait_or_abort(accempty + acc, uint32_t((t >> 1) - 1) & 1u, abort_flag, a.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + uint32_t(acc) * NACC;
+        for (int nz = z0; nz < z1; ++nz) {
+          if (!wait_or_abort(rfull + r.s, r.ph, abort_flag, a.err) ||
+              !wait_or_abort(ofull + o.s, o.ph, abort_flag, a.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(opx(o.s)), sb = smem_u32(img(r.s));
+#pragma unroll
+          for (int ks = 0; ks < KSTEPS; ++ks) {
+            const uint64_t ah = make_sdesc(sa + 256u * ks, 128u, SBO);
+            const uint64_t bd = make_sdesc(sb + 256u * ks, 128u, SBO);
+            mma_bf16(d, ah, bd, IDESC, (nz > z0 || ks > 0) ? 1u : 0u);
+            mma_bf16(d, make_sdesc(sa + P::OPX_BYTES + 256u * ks, 128u, SBO), bd, IDESC, 1u);
+            if (SPLIT) mma_bf16(d, ah, make_sdesc(sb + P::IMG1 + 256u * ks, 128u, SBO), IDESC, 1u);
+          }
+          mma_commit(rempty + r.s);
+          mma_commit(oempty + o.s);
+          last = o;
+          any = true;
+          r.next(NR);
+          o.next(NO);
+        }
+        if (!ok) break;
+        mma_commit(accfull + acc);
+        ++t;
+      }
+      // after giving up: bounded wait for the MMAs already issued (the last commit covers them)
+      if (!ok && any) mbar_wait_bounded(oempty + last.s, last.ph);
+    }
+  } else {
+    // ---- conversion and epilogue (warps 2..5)
+    const int ct = tid - 64;
+    const int quad = warp & 3;                 // the TMEM lane quarter this warp may read
+    const int m = quad * 32 + lane;            // this thread's right-hand side in the epilogue
+    // y_i = epilogue(acc_i) for block row `row`; from TMEM accumulator t % 2, or zero for an empty row
+    auto epilogue = [&](int64_t row, int64_t t, bool empty_row) -> bool {
+      const int acc = int(t & 1);
+      if (!empty_row) {
+        const bool w = wait_or_abort(accfull + acc, uint32_t(t >> 1) & 1u, abort_flag, a.err);
+        if (__any_sync(0xffffffffu, !w)) return false;
+        tc_fence_after();
+      }
+#pragma unroll
+      for (int c0 = 0; c0 < B; c0 += 16) {
+        float v[16];
+        if (!empty_row) {
+          tmem_ld16(tmem + (uint32_t(quad * 32) << 16) + uint32_t(acc) * NACC + uint32_t(c0), v);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = 0.0f;
+        }
+        if (m < R) {
+          const int64_t o = row * a.es + int64_t(m) * a.rs + c0;
+          const float sc = float(a.s);
+#pragma unroll
+          for (int q = 0; q < 16; q += 4) {
+            float4 y = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+            if (a.mode == M_RES) {
+              const float4 rr = *reinterpret_cast<const float4*>(a.rhs + o + q);
+              y = make_float4(rr.x - y.x, rr.y - y.y, rr.z - y.z, rr.w - y.w);
+            } else if (a.mode == M_AXPY) {
+              const float4 xi = *reinterpret_cast<const float4*>(a.xin + o + q);
+              y = make_float4(xi.x + sc * y.x, xi.y + sc * y.y, xi.z + sc * y.z, xi.w + sc * y.w);
+            } else if (a.mode != M_Y) {
+              y = make_float4(sc * y.x, sc * y.y, sc * y.z, sc * y.w);
+            }
+            *reinterpret_cast<float4*>(a.y + o + q) = y;
+          }
+        }
+      }
+      if (!empty_row) {
+        tc_fence_before();
+        mbar_arrive(accempty + acc);
+      }
+      return true;
+    };
+    int64_t k = 0, t = 0, prev_row = -1, prev_t = 0;
+    Ring r, o;
+    bool ok = true;
+    for (int64_t row = blockIdx.x; row < a.nrows && ok; row += gridDim.x) {
+      const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
+      for (int nz = z0; nz < z1; ++nz, ++k) {
+        bool w = wait_or_abort(rfull + r.s, r.ph, abort_flag, a.err);
+        if (w && k >= NO) w = wait_or_abort(oempty + o.s, o.ph ^ 1u, abort_flag, a.err);
+        if (__any_sync(0xffffffffu, !w)) { ok = false; break; }
+        // X_j^T -> hi / lo BF16 operands: one float4 (4 modes of one right-hand
+        // side) per step, 16-byte reads, 8-byte stores that tile the core
+        // matrices without bank conflicts
+        const float* xr = reinterpret_cast<const float*>(rawx(r.s));
+        unsigned char* op = opx(o.s);
+        for (int e = ct; e < R * (B / 4); e += kConvThreads) {
+          const int mm = e / (B / 4), q4 = e % (B / 4);
+          const float4 v = *reinterpret_cast<const float4*>(xr + mm * B + q4 * 4);
           const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
           const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
-          const uint32_t off = core_off(r, q4 >> 1, KQ) + (q4 & 1) * 8;
-          *reinterpret_cast<uint2*>(bo + off) =
+          const uint32_t off = core_off(mm, q4 >> 1, KQ) + (q4 & 1) * 8;
+          *reinterpret_cast<uint2*>(op + off) =
               make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
-          *reinterpret_cast<uint2*>(bo + P::B_BYTES + off) =
+          *reinterpret_cast<uint2*>(op + P::OPX_BYTES + off) =
               make_uint2(pack_bf16(v.x - f0.x, v.y - f0.y), pack_bf16(v.z - f1.x, v.w - f1.y));
         }
+        fence_proxy_async();     // operands visible to the tensor cores; raw reads ordered before new copies
+        mbar_arrive(ofull + o.s);
+        r.next(NR);
+        o.next(NO);
       }
-      fence_proxy_async();     // operands visible to the tensor cores; raw reads ordered before new copies
-      __syncthreads();
-      if (tid == 0) {
-        if (issue(bf)) ++issued;                         // raw buffer bf is free again
-        tc_fence_after();
-        const uint32_t sa = smem_u32(o), sbh = smem_u32(bo);
-#pragma unroll
-        for (int s = 0; s < KSTEPS; ++s) {
-          const uint64_t ah = make_sdesc(sa + 256u * s, 128u, SBO);
-          const uint64_t bd = make_sdesc(sbh + 256u * s, 128u, SBO);
-          mma_bf16(tmem, ah, bd, IDESC, (nz > z0 || s > 0) ? 1u : 0u);
-          mma_bf16(tmem, make_sdesc(sa + P::A_BYTES + 256u * s, 128u, SBO), bd, IDESC, 1u);
-          if (SPLIT) mma_bf16(tmem, ah, make_sdesc(sbh + P::B_BYTES + 256u * s, 128u, SBO), IDESC, 1u);
-        }
-        mma_commit(bars + 2 + bf);
+      if (!ok) break;
+      // the previous non-empty row's accumulator, one row behind the conversions
+      if (prev_row >= 0) {
+        if (!epilogue(prev_row, prev_t, false)) { ok = false; break; }
+        prev_row = -1;
       }
-      pend |= 1u << bf;
-      ++consumed;
-    }
-    if (timed_out) break;
-    // the row's products are complete once both operand buffers' MMAs are
-    bool ok = true;
-    if (ok && (pend & 1u)) ok = mbar_wait_bounded(bars + 2, mph & 1u);
-    if (ok && (pend & 2u)) ok = mbar_wait_bounded(bars + 3, (mph >> 1) & 1u);
-    if (__syncthreads_or(!ok)) { timed_out = true; break; }
-    mph ^= pend;
-    pend = 0;
-    tc_fence_after();
-    // epilogue: warp w holds right-hand sides 32w..32w+31, one per lane
-    const int m = warp * 32 + lane;
-    const bool empty = (z1 == z0);
-#pragma unroll
-    for (int c0 = 0; c0 < B; c0 += 16) {
-      float acc[16];
-      tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(c0), acc);
-      if (m < R) {
-        const int64_t o = row * a.es + int64_t(m) * a.rs + c0;
-#pragma unroll
-        for (int q = 0; q < 16; q += 4) {
-          float4 y;
-          float* yy = reinterpret_cast<float*>(&y);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float sv = empty ? 0.0f : acc[q + e];
-            float out;
-            switch (a.mode) {
-              case M_Y: out = sv; break;
-              case M_RES: out = a.rhs[o + q + e] - sv; break;
-              case M_AXPY: out = a.xin[o + q + e] + float(a.s) * sv; break;
-              default: out = float(a.s) * sv; break;
-            }
-            yy[e] = out;
-          }
-          *reinterpret_cast<float4*>(a.y + o + q) = y;
-        }
+      if (z0 == z1) {
+        epilogue(row, 0, true);
+      } else {
+        prev_row = row;
+        prev_t = t++;
       }
     }
-    tc_fence_before();
-    __syncthreads();
+    if (ok && prev_row >= 0) epilogue(prev_row, prev_t, false);
   }
-  if (timed_out) {
-    if (tid == 0 && a.err) atomicExch(a.err, 1);
-    // bounded drain of this CTA's own copies and MMAs before TMEM and shared memory go away
-    if (tid == 0) {
-      for (int k = consumed; k < issued; ++k) {
-        const int bf = k & 1;
-        mbar_wait_bounded(bars + bf, (fph >> bf) & 1u);
-        fph ^= 1u << bf;
-      }
-      if (pend & 1u) mbar_wait_bounded(bars + 2, mph & 1u);
-      if (pend & 2u) mbar_wait_bounded(bars + 3, (mph >> 1) & 1u);
-    }
-  }
+
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0)
+  if (warp == 0) {
+    __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+  }
 }
 
 // Self-test of the bounded-wait error path: one thread waits on an mbarrier
@@ -393,7 +483,7 @@ static int max_ctas(int R) {
   typedef TcPlan<B, SPLIT> P;
   const int smem = int(P::total(R));
   const int by_smem = (227 * 1024) / (smem + 1024);
-  const int by_tmem = 512 / (B < 32 ? 32 : B);
+  const int by_tmem = 512 / (2 * (B < 32 ? 32 : B));
   const int by_threads = 2048 / kTcThreads;
   return std::max(1, std::min(by_smem, std::min(by_tmem, by_threads)));
 }
@@ -413,7 +503,7 @@ static cudaError_t launch_tc(const BatchArgs& a, cudaStream_t st) {
   static cudaError_t cfg = cudaSuccess;
   std::call_once(once, [] {
     cfg = cudaFuncSetAttribute(bsr_tc_kernel<B, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(P::total(kTcM)));
+                               int(kSmemCap - 1024));
   });
   if (cfg != cudaSuccess) return cfg;
   const int fit = max_ctas<B, SPLIT>(a.R);

@@ -1,8 +1,9 @@
 """Batched right-hand sides: tensor-core block apply and batched CG (GPU).
 
-  * The tcgen05 apply (BF16 row-major blocks, FP32 vectors split into hi/lo
-    BF16 parts, FP32 accumulation in tensor memory) matches the FP64 product
-    of the stored BF16 blocks to 1e-5 relative for R = 1 ... 128.
+  * The tcgen05 apply (blocks stored as BF16 operand images -- hi and lo for
+    FP32 storage --, FP32 vectors split into hi/lo BF16 parts, FP32
+    accumulation in tensor memory) matches the FP64 product of the stored
+    blocks to 1e-5 relative for R = 1 ... 128.
   * A batched solve gives every right-hand side the same iterate, bit for bit,
     as solving it alone (per-RHS scalars, converged RHS frozen), reaches the
     1e-10 residual, and agrees with the FP64 oracle solution.
