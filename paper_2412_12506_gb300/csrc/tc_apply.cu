@@ -32,7 +32,7 @@
 //                         and at the end of a block row commits the row's
 //                         accumulator (two accumulators in TMEM alternate);
 //   warps 2..5            convert each item's X_j slab to the hi / lo BF16
-//                         operands (a 2-deep operand ring), and -- one block
+//                         operands (a 3-deep operand ring), and -- one block
 //                         row behind -- read the finished accumulator from
 //                         TMEM (warp w: lanes 32*(w%4)..+31, one right-hand
 //                         side per lane) and apply the fused epilogue.
@@ -54,7 +54,7 @@ namespace {
 constexpr int kTcM = 128;
 constexpr int kConvThreads = 128;                   // warps 2..5: conversion and epilogue
 constexpr int kTcThreads = 64 + kConvThreads;       // + copy warp 0 and MMA warp 1
-constexpr uint32_t kCtrlBytes = 256;                // 24 mbarriers, TMEM address, abort flag
+constexpr uint32_t kCtrlBytes = 256;                // 26 mbarriers, TMEM address, abort flag
 constexpr uint32_t kSmemCap = 227 * 1024;           // dynamic shared memory per CTA
 constexpr unsigned kSpinLimit = 1u << 20;   // bounded waits: error flag instead of a hang
 
@@ -179,16 +179,16 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
 __host__ __device__ __forceinline__ uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
 
 // Shared-memory plan of one CTA for b = B, R right-hand sides:
-//   NO operand stages   [X hi | X lo]          (BF16, M = 128 rows each)
-//   NR raw stages       [raw X_j slab | A_ij image(s)]
-//   control words       mbarriers, TMEM address, abort flag
+//   NO = 3 operand stages   [X hi | X lo]      (BF16, M = 128 rows each)
+//   NR raw stages           [raw X_j slab | A_ij image(s)]
+//   control words           mbarriers, TMEM address, abort flag
 // Raw stages are cheap, so there are many of them (the copies in flight hide
 // HBM latency); a raw stage is held until the MMAs that read its A image are
 // done.  b = 16 CTAs are sized so that four fit on an SM.
 template <int B, bool SPLIT>
 struct TcPlan {
   static constexpr int KQ = B / 8;
-  static constexpr int NO = 2;
+  static constexpr int NO = 3;
   static constexpr int kMaxRaw = 8;
   static constexpr uint32_t OPX_BYTES = kTcM * B * 2;                  // one BF16 part of X^T (M = 128 rows)
   static constexpr uint32_t OP_BYTES = 2 * OPX_BYTES;
@@ -203,6 +203,29 @@ struct TcPlan {
   }
   __host__ __device__ static uint32_t total(int R) {
     return NO * OP_BYTES + uint32_t(raw_stages(R)) * raw_bytes(R) + kCtrlBytes;
+  }
+};
+
+// The rows of one CTA (blockIdx.x, + gridDim.x, ...) with the extent of the
+// current row and, already loaded, of the next one: the row_ptr loads of a
+// row are in flight while the previous row is processed.
+struct RowCursor {
+  int64_t row;
+  int z0 = 0, z1 = 0, n0 = 0, n1 = 0;
+  __device__ __forceinline__ RowCursor(const BatchArgs& a, int64_t first) : row(first) {
+    if (row < a.nrows) { z0 = a.row_ptr[row]; z1 = a.row_ptr[row + 1]; }
+    fetch_next(a);
+  }
+  __device__ __forceinline__ void fetch_next(const BatchArgs& a) {
+    const int64_t nr = row + gridDim.x;
+    n0 = n1 = 0;
+    if (nr < a.nrows) { n0 = a.row_ptr[nr]; n1 = a.row_ptr[nr + 1]; }
+  }
+  __device__ __forceinline__ void advance(const BatchArgs& a) {
+    row += gridDim.x;
+    z0 = n0;
+    z1 = n1;
+    fetch_next(a);
   }
 };
 
@@ -288,16 +311,22 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
       int64_t k = 0;
       Ring r;
       bool ok = true;
-      for (int64_t row = blockIdx.x; row < a.nrows && ok; row += gridDim.x) {
-        const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
+      RowCursor rc(a, blockIdx.x);
+      int col0 = rc.z0 < rc.z1 ? a.col[rc.z0] : 0;
+      for (; rc.row < a.nrows && ok; rc.advance(a)) {
+        const int z0 = rc.z0, z1 = rc.z1;
+        // the next row's extent is in flight (RowCursor); fetch its first block column early too
+        const int ncol0 = rc.n0 < rc.n1 ? a.col[rc.n0] : 0;
         for (int nz = z0; nz < z1; ++nz, ++k) {
           if (k >= NR && !wait_or_abort(rempty + r.s, r.ph ^ 1u, abort_flag, a.err)) { ok = false; break; }
+          const int j = nz == z0 ? col0 : a.col[nz];
           mbar_arrive_expect_tx(rfull + r.s, xbytes + P::IMG_BYTES);
-          bulk_g2s(rawx(r.s), a.x + int64_t(a.col[nz]) * a.es, xbytes, rfull + r.s);
+          bulk_g2s(rawx(r.s), a.x + int64_t(j) * a.es, xbytes, rfull + r.s);
           bulk_g2s(img(r.s), static_cast<const unsigned char*>(a.vals) + int64_t(nz) * P::IMG_BYTES, P::IMG_BYTES,
                    rfull + r.s);
           r.next(NR);
         }
+        col0 = ncol0;
       }
       if (!ok || *abort_flag) {
         // bounded drain of this CTA's copies in flight before shared memory goes away
@@ -313,8 +342,8 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
       int64_t t = 0;
       Ring r, o, last;
       bool ok = true, any = false;
-      for (int64_t row = blockIdx.x; row < a.nrows && ok; row += gridDim.x) {
-        const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
+      for (RowCursor rc(a, blockIdx.x); rc.row < a.nrows && ok; rc.advance(a)) {
+        const int z0 = rc.z0, z1 = rc.z1;
         if (z0 == z1) continue;
         const int acc = int(t & 1);
         if (t >= 2 && !wait_or_abort(accempty + acc, uint32_t((t >> 1) - 1) & 1u, abort_flag, a.err)) {
@@ -403,18 +432,22 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
     int64_t k = 0, t = 0, prev_row = -1, prev_t = 0;
     Ring r, o;
     bool ok = true;
-    for (int64_t row = blockIdx.x; row < a.nrows && ok; row += gridDim.x) {
-      const int z0 = a.row_ptr[row], z1 = a.row_ptr[row + 1];
+    for (RowCursor rc(a, blockIdx.x); rc.row < a.nrows && ok; rc.advance(a)) {
+      const int64_t row = rc.row;
+      const int z0 = rc.z0, z1 = rc.z1;
       for (int nz = z0; nz < z1; ++nz, ++k) {
         bool w = wait_or_abort(rfull + r.s, r.ph, abort_flag, a.err);
         if (w && k >= NO) w = wait_or_abort(oempty + o.s, o.ph ^ 1u, abort_flag, a.err);
         if (__any_sync(0xffffffffu, !w)) { ok = false; break; }
         // X_j^T -> hi / lo BF16 operands: one float4 (4 modes of one right-hand
         // side) per step, 16-byte reads, 8-byte stores that tile the core
-        // matrices without bank conflicts
+        // matrices without bank conflicts; unrolled so the steps overlap
         const float* xr = reinterpret_cast<const float*>(rawx(r.s));
         unsigned char* op = opx(o.s);
-        for (int e = ct; e < R * (B / 4); e += kConvThreads) {
+#pragma unroll 4
+        for (int i = 0; i < kTcM * (B / 4) / kConvThreads; ++i) {
+          const int e = ct + i * kConvThreads;
+          if (e >= R * (B / 4)) break;
           const int mm = e / (B / 4), q4 = e % (B / 4);
           const float4 v = *reinterpret_cast<const float4*>(xr + mm * B + q4 * 4);
           const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
