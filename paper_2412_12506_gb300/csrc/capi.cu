@@ -173,7 +173,7 @@ struct ldgmg_hier {
   int vprec = 0;         // 0: double level vectors, 1: float
   size_t vsz = 8;
   int Rmax = 1;          // right-hand sides per call
-  bool batched = false;  // tensor-core hierarchy (row-major BF16 blocks)
+  bool batched = false;  // tensor-core hierarchy (blocks stored as operand images)
   bool use_df = false;   // batched outer apply in double-FP32 arithmetic
   std::vector<HostLevel> host;   // host[0] is unused (the op holds the finest level)
   std::vector<DevLevel> lv;
@@ -196,6 +196,8 @@ struct ldgmg_hier {
   size_t dev_bytes = 0;          // device memory held by this handle
   // autotuned launch shape of the tensor-core apply (CTAs per SM; 0 = all that fit)
   int tc_ctas = 0;
+  void* ximg = nullptr;          // tensor-core path: operand images of the vector being applied
+  size_t ximg_bytes = 0;         // its capacity (level 0 at max_rhs; grown for wider inspection applies)
   double tc_ms = 0.0;            // its measured time on level 0 with max_rhs right-hand sides
   // residual history of the last solve: ||r_k||^2 of right-hand side r at
   // hist[k * R + r], k = 0..iters (device, CG) / host copy after the solve
@@ -231,6 +233,28 @@ static ldgmg_status apply_mat(ldgmg_hier* h, const DevMat& M, int mode, const vo
     a.row_ptr = M.row_ptr;
     a.col = M.col;
     a.vals = M.vals;
+    if (!h) return fail(LDGMG_EINVAL, "tensor-core apply without its hierarchy");
+    const size_t need = x_image_bytes(M.nrows, R, int(b));
+    if (need > h->ximg_bytes) {
+      // only ldgmg_level_apply_batched can ask for more right-hand sides than
+      // max_rhs; never inside a graph capture (V-cycles stay within max_rhs)
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return fail(LDGMG_EINVAL, "tensor-core image work space too small inside a capture");
+      CK(cudaDeviceSynchronize());        // no queued work may still read the old space
+      cudaFree(h->ximg);
+      h->ximg = nullptr;
+      h->dev_bytes -= h->ximg_bytes;
+      h->ximg_bytes = 0;
+      if (cudaMalloc(&h->ximg, need) != cudaSuccess) {
+        h->ximg = nullptr;
+        return fail(LDGMG_ENOMEM, "cudaMalloc(" + std::to_string(need) + " bytes) for tensor-core images");
+      }
+      h->ximg_bytes = need;
+      h->dev_bytes += need;
+    }
+    CK(split_x_images(static_cast<const float*>(x), M.nrows, R, int(b), h->ximg, st));
+    a.ximg = h->ximg;
     a.x = static_cast<const float*>(x);
     a.rhs = static_cast<const float*>(rhs);
     a.xin = static_cast<const float*>(xin);
@@ -447,6 +471,7 @@ void ldgmg_hier_free(ldgmg_hier* h) {
     cudaFree(v);
   cudaFree(h->active);
   cudaFree(h->err);
+  cudaFree(h->ximg);
   cudaFree(h->hist);
   cudaFree(h->gq);
   cudaFree(h->gz);
@@ -756,6 +781,10 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
       return bail(LDGMG_ENOMEM);
     if (cudaMallocHost((void**)&h->hgs, size_t(m + 2) * sizeof(double)) != cudaSuccess)
       return bail(fail(LDGMG_ENOMEM, "cudaMallocHost"));
+  }
+  if (batched) {
+    h->ximg_bytes = x_image_bytes(L0.N, h->Rmax, L0.b);
+    if (dalloc(&h->ximg, h->ximg_bytes) != LDGMG_OK) return bail(LDGMG_ENOMEM);
   }
   if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "memset"));
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "setup sync"));

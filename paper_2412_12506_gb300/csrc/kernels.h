@@ -59,6 +59,7 @@ struct BatchArgs {
   const int* row_ptr;
   const int* col;
   const void* vals;       // block operand images (BF16, or BF16 hi + lo for FP32 storage)
+  const void* ximg;       // operand images of x, written by split_x_images for this R
   const float* x;
   const float* rhs;
   const float* xin;
@@ -76,8 +77,17 @@ bool tc_block_size_supported(int b);
 cudaError_t bounded_wait_probe(int* err, cudaStream_t st);
 // most CTAs of the tensor-core kernel that fit on one SM for (b, prec, R)
 int tc_max_ctas_per_sm(int b, int prec, int R);
-// prec: P_BF16 (2 MMAs per K step) or P_FP32 (3 MMAs: A_hi x_hi + A_hi x_lo + A_lo x_hi)
+// prec: P_BF16 (2 MMAs per K step) or P_FP32 (3 MMAs: A_hi x_hi + A_hi x_lo + A_lo x_hi).
+// a.ximg must hold split_x_images(a.x) for the same R (a.x itself is not read).
 cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st);
+
+// Operand images of a batched vector x ([element][rhs][mode], R right-hand
+// sides, b = 16 or 64) for the tensor-core apply: per element j the image of
+// hi = bf16(x_j^T) and then that of lo = bf16(x_j^T - hi), each R_8 x b BF16
+// (R_8 = R rounded up to 8; rows R..R_8-1 zero) in the K-major core-matrix
+// layout of tc_image_offset (rows = right-hand sides, K = modes).
+size_t x_image_bytes(int64_t N, int R, int b);
+cudaError_t split_x_images(const float* x, int64_t N, int R, int b, void* ximg, cudaStream_t st);
 
 // vals[nz] = scale * pool[ids[nz]] converted to `prec`, stored column-major
 // with column stride cs (tc_image = 0; padding rows written as zero) or as

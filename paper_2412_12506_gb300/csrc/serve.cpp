@@ -120,8 +120,8 @@ namespace {
 // Device footprint of a class before it is built (admission); replaced by the
 // measured ldgmg_*_device_bytes once it is.  Block rows per level times stored
 // blocks per row times block bytes, for A, the smoother (B and B^T, or D),
-// level vectors, the FP64 outer operator and Krylov space, and the bottom
-// pseudo-inverse, plus 10%.
+// level vectors, the FP64 outer operator and Krylov space, the bottom
+// pseudo-inverse and (tensor-core classes) the operand images of x, plus 10%.
 size_t estimate(const ldgmg_server_opts& o, const Class& c) {
   const ClassKey& k = c.key;
   const int d = k.dim;
@@ -149,6 +149,8 @@ size_t estimate(const ldgmg_server_opts& o, const Class& c) {
     Nl /= double(1 << d);
   }
   total += double(c.N) * b * 8.0 * rmax * 8.0;           // CG vectors and staging
+  const bool tc = rmax > 1 && (c.b == 16 || c.b == 64) && vs == 4.0 && o.setup.smoother != LDGMG_GS;
+  if (tc) total += double(c.N) * b * 4.0 * double((rmax + 7) / 8 * 8);   // tensor-core operand images of x
   if (k.stokes >= 0) total += double(c.N) * b * 8.0 * (2.0 * o.setup.restart + 1.0);
   return size_t(total * 1.1);
 }

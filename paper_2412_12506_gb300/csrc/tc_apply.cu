@@ -17,25 +17,25 @@
 // Operands live in shared memory in the canonical K-major, no-swizzle
 // layout: 8-row x 16-byte core matrices, rows 16 B apart, core matrices
 // adjacent in K 128 B apart (LBO) and adjacent in M/N (b/8)*128 B apart
-// (SBO).  Matrix blocks are stored in HBM already as these operand images
-// (setup splits FP32 blocks into hi / lo), so they are staged by one bulk
-// copy each and never touched by the CTA's threads; the X_j slabs arrive as
-// FP32 and are split into the hi / lo images in shared memory.
+// (SBO).  Both factors arrive in HBM already as these operand images: the
+// matrix blocks since setup (FP32 blocks as hi and lo images), the vector
+// from split_x_images, a streaming pass that splits X into hi / lo once per
+// apply instead of once per use (each X_j is used by ~5 block rows).  So the
+// apply moves bytes and issues MMAs; no thread touches an operand.
 //
 // One CTA has three roles that hand work on through mbarriers only (no CTA
 // barrier inside the loop):
-//   warp 0 (one thread)   bulk-copies the X_j slab and A_ij image of each
-//                         (block row, block) item into a deep ring of raw
-//                         stages;
-//   warp 1 (one thread)   issues the MMAs of an item once its X operand is
-//                         converted, commits its raw and operand stages back,
-//                         and at the end of a block row commits the row's
+//   warp 0 (one thread)   bulk-copies the X_j hi / lo images and the A_ij
+//                         image(s) of each (block row, block) item into a
+//                         ring of stages;
+//   warp 1 (one thread)   issues the MMAs of an item once its stage has
+//                         landed, commits the stage back to the copier, and
+//                         at the end of a block row commits the row's
 //                         accumulator (two accumulators in TMEM alternate);
-//   warps 2..5            convert each item's X_j slab to the hi / lo BF16
-//                         operands (a 3-deep operand ring), and -- one block
-//                         row behind -- read the finished accumulator from
-//                         TMEM (warp w: lanes 32*(w%4)..+31, one right-hand
-//                         side per lane) and apply the fused epilogue.
+//   warps 2..5            read a finished accumulator from TMEM (warp w:
+//                         lanes 32*(w%4)..+31, one right-hand side per lane)
+//                         and apply the fused epilogue while the MMAs of the
+//                         next block row run.
 // Every wait is bounded; a role that gives up raises the CTA's abort flag,
 // the others see it in their own waits, and the CTA drains its own copies
 // and MMAs (bounded) before it frees TMEM and exits with the error flag set.
@@ -52,9 +52,9 @@ namespace ldgmg {
 namespace {
 
 constexpr int kTcM = 128;
-constexpr int kConvThreads = 128;                   // warps 2..5: conversion and epilogue
+constexpr int kConvThreads = 128;                   // warps 2..5: epilogue
 constexpr int kTcThreads = 64 + kConvThreads;       // + copy warp 0 and MMA warp 1
-constexpr uint32_t kCtrlBytes = 256;                // 26 mbarriers, TMEM address, abort flag
+constexpr uint32_t kCtrlBytes = 256;                // 20 mbarriers, TMEM address, abort flag
 constexpr uint32_t kSmemCap = 227 * 1024;           // dynamic shared memory per CTA
 constexpr unsigned kSpinLimit = 1u << 20;   // bounded waits: error flag instead of a hang
 
@@ -176,34 +176,22 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
   return true;
 }
 
-__host__ __device__ __forceinline__ uint32_t round128(uint32_t x) { return (x + 127u) & ~127u; }
-
-// Shared-memory plan of one CTA for b = B, R right-hand sides:
-//   NO = 3 operand stages   [X hi | X lo]      (BF16, M = 128 rows each)
-//   NR raw stages           [raw X_j slab | A_ij image(s)]
-//   control words           mbarriers, TMEM address, abort flag
-// Raw stages are cheap, so there are many of them (the copies in flight hide
-// HBM latency); a raw stage is held until the MMAs that read its A image are
-// done.  b = 16 CTAs are sized so that four fit on an SM.
+// Shared-memory plan of one CTA for b = B: NS stages, each
+//   [X hi | X lo (BF16, M = 128 rows each; rows >= R_8 stay zero) | A_ij image(s)]
+// then the control words (mbarriers, TMEM address, abort flag).  b = 16 CTAs
+// are sized so that four fit on an SM.
 template <int B, bool SPLIT>
 struct TcPlan {
   static constexpr int KQ = B / 8;
-  static constexpr int NO = 3;
-  static constexpr int kMaxRaw = 8;
+  static constexpr int kMaxStages = 8;
   static constexpr uint32_t OPX_BYTES = kTcM * B * 2;                  // one BF16 part of X^T (M = 128 rows)
-  static constexpr uint32_t OP_BYTES = 2 * OPX_BYTES;
   static constexpr uint32_t IMG1 = B * B * 2;                          // one BF16 image of A_ij
   static constexpr uint32_t IMG_BYTES = IMG1 * (SPLIT ? 2 : 1);        // as stored in HBM
+  static constexpr uint32_t STAGE = 2 * OPX_BYTES + ((IMG_BYTES + 127u) & ~127u);
   static constexpr uint32_t BUDGET = B == 16 ? kSmemCap / 4 - 1024 : kSmemCap - 1024;
-  __host__ __device__ static uint32_t rawx_bytes(int R) { return round128(uint32_t(R) * B * 4); }
-  __host__ __device__ static uint32_t raw_bytes(int R) { return rawx_bytes(R) + round128(IMG_BYTES); }
-  __host__ __device__ static int raw_stages(int R) {
-    const uint32_t fit = (BUDGET - kCtrlBytes - NO * OP_BYTES) / raw_bytes(R);
-    return int(fit < 2 ? 2 : (fit > uint32_t(kMaxRaw) ? uint32_t(kMaxRaw) : fit));
-  }
-  __host__ __device__ static uint32_t total(int R) {
-    return NO * OP_BYTES + uint32_t(raw_stages(R)) * raw_bytes(R) + kCtrlBytes;
-  }
+  static constexpr int NS_FIT = int((BUDGET - kCtrlBytes) / STAGE);
+  static constexpr int NS = NS_FIT < 2 ? 2 : (NS_FIT > kMaxStages ? kMaxStages : NS_FIT);
+  static constexpr uint32_t TOTAL = NS * STAGE + kCtrlBytes;
 };
 
 // The rows of one CTA (blockIdx.x, + gridDim.x, ...) with the extent of the
@@ -243,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   static_assert(B == 16 || B == 64, "tensor-core path supports b = 16 and b = 64");
   typedef TcPlan<B, SPLIT> P;
   constexpr int KQ = P::KQ;
-  constexpr int NO = P::NO;
+  constexpr int NS = P::NS;
   constexpr int KSTEPS = B / 16;
   constexpr uint32_t NACC = B < 32 ? 32 : B;     // TMEM columns of one accumulator
   constexpr uint32_t NCOLS = 2 * NACC;
@@ -251,28 +239,24 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   constexpr uint32_t SBO = KQ * 128;
   extern __shared__ __align__(1024) unsigned char smem[];
   const int R = a.R;
-  const int NR = P::raw_stages(R);
-  const uint32_t raw_b = P::raw_bytes(R);
-  const uint32_t xbytes = uint32_t(R) * B * 4;
-  auto opx = [&](int s) { return smem + s * P::OP_BYTES; };                       // X hi; X lo at + OPX_BYTES
-  auto rawx = [&](int s) { return smem + NO * P::OP_BYTES + s * raw_b; };
-  auto img = [&](int s) { return smem + NO * P::OP_BYTES + s * raw_b + P::rawx_bytes(R); };
-  unsigned char* ctrl = smem + NO * P::OP_BYTES + NR * raw_b;
-  uint64_t* rfull = reinterpret_cast<uint64_t*>(ctrl);   // raw stage landed (transaction count)
-  uint64_t* rempty = rfull + P::kMaxRaw;                   // MMAs reading the raw stage's A image done (commit)
-  uint64_t* ofull = rempty + P::kMaxRaw;                   // X operand converted (kConvThreads arrivals)
-  uint64_t* oempty = ofull + NO;                           // MMAs reading the operand stage done (commit)
-  uint64_t* accfull = oempty + NO;                         // a block row's products complete (commit)
-  uint64_t* accempty = accfull + 2;                        // accumulator read out (kConvThreads arrivals)
+  const int R8 = (R + 7) & ~7;
+  const uint32_t xi_bytes = uint32_t(R8) * B * 2;          // one image of X_j (hi or lo)
+  auto opx = [&](int s) { return smem + s * P::STAGE; };                     // X hi; X lo at + OPX_BYTES
+  auto img = [&](int s) { return smem + s * P::STAGE + 2 * P::OPX_BYTES; };
+  unsigned char* ctrl = smem + NS * P::STAGE;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);     // stage landed (transaction count)
+  uint64_t* empty = full + P::kMaxStages;                   // the stage's MMAs complete (commit)
+  uint64_t* accfull = empty + P::kMaxStages;                // a block row's products complete (commit)
+  uint64_t* accempty = accfull + 2;                         // accumulator read out (kConvThreads arrivals)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + 224);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(ctrl + 228);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // rows of absent right-hand sides stay zero in every operand stage
-  for (int t = tid; t < NO * kTcM * KQ; t += kTcThreads) {
+  // rows the copies never write (>= R_8) stay zero in every stage's X operand
+  for (int t = tid; t < NS * kTcM * KQ; t += kTcThreads) {
     const int s = t / (kTcM * KQ), e = t % (kTcM * KQ);
     const int m = e / KQ, kq = e % KQ;
-    if (m >= R) {
+    if (m >= R8) {
       *reinterpret_cast<uint4*>(opx(s) + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
       *reinterpret_cast<uint4*>(opx(s) + P::OPX_BYTES + core_off(m, kq, KQ)) = make_uint4(0, 0, 0, 0);
     }
@@ -284,13 +268,9 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < P::kMaxRaw; ++i) {
-      mbar_init(rfull + i, 1);
-      mbar_init(rempty + i, 1);
-    }
-    for (int i = 0; i < NO; ++i) {
-      mbar_init(ofull + i, kConvThreads);
-      mbar_init(oempty + i, 1);
+    for (int i = 0; i < P::kMaxStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(accfull + i, 1);
@@ -306,8 +286,9 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
-    // ---- copier: item k goes to raw stage k % NR once the MMAs of item k - NR are done
+    // ---- copier: item k goes to stage k % NS once the MMAs of item k - NS are done
     if (lane == 0) {
+      const unsigned char* xim = static_cast<const unsigned char*>(a.ximg);
       int64_t k = 0;
       Ring r;
       bool ok = true;
@@ -318,21 +299,23 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
         // the next row's extent is in flight (RowCursor); fetch its first block column early too
         const int ncol0 = rc.n0 < rc.n1 ? a.col[rc.n0] : 0;
         for (int nz = z0; nz < z1; ++nz, ++k) {
-          if (k >= NR && !wait_or_abort(rempty + r.s, r.ph ^ 1u, abort_flag, a.err)) { ok = false; break; }
+          if (k >= NS && !wait_or_abort(empty + r.s, r.ph ^ 1u, abort_flag, a.err)) { ok = false; break; }
           const int j = nz == z0 ? col0 : a.col[nz];
-          mbar_arrive_expect_tx(rfull + r.s, xbytes + P::IMG_BYTES);
-          bulk_g2s(rawx(r.s), a.x + int64_t(j) * a.es, xbytes, rfull + r.s);
+          const unsigned char* xj = xim + int64_t(j) * 2 * xi_bytes;
+          mbar_arrive_expect_tx(full + r.s, 2 * xi_bytes + P::IMG_BYTES);
+          bulk_g2s(opx(r.s), xj, xi_bytes, full + r.s);
+          bulk_g2s(opx(r.s) + P::OPX_BYTES, xj + xi_bytes, xi_bytes, full + r.s);
           bulk_g2s(img(r.s), static_cast<const unsigned char*>(a.vals) + int64_t(nz) * P::IMG_BYTES, P::IMG_BYTES,
-                   rfull + r.s);
-          r.next(NR);
+                   full + r.s);
+          r.next(NS);
         }
         col0 = ncol0;
       }
       if (!ok || *abort_flag) {
         // bounded drain of this CTA's copies in flight before shared memory goes away
-        for (int s = 0; s < NR && s < k; ++s) {
-          const int64_t cnt = k / NR + (s < k % NR ? 1 : 0);     // copies issued into stage s
-          mbar_wait_bounded(rfull + s, uint32_t(cnt - 1) & 1u);
+        for (int s = 0; s < NS && s < k; ++s) {
+          const int64_t cnt = k / NS + (s < k % NS ? 1 : 0);     // copies issued into stage s
+          mbar_wait_bounded(full + s, uint32_t(cnt - 1) & 1u);
         }
       }
     }
@@ -340,7 +323,7 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
     // ---- MMA issuer: Y_i^T += X_j^T A_ij^T per item, accumulator t % 2 for the t-th non-empty row
     if (lane == 0) {
       int64_t t = 0;
-      Ring r, o, last;
+      Ring r, last;
       bool ok = true, any = false;
       for (RowCursor rc(a, blockIdx.x); rc.row < a.nrows && ok; rc.advance(a)) {
         const int z0 = rc.z0, z1 = rc.z1;
@@ -353,13 +336,9 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
         tc_fence_after();
         const uint32_t d = tmem + uint32_t(acc) * NACC;
         for (int nz = z0; nz < z1; ++nz) {
-          if (!wait_or_abort(rfull + r.s, r.ph, abort_flag, a.err) ||
-              !wait_or_abort(ofull + o.s, o.ph, abort_flag, a.err)) {
-            ok = false;
-            break;
-          }
+          if (!wait_or_abort(full + r.s, r.ph, abort_flag, a.err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t sa = smem_u32(opx(o.s)), sb = smem_u32(img(r.s));
+          const uint32_t sa = smem_u32(opx(r.s)), sb = smem_u32(img(r.s));
 #pragma unroll
           for (int ks = 0; ks < KSTEPS; ++ks) {
             const uint64_t ah = make_sdesc(sa + 256u * ks, 128u, SBO);
@@ -368,31 +347,30 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
             mma_bf16(d, make_sdesc(sa + P::OPX_BYTES + 256u * ks, 128u, SBO), bd, IDESC, 1u);
             if (SPLIT) mma_bf16(d, ah, make_sdesc(sb + P::IMG1 + 256u * ks, 128u, SBO), IDESC, 1u);
           }
-          mma_commit(rempty + r.s);
-          mma_commit(oempty + o.s);
-          last = o;
+          mma_commit(empty + r.s);
+          last = r;
           any = true;
-          r.next(NR);
-          o.next(NO);
+          r.next(NS);
         }
         if (!ok) break;
         mma_commit(accfull + acc);
         ++t;
       }
       // after giving up: bounded wait for the MMAs already issued (the last commit covers them)
-      if (!ok && any) mbar_wait_bounded(oempty + last.s, last.ph);
+      if (!ok && any) mbar_wait_bounded(empty + last.s, last.ph);
     }
   } else {
-    // ---- conversion and epilogue (warps 2..5)
-    const int ct = tid - 64;
+    // ---- epilogue (warps 2..5)
     const int quad = warp & 3;                 // the TMEM lane quarter this warp may read
-    const int m = quad * 32 + lane;            // this thread's right-hand side in the epilogue
-    // y_i = epilogue(acc_i) for block row `row`; from TMEM accumulator t % 2, or zero for an empty row
-    auto epilogue = [&](int64_t row, int64_t t, bool empty_row) -> bool {
+    const int m = quad * 32 + lane;            // this thread's right-hand side
+    int64_t t = 0;
+    for (RowCursor rc(a, blockIdx.x); rc.row < a.nrows; rc.advance(a)) {
+      const int64_t row = rc.row;
+      const bool empty_row = rc.z0 == rc.z1;
       const int acc = int(t & 1);
       if (!empty_row) {
         const bool w = wait_or_abort(accfull + acc, uint32_t(t >> 1) & 1u, abort_flag, a.err);
-        if (__any_sync(0xffffffffu, !w)) return false;
+        if (__any_sync(0xffffffffu, !w)) break;
         tc_fence_after();
       }
 #pragma unroll
@@ -426,57 +404,9 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
       if (!empty_row) {
         tc_fence_before();
         mbar_arrive(accempty + acc);
-      }
-      return true;
-    };
-    int64_t k = 0, t = 0, prev_row = -1, prev_t = 0;
-    Ring r, o;
-    bool ok = true;
-    for (RowCursor rc(a, blockIdx.x); rc.row < a.nrows && ok; rc.advance(a)) {
-      const int64_t row = rc.row;
-      const int z0 = rc.z0, z1 = rc.z1;
-      for (int nz = z0; nz < z1; ++nz, ++k) {
-        bool w = wait_or_abort(rfull + r.s, r.ph, abort_flag, a.err);
-        if (w && k >= NO) w = wait_or_abort(oempty + o.s, o.ph ^ 1u, abort_flag, a.err);
-        if (__any_sync(0xffffffffu, !w)) { ok = false; break; }
-        // X_j^T -> hi / lo BF16 operands: one float4 (4 modes of one right-hand
-        // side) per step, 16-byte reads, 8-byte stores that tile the core
-        // matrices without bank conflicts; unrolled so the steps overlap
-        const float* xr = reinterpret_cast<const float*>(rawx(r.s));
-        unsigned char* op = opx(o.s);
-#pragma unroll 4
-        for (int i = 0; i < kTcM * (B / 4) / kConvThreads; ++i) {
-          const int e = ct + i * kConvThreads;
-          if (e >= R * (B / 4)) break;
-          const int mm = e / (B / 4), q4 = e % (B / 4);
-          const float4 v = *reinterpret_cast<const float4*>(xr + mm * B + q4 * 4);
-          const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
-          const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
-          const uint32_t off = core_off(mm, q4 >> 1, KQ) + (q4 & 1) * 8;
-          *reinterpret_cast<uint2*>(op + off) =
-              make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
-          *reinterpret_cast<uint2*>(op + P::OPX_BYTES + off) =
-              make_uint2(pack_bf16(v.x - f0.x, v.y - f0.y), pack_bf16(v.z - f1.x, v.w - f1.y));
-        }
-        fence_proxy_async();     // operands visible to the tensor cores; raw reads ordered before new copies
-        mbar_arrive(ofull + o.s);
-        r.next(NR);
-        o.next(NO);
-      }
-      if (!ok) break;
-      // the previous non-empty row's accumulator, one row behind the conversions
-      if (prev_row >= 0) {
-        if (!epilogue(prev_row, prev_t, false)) { ok = false; break; }
-        prev_row = -1;
-      }
-      if (z0 == z1) {
-        epilogue(row, 0, true);
-      } else {
-        prev_row = row;
-        prev_t = t++;
+        ++t;
       }
     }
-    if (ok && prev_row >= 0) epilogue(prev_row, prev_t, false);
   }
 
   tc_fence_before();
@@ -485,6 +415,41 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   if (warp == 0) {
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS) : "memory");
+  }
+}
+
+// X ([element][rhs][mode], FP32) -> per element the hi and lo BF16 operand
+// images; one thread per (element, right-hand side row, 8 modes): a 32-byte
+// read and two 16-byte writes (consecutive threads: consecutive reads, and
+// writes that tile 512-byte runs of the images).
+template <int B>
+__global__ void split_x_kernel(const float* __restrict__ x, uint32_t units, int R, int R8,
+                               unsigned char* __restrict__ ximg) {
+  constexpr int KQ = B / 8;
+  const uint32_t per = uint32_t(R8) * KQ;
+  const uint32_t xi = uint32_t(R8) * B * 2;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < units; t += gridDim.x * blockDim.x) {
+    const uint32_t j = t / per, u = t % per;
+    const int m = int(u / KQ), kq = int(u % KQ);
+    uint4 hi = make_uint4(0, 0, 0, 0), lo = make_uint4(0, 0, 0, 0);
+    if (m < R) {
+      const float4* src = reinterpret_cast<const float4*>(x + (int64_t(j) * R + m) * B + kq * 8);
+      const float4 v0 = src[0], v1 = src[1];
+      const float f[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(f[2 * q], f[2 * q + 1]);
+        const float2 hf = __bfloat1622float2(hb);
+        h[q] = *reinterpret_cast<const uint32_t*>(&hb);
+        l[q] = pack_bf16(f[2 * q] - hf.x, f[2 * q + 1] - hf.y);
+      }
+      hi = make_uint4(h[0], h[1], h[2], h[3]);
+      lo = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    unsigned char* dst = ximg + int64_t(j) * 2 * xi + core_off(m, kq, KQ);
+    *reinterpret_cast<uint4*>(dst) = hi;
+    *reinterpret_cast<uint4*>(dst + xi) = lo;
   }
 }
 
@@ -509,49 +474,61 @@ cudaError_t bounded_wait_probe(int* err, cudaStream_t st) {
 
 bool tc_block_size_supported(int b) { return b == 16 || b == 64; }
 
+size_t x_image_bytes(int64_t N, int R, int b) { return size_t(N) * size_t((R + 7) & ~7) * size_t(b) * 4; }
+
+cudaError_t split_x_images(const float* x, int64_t N, int R, int b, void* ximg, cudaStream_t st) {
+  if (R < 1 || R > kTcM || N < 0 || !tc_block_size_supported(b)) return cudaErrorInvalidValue;
+  const int R8 = (R + 7) & ~7;
+  const int64_t units = N * R8 * (b / 8);
+  if (units == 0) return cudaSuccess;
+  if (units >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+  const int grid = int(std::min<int64_t>((units + 255) / 256, 152 * 16));
+  if (b == 16) split_x_kernel<16><<<grid, 256, 0, st>>>(x, uint32_t(units), R, R8, static_cast<unsigned char*>(ximg));
+  else split_x_kernel<64><<<grid, 256, 0, st>>>(x, uint32_t(units), R, R8, static_cast<unsigned char*>(ximg));
+  return launched();
+}
+
 // resident CTAs per SM from the kernel's own needs: shared memory (227 KB
 // per SM, ~1 KB reserved per CTA), TMEM (512 columns), threads (2048)
 template <int B, bool SPLIT>
-static int max_ctas(int R) {
+static int max_ctas() {
   typedef TcPlan<B, SPLIT> P;
-  const int smem = int(P::total(R));
-  const int by_smem = (227 * 1024) / (smem + 1024);
+  const int by_smem = int(kSmemCap) / int(P::TOTAL + 1024);
   const int by_tmem = 512 / (2 * (B < 32 ? 32 : B));
   const int by_threads = 2048 / kTcThreads;
   return std::max(1, std::min(by_smem, std::min(by_tmem, by_threads)));
 }
 
 int tc_max_ctas_per_sm(int b, int prec, int R) {
+  (void)R;
   const bool split = prec == P_FP32;
-  if (b == 16) return split ? max_ctas<16, true>(R) : max_ctas<16, false>(R);
-  if (b == 64) return split ? max_ctas<64, true>(R) : max_ctas<64, false>(R);
+  if (b == 16) return split ? max_ctas<16, true>() : max_ctas<16, false>();
+  if (b == 64) return split ? max_ctas<64, true>() : max_ctas<64, false>();
   return 0;
 }
 
 template <int B, bool SPLIT>
 static cudaError_t launch_tc(const BatchArgs& a, cudaStream_t st) {
   typedef TcPlan<B, SPLIT> P;
-  const int smem = int(P::total(a.R));
   static std::once_flag once;
   static cudaError_t cfg = cudaSuccess;
   std::call_once(once, [] {
-    cfg = cudaFuncSetAttribute(bsr_tc_kernel<B, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(kSmemCap - 1024));
+    cfg = cudaFuncSetAttribute(bsr_tc_kernel<B, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(P::TOTAL));
   });
   if (cfg != cudaSuccess) return cfg;
-  const int fit = max_ctas<B, SPLIT>(a.R);
+  const int fit = max_ctas<B, SPLIT>();
   const int per_sm = a.ctas_per_sm > 0 ? std::min(a.ctas_per_sm, fit) : fit;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = std::min<int64_t>(a.nrows, int64_t(std::max(sms, 1)) * per_sm);
   if (grid <= 0) return cudaSuccess;
-  bsr_tc_kernel<B, SPLIT><<<unsigned(grid), kTcThreads, smem, st>>>(a);
+  bsr_tc_kernel<B, SPLIT><<<unsigned(grid), kTcThreads, P::TOTAL, st>>>(a);
   return launched();
 }
 
 cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st) {
-  if (a.R < 1 || a.R > kTcM) return cudaErrorInvalidValue;
+  if (a.R < 1 || a.R > kTcM || !a.ximg) return cudaErrorInvalidValue;
   const bool split = prec == P_FP32;
   if (!split && prec != P_BF16) return cudaErrorInvalidValue;
   switch (b) {

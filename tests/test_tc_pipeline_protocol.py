@@ -2,20 +2,20 @@
 modelled on the CPU.
 
 The kernel's three roles -- the copier (warp 0), the MMA issuer (warp 1) and
-the converter / epilogue warps (2..5) -- share a ring of NR raw stages, a ring
-of NO operand stages and two TMEM accumulators, and hand work on through
-mbarriers that are waited on by phase parity.  This model replays the same
-per-role sequence of waits, arrivals and commits (as written in the kernel)
-under random interleavings, with bulk copies landing and MMAs completing at
-random later times, and checks:
+the epilogue warps (2..5) -- share a ring of NS stages (each holding an
+item's X_j hi / lo images and A_ij image) and two TMEM accumulators, and hand
+work on through mbarriers that are waited on by phase parity.  This model
+replays the same per-role sequence of waits, arrivals and commits (as written
+in the kernel) under random interleavings, with bulk copies landing and MMAs
+completing at random later times, and checks:
 
-  * no deadlock for any row structure (empty rows, rows longer than a ring);
+  * no deadlock for any row structure (empty rows, rows longer than the ring);
   * every parity wait is unambiguous: when a role waits for phase u of a
     barrier, the barrier has completed exactly u or u + 1 phases;
-  * no buffer hazard: a raw stage is not overwritten while an MMA may still
-    read its A image, an operand stage is not rewritten while its MMA runs,
-    an accumulator is not reused before its epilogue read it, the MMAs of an
-    item see the data of that item, and each non-empty row gets one epilogue.
+  * no buffer hazard: a stage is not overwritten while an MMA may still read
+    it, the MMAs of an item see that item's data, an accumulator is not
+    written by the next row's MMAs before its epilogue read it, an epilogue
+    reads only finished products, and each non-empty row gets one epilogue.
 """
 import random
 
@@ -65,38 +65,36 @@ class Ring:
             self.s, self.ph = 0, self.ph ^ 1
 
 
-def simulate(rows, NR, NO, seed, drop=None):
+def simulate(rows, NS, seed, drop=None):
     """drop: name of one wait to leave out (a planted mistake), or None."""
     rnd = random.Random(seed)
-    rfull = [Barrier(1) for _ in range(NR)]
-    rempty = [Barrier(1) for _ in range(NR)]
-    ofull = [Barrier(128) for _ in range(NO)]
-    oempty = [Barrier(1) for _ in range(NO)]
+    full = [Barrier(1) for _ in range(NS)]
+    empty = [Barrier(1) for _ in range(NS)]
     accfull = [Barrier(1) for _ in range(2)]
     accempty = [Barrier(128) for _ in range(2)]
-    raw_x, raw_a, opx = [None] * NR, [None] * NR, [None] * NO
+    stage = [dict() for _ in range(NS)]      # which item's data each part of a stage holds
     issued = []            # (item, accumulator row index t) per MMA group, in issue order
     done = [0]             # MMA groups completed (in order)
     commits = []           # (groups issued when committed, barrier)
-    copies = []            # bulk copies in flight: (stage, item, which)
+    copies = []            # bulk copies in flight: (stage, item, part)
     epilogues = set()
 
     def copier():
-        k, r = 0, Ring(NR)
+        k, r = 0, Ring(NS)
         for z in rows:
             for _ in range(z):
-                if k >= NR and drop != "copier_rempty":
-                    while not rempty[r.s].try_wait_parity(r.ph ^ 1, k // NR - 1):
+                if k >= NS and drop != "copier_empty":
+                    while not empty[r.s].try_wait_parity(r.ph ^ 1, k // NS - 1):
                         yield
-                if k >= NR:
-                    assert done[0] >= k - NR + 1, "raw stage overwritten while an MMA may read it"
-                rfull[r.s].arrive_expect_tx(2)
-                copies.extend([(r.s, k, "x"), (r.s, k, "a")])
+                if k >= NS:
+                    assert done[0] >= k - NS + 1, "stage overwritten while an MMA may read it"
+                full[r.s].arrive_expect_tx(3)
+                copies.extend([(r.s, k, "xhi"), (r.s, k, "xlo"), (r.s, k, "a")])
                 r.next()
                 k += 1
 
     def mma():
-        k, t, r, o = 0, 0, Ring(NR), Ring(NO)
+        k, t, r = 0, 0, Ring(NS)
         for z in rows:
             if z == 0:
                 continue
@@ -104,56 +102,33 @@ def simulate(rows, NR, NO, seed, drop=None):
             if t >= 2 and drop != "mma_accempty":
                 while not accempty[acc].try_wait_parity(((t >> 1) - 1) & 1, (t >> 1) - 1):
                     yield
-            assert t < 2 or (t - 2) in epilogues, "accumulator reused before its epilogue"
+            assert t < 2 or (t - 2) in epilogues, "accumulator overwritten before its epilogue read it"
             for _ in range(z):
-                while not rfull[r.s].try_wait_parity(r.ph, k // NR):
+                while not full[r.s].try_wait_parity(r.ph, k // NS):
                     yield
-                while not ofull[o.s].try_wait_parity(o.ph, k // NO):
-                    yield
-                assert raw_a[r.s] == k and opx[o.s] == k, f"MMA of item {k} sees another item's data"
+                assert all(stage[r.s].get(part) == k for part in ("xhi", "xlo", "a")), \
+                    f"MMA of item {k} sees another item's data"
                 issued.append((k, t))
-                commits.extend([(len(issued), rempty[r.s]), (len(issued), oempty[o.s])])
+                commits.append((len(issued), empty[r.s]))
                 r.next()
-                o.next()
                 k += 1
             commits.append((len(issued), accfull[acc]))
             t += 1
 
-    def converters():
-        k, t, prev, r, o = 0, 0, None, Ring(NR), Ring(NO)
-
-        def epilogue(tr):
-            acc = tr & 1
-            while not accfull[acc].try_wait_parity((tr >> 1) & 1, tr >> 1):
-                yield
-            assert all(issued[i][1] != tr for i in range(done[0], len(issued))), "epilogue before its MMAs"
-            epilogues.add(tr)
-            accempty[acc].arrive(128)
-
+    def epilogue_warps():
+        t = 0
         for z in rows:
-            for _ in range(z):
-                while not rfull[r.s].try_wait_parity(r.ph, k // NR):
-                    yield
-                if k >= NO and drop != "converter_oempty":
-                    while not oempty[o.s].try_wait_parity(o.ph ^ 1, k // NO - 1):
-                        yield
-                if k >= NO:
-                    assert done[0] >= k - NO + 1, "operand stage rewritten while its MMA runs"
-                assert raw_x[r.s] == k
-                opx[o.s] = k
-                ofull[o.s].arrive(128)
-                r.next()
-                o.next()
-                k += 1
-            if prev is not None:
-                yield from epilogue(prev)
-                prev = None
-            if z:
-                prev, t = t, t + 1
-        if prev is not None:
-            yield from epilogue(prev)
+            if z == 0:
+                continue          # an empty row's output needs no accumulator
+            acc = t & 1
+            while not accfull[acc].try_wait_parity((t >> 1) & 1, t >> 1):
+                yield
+            assert all(issued[i][1] != t for i in range(done[0], len(issued))), "epilogue before its MMAs"
+            epilogues.add(t)
+            accempty[acc].arrive(128)
+            t += 1
 
-    roles = [copier(), mma(), converters()]
+    roles = [copier(), mma(), epilogue_warps()]
     alive = [True, True, True]
     for _ in range(10 ** 6):
         choices = [i for i in range(3) if alive[i]]
@@ -165,9 +140,9 @@ def simulate(rows, NR, NO, seed, drop=None):
             break
         c = rnd.choice(choices)
         if c == "copy":
-            s, k, which = copies.pop(rnd.randrange(len(copies)))
-            (raw_x if which == "x" else raw_a)[s] = k
-            rfull[s].complete_tx(1)
+            s, k, part = copies.pop(rnd.randrange(len(copies)))
+            stage[s][part] = k
+            full[s].complete_tx(1)
         elif c == "mma":
             done[0] += 1
             for n, bar in [cm for cm in commits if cm[0] == done[0]]:
@@ -183,33 +158,24 @@ def simulate(rows, NR, NO, seed, drop=None):
     assert len(epilogues) == sum(1 for z in rows if z)
 
 
-@pytest.mark.parametrize("NR,NO", [(2, 2), (3, 3), (6, 3), (8, 2), (4, 4)])
-def test_random_schedules(NR, NO):
+@pytest.mark.parametrize("NS", [2, 3, 4, 6, 8])
+def test_random_schedules(NS):
     for seed in range(300):
-        rnd = random.Random(seed * 7 + NR)
+        rnd = random.Random(seed * 7 + NS)
         rows = [rnd.choice([0, 1, 1, 2, 5, 5, 5, 7, 9, 13]) for _ in range(rnd.randint(0, 14))]
-        simulate(rows, NR, NO, seed)
+        simulate(rows, NS, seed)
 
 
-@pytest.mark.parametrize("drop", ["copier_rempty", "converter_oempty"])
-def test_model_catches_a_dropped_wait(drop):
-    """Leaving out either stage-reuse wait is caught by the model on some
-    schedule (the checks are not vacuous)."""
+@pytest.mark.parametrize("drop,rows,NS", [("copier_empty", [5, 5, 5, 7, 5, 13, 5, 5], 3),
+                                          ("mma_accempty", [1] * 10, 8)])
+def test_model_catches_a_dropped_wait(drop, rows, NS):
+    """Leaving out either reuse wait is caught by the model on some schedule
+    (the checks are not vacuous).  The accumulator wait matters when the MMAs
+    can run two rows ahead of the epilogue: short rows, a deep ring."""
     caught = 0
     for seed in range(200):
         try:
-            simulate([5, 5, 5, 7, 5, 13, 5, 5], 3, 2, seed, drop=drop)
+            simulate(rows, NS, seed, drop=drop)
         except AssertionError:
             caught += 1
     assert caught > 0
-
-
-def test_accumulator_wait_is_implied_by_the_converter_order():
-    """The MMA issuer's wait for an accumulator's epilogue never blocks in the
-    model: the converters read the accumulator of row t - 2 before they
-    convert row t, and the MMAs of row t need those conversions.  The kernel
-    keeps the wait all the same, for the tcgen05 ordering of the TMEM read
-    (tcgen05.ld, then fence::before_thread_sync and the arrival) against the
-    next MMA's write."""
-    for seed in range(200):
-        simulate([5, 5, 5, 7, 5, 13, 5, 5], 3, 2, seed, drop="mma_accempty")
