@@ -6,13 +6,13 @@
 //   M = 128 (right-hand sides; rows >= R are zero),  N = b,  K = 16 per step,
 // BF16 operands and an FP32 accumulator in tensor memory.  The FP32 vectors
 // are split into hi + lo BF16 parts (hi = bf16(x), lo = bf16(x - hi)) and both
-// are multiplied, so the product carries ~16 bits of x -- the same accuracy
-// as the CUDA-core path that multiplies BF16-stored blocks by FP32 vectors.
-// With FP32-stored blocks the matrix is split the same way while it is staged
-// and three products are accumulated (A_hi x_hi + A_hi x_lo + A_lo x_hi;
-// A_lo x_lo is below 2^-16 of the result): both factors then carry about 17
-// significant bits (|x - x_hi - x_lo| <= 2^-17 |x|), between BF16 (8) and
-// FP32 (24), with FP32 accumulation.
+// are multiplied, so x enters with ~17 significant bits (|x - hi - lo| <=
+// 2^-17 |x|); with BF16-stored blocks (8 bits) the block rounding dominates,
+// as on the CUDA-core path that multiplies them by FP32 vectors.  FP32-stored
+// blocks are split the same way (at setup) and three products are accumulated
+// (A_hi x_hi + A_hi x_lo + A_lo x_hi; A_lo x_lo is below 2^-16 of the
+// result): both factors then carry about 17 significant bits, between BF16
+// (8) and FP32 (24), with FP32 accumulation.
 //
 // Operands live in shared memory in the canonical K-major, no-swizzle
 // layout: 8-row x 16-byte core matrices, rows 16 B apart, core matrices
@@ -52,8 +52,8 @@ namespace ldgmg {
 namespace {
 
 constexpr int kTcM = 128;
-constexpr int kConvThreads = 128;                   // warps 2..5: epilogue
-constexpr int kTcThreads = 64 + kConvThreads;       // + copy warp 0 and MMA warp 1
+constexpr int kEpiThreads = 128;                    // warps 2..5: epilogue
+constexpr int kTcThreads = 64 + kEpiThreads;        // + copy warp 0 and MMA warp 1
 constexpr uint32_t kCtrlBytes = 256;                // 20 mbarriers, TMEM address, abort flag
 constexpr uint32_t kSmemCap = 227 * 1024;           // dynamic shared memory per CTA
 constexpr unsigned kSpinLimit = 1u << 20;   // bounded waits: error flag instead of a hang
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
   uint64_t* full = reinterpret_cast<uint64_t*>(ctrl);     // stage landed (transaction count)
   uint64_t* empty = full + P::kMaxStages;                   // the stage's MMAs complete (commit)
   uint64_t* accfull = empty + P::kMaxStages;                // a block row's products complete (commit)
-  uint64_t* accempty = accfull + 2;                         // accumulator read out (kConvThreads arrivals)
+  uint64_t* accempty = accfull + 2;                         // accumulator read out (kEpiThreads arrivals)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctrl + 224);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(ctrl + 228);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kTcThreads) bsr_tc_kernel(BatchArgs a) {
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(accfull + i, 1);
-      mbar_init(accempty + i, kConvThreads);
+      mbar_init(accempty + i, kEpiThreads);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
