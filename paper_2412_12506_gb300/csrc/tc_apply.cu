@@ -192,6 +192,9 @@ struct TcPlan {
   static constexpr int NS_FIT = int((BUDGET - kCtrlBytes) / STAGE);
   static constexpr int NS = NS_FIT < 2 ? 2 : (NS_FIT > kMaxStages ? kMaxStages : NS_FIT);
   static constexpr uint32_t TOTAL = NS * STAGE + kCtrlBytes;
+  static_assert(TOTAL <= kSmemCap - 1024, "stages exceed the dynamic shared memory of a CTA");
+  static_assert(STAGE % 128 == 0 && OPX_BYTES % 128 == 0, "stage parts must stay 128-byte aligned");
+  static_assert((2 * kMaxStages + 4) * 8 <= 224, "mbarriers would overlap the TMEM address word");
 };
 
 // The rows of one CTA (blockIdx.x, + gridDim.x, ...) with the extent of the
