@@ -371,3 +371,26 @@ def test_gauss_seidel_vcycle_symmetry_and_pairing_speed():
         _, k_oi, _ = st.gmres(A.mat, mg.VCycle(levels, "gs", 3, 3, pre="B1", post="BT"), rhs, tol=1e-10)
         _, k_oo, _ = st.gmres(A.mat, mg.VCycle(levels, "gs", 3, 3, pre="B1", post="B1"), rhs, tol=1e-10)
         assert k_oo < k_oi, (k_oo, k_oi)
+
+
+@pytest.mark.parametrize("d,n,p", [(2, 16, 2), (2, 16, 1), (3, 8, 1)])
+@pytest.mark.parametrize("mu_in,mu_out", [(1e4, 1.0), (1.0, 1e4)])
+def test_coarsening_equals_rediscretisation_across_aligned_jump(d, n, p, mu_in, mu_out):
+    """Sec. 2.2 option (ii) with a coefficient jump.  The inclusion (1/4, 3/4)^d
+    of Sec. 2.4.3 stays a union of whole elements on every level with n >= 4,
+    so an injected coarse function has no jump on the fine faces inside a coarse
+    element and the same upwind side on the others.  The coarsened G, M_mu and
+    E are then exactly those assembled on the coarse mesh with the coarse
+    element coefficients, and so is A.  Dropping mu from M_mu,c (I^T M I) or
+    the 1/2 of E_c makes this fail by O(1)."""
+    levels = mg.build_levels(d, n, p, square_mu(d, n, mu_in, mu_out))
+    checked = 0
+    for lv in levels[1:]:
+        if lv.n < 4:
+            continue
+        direct = ldg.assemble(d, lv.n, p, square_mu(d, lv.n, mu_in, mu_out))
+        Ac, Ad = lv.A.dense(), direct.A.dense()
+        assert np.abs(Ac - Ad).max() <= 1e-12 * np.abs(Ad).max()
+        assert (lv.A.pat != direct.A.pat).nnz == 0
+        checked += 1
+    assert checked == len([k for k in range(1, 8) if n >> k >= 4])

@@ -306,3 +306,22 @@ def test_stokes_gauss_seidel_vs_sai1():
         eta_gs, eta_sai = krylov.eta(h_gs), krylov.eta(h_sai)
         assert 0.5 <= eta_gs <= 1.2, eta_gs
         assert eta_sai < eta_gs, (eta_sai, eta_gs)
+
+
+@pytest.mark.parametrize("gamma", [0, 1])
+@pytest.mark.parametrize("mu_in,mu_out", [(1e3, 1.0), (1.0, 1e3)])
+def test_stokes_coarsening_equals_rediscretisation_across_aligned_jump(gamma, mu_in, mu_out):
+    """As the scalar case: with the viscosity inclusion (1/4, 3/4)^2 of Sec. 3.4.3
+    aligned with every level with n >= 4, per-field coarsening (M_mu,c, E_c = E/2,
+    E_p,c = 2 E_p with its min-mu weight) equals the Stokes operator assembled
+    on the coarse mesh with the coarse viscosities."""
+    from paper_2412_12506_gb300.inputs import square_mu
+    d, n, p = 2, 16, 2
+    levels = st.build_stokes_levels(d, n, p, square_mu(d, n, mu_in, mu_out), gamma=gamma)
+    for lv in levels[1:]:
+        if lv.n < 4:
+            continue
+        direct = st.assemble_stokes(d, lv.n, p, square_mu(d, lv.n, mu_in, mu_out), gamma=gamma).A
+        Ac, Ad = lv.A.dense(), direct.dense()
+        assert np.abs(Ac - Ad).max() <= 1e-12 * np.abs(Ad).max()
+        assert (lv.A.pat != direct.pat).nnz == 0
