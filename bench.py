@@ -40,8 +40,8 @@ if ROOT not in sys.path:
 METRIC = "1e-10 solves/s (mixed-precision V-cycle + FP64 CG)"
 
 # DRAM bytes (read + write) per block row of the finest-level B apply, from one
-# ncu capture on the 16^3 case (profiles/bsr_kernel_fp16_poisson3d_n16_p3.md,
-# mean of 3 launches), scaled by rows to the launch timed here; valid only for
+# ncu capture on the 16^3 case (mean of 3 launches), scaled by rows to the
+# launch timed here; valid only for
 # the kernel source it was taken on (sha256 prefix of bsr_apply.cu), else
 # reported as null.
 TRAFFIC_PER_ROW = {"fp16": (238.53e6 / 4096, "e8dc9956e336c68c")}

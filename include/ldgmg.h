@@ -240,6 +240,17 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
  * length; at most cap values are written (relres may be NULL). */
 ldgmg_status ldgmg_solve_history(const ldgmg_hier* h, int rhs, double* relres, int cap, int* count);
 
+/* y = A x with the operator apply of the outer CG (Sec. 2.2: the residual
+ * update q = A p of every CG iteration), exactly as ldgmg_solve runs it on this
+ * hierarchy: the double-FP32 kernels (outer_apply DF; one right-hand side or
+ * several, b = 16 / 64), the FP64 block-reuse kernel (several right-hand sides,
+ * b = 16 / 64) or the FP64 CUDA-core kernel (every other case).  x_dev, y_dev:
+ * device arrays of N*b*nrhs doubles in the layout the batched CG keeps,
+ * [element][rhs][mode] (the stacked layout when nrhs = 1); must not overlap.
+ * 1 <= nrhs <= max_rhs.  GMRES hierarchies -> EUNSUPPORTED (their apply is
+ * ldgmg_apply).  Enqueues on `stream`; does not synchronise. */
+ldgmg_status ldgmg_krylov_apply(ldgmg_hier* h, int nrhs, const double* x_dev, double* y_dev, void* stream);
+
 /* ---- per-level entry points (one step of the hot path each) --------------
  * Level vectors are in the hierarchy's working type: double for an FP64
  * hierarchy, float for FP32/BF16.  All pointers are device pointers. */
@@ -293,9 +304,16 @@ void ldgmg_hier_free(ldgmg_hier* h);
  * synchronisation.  Such callers cannot create an ldgmg_op either, so this
  * call takes plain sizes.
  *
- * Same result as ldgmg_project_kernel (up to summation order): removes the
- * constant mode from v_dev, an N*b FP64 device vector laid out [element][mode],
- * in place.  N must satisfy 1 <= N <= LDGMG_NOALLOC_MAX_ELEMENTS, else EINVAL.
+ * Removes the constant mode of ONE field in place: subtracts the mean of the
+ * values v_dev[e*b] over the N elements e from each of them (the mode-0
+ * coefficients when v_dev points at an element's first mode).  For a scalar
+ * operator (one field, b = (p+1)^dim) that is ldgmg_project_kernel's result up
+ * to summation order.  A Stokes vector has dim + 1 fields per element; b alone
+ * cannot tell it from a scalar one (b = 27 is both), so this call does not try:
+ * project a Stokes vector with one call per field f, passing v_dev + f*field_b
+ * and the full block size b as the stride (ldgmg_op_fields gives field_b).
+ * v_dev must hold at least (N-1)*b + 1 doubles; the library cannot check its
+ * length.  N must satisfy 1 <= N <= LDGMG_NOALLOC_MAX_ELEMENTS, else EINVAL.
  * It allocates nothing: its reduction scratch is a fixed file-scope device
  * array of (LDGMG_NOALLOC_MAX_ELEMENTS / 4096 + 1) doubles (about 32 KB) that
  * every GPU which loads the library holds until the process exits.  The first

@@ -11,7 +11,9 @@
  *   - Admission by HBM footprint.  A class is built only when its estimated
  *     device footprint fits the budget; idle classes (nothing queued, nothing
  *     running) are evicted least-recently-used first to make room.  Requests
- *     of a class that does not fit yet wait in its queue.
+ *     of a class that does not fit yet wait in its queue.  A class whose
+ *     estimated footprint alone exceeds the budget is refused: it is never
+ *     built and its requests complete with status LDGMG_ENOMEM.
  *   - Continuous batching.  Worker threads, each with its own CUDA stream,
  *     take the oldest waiting class that is built and not running, and solve
  *     as many of its queued requests as one call takes: for scalar operators
@@ -74,7 +76,8 @@ typedef struct {
 
 typedef struct {
   uint64_t submitted, completed;
-  uint64_t builds, evictions, build_failures;
+  uint64_t builds, evictions;
+  uint64_t build_failures;  /* classes whose build failed or that admission refused (too large) */
   uint64_t solve_calls;     /* ldgmg_solve calls; completed / solve_calls = mean batch */
   int max_batch_seen;
   int classes_resident;

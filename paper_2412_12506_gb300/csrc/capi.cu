@@ -1139,6 +1139,32 @@ static ldgmg_status gmres_solve(ldgmg_hier* h, const double* b, double* x, doubl
   return converged ? LDGMG_OK : fail(LDGMG_ENOTCONV, "max_iter reached");
 }
 
+// q = A p with the operator apply of the outer CG (Sec. 2.2), FP64 vectors of R
+// right-hand sides laid out [element][rhs][mode].  Batched hierarchies apply A
+// once per block row for all right-hand sides, in double-FP32 (use_df) or
+// FP64.  The arithmetic of each right-hand side does not depend on R, so a
+// right-hand side solved alone matches the batch.  Multi-RHS hierarchies use
+// the same outer apply for every R (so each right-hand side is bitwise the
+// same alone and batched): the block-reuse kernels for b = 16 / 64, else the
+// CUDA-core kernel.
+static ldgmg_status krylov_apply(ldgmg_hier* h, const double* p, double* q, int R, cudaStream_t s) {
+  const int bsz = h->op->host.b;
+  const bool multi = (h->batched || h->Rmax > 1) && R <= 64 && tc_block_size_supported(bsz);
+  if (multi && h->use_df) CK(bsr_apply_df(h->op->A, h->op->A_pairs, M_Y, p, nullptr, q, R, s));
+  else if (multi) CK(bsr_apply_multi64(h->op->A, M_Y, p, nullptr, q, R, s));
+  else if (h->use_df && R == 1) CK(bsr_apply_df1(h->op->A, h->op->A_pairs, M_Y, p, nullptr, q, s));
+  else CK(bsr_apply_strided(h->op->A, M_Y, p, nullptr, nullptr, q, 1.0, R, int64_t(R) * bsz, bsz, s));
+  return LDGMG_OK;
+}
+
+ldgmg_status ldgmg_krylov_apply(ldgmg_hier* h, int nrhs, const double* x, double* y, void* stream) {
+  g_err.clear();
+  if (!h || !x || !y) return fail(LDGMG_EINVAL, "null argument");
+  if (nrhs < 1 || nrhs > h->Rmax) return fail(LDGMG_EINVAL, "nrhs must be in 1..max_rhs of the setup");
+  if (h->gmres) return fail(LDGMG_EUNSUPPORTED, "GMRES hierarchies apply A in FP64 (ldgmg_apply)");
+  return krylov_apply(h, x, y, nrhs, (cudaStream_t)stream);
+}
+
 ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x, int nrhs, int* iters,
                          double* relres, void* stream) {
   NvtxRange nvtx_("ldgmg_solve");
@@ -1240,7 +1266,6 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     // Multi-RHS hierarchies use the same outer apply for every R (so each
     // right-hand side is bitwise the same alone and batched): the block-reuse
     // kernels for b = 16 / 64, else the CUDA-core kernel.
-    const bool multi = (h->batched || h->Rmax > 1) && R <= 64 && tc_block_size_supported(int(bsz));
     // One CG iteration (Sec. 2.2).  The stopping test runs on the device right
     // after the residual norms (cg_check_b), so a converged right-hand side is
     // frozen (alpha = beta = 0) at the same iteration as with a host test, and
@@ -1248,10 +1273,7 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
     // right-hand side converged changes nothing.
     // part 1: q = A p, alpha, x and r updates, residual norms, stopping test
     auto step = [&](cudaStream_t s) -> ldgmg_status {
-      if (multi && h->use_df) CK(bsr_apply_df(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, R, s));
-      else if (multi) CK(bsr_apply_multi64(h->op->A, M_Y, h->p, nullptr, h->q, R, s));
-      else if (h->use_df && R == 1) CK(bsr_apply_df1(h->op->A, h->op->A_pairs, M_Y, h->p, nullptr, h->q, s));
-      else CK(bsr_apply_strided(h->op->A, M_Y, h->p, nullptr, nullptr, h->q, 1.0, R, R * bsz, bsz, s));
+      CKS(krylov_apply(h, h->p, h->q, R, s));
       CK(dot_batched(N, R, int(bsz), h->p, h->q, h->partials, slot(S_PQ), s));
       CK(cg_alpha_b(R, S, dact, s));
       CK(cg_update_xr_b(N, R, int(bsz), xg, h->r, h->p, h->q, S, s));

@@ -168,20 +168,24 @@ void complete(ldgmg_server* s, const std::shared_ptr<Req>& r) {
   s->st.completed++;
 }
 
-// Called with s->mu held.
+// Requests queued on a failed (or refused) class complete with its status.
+void fail_queue(ldgmg_server* s, Class* c) {
+  while (!c->queue.empty()) {
+    auto r = c->queue.front();
+    c->queue.pop_front();
+    r->res.status = c->fail_status;
+    r->res.t_start = r->res.t_end = s->now();
+    r->res.relres = std::numeric_limits<double>::quiet_NaN();
+    complete(s, r);
+  }
+}
+
+// Called with s->mu held; the caller wakes waiters (cv_done) afterwards.
 void plan(ldgmg_server* s) {
   // (1) failed builds: their queued requests complete with the build status
   for (auto& kv : s->classes) {
     Class* c = kv.second.get();
-    if (c->state != Class::FAILED) continue;
-    while (!c->queue.empty()) {
-      auto r = c->queue.front();
-      c->queue.pop_front();
-      r->res.status = c->fail_status;
-      r->res.t_start = r->res.t_end = s->now();
-      r->res.relres = std::numeric_limits<double>::quiet_NaN();
-      complete(s, r);
-    }
+    if (c->state == Class::FAILED) fail_queue(s, c);
   }
   // (2) admission, oldest waiting request first
   std::vector<Class*> want;
@@ -193,6 +197,14 @@ void plan(ldgmg_server* s) {
             [](Class* a, Class* b) { return a->queue.front()->res.t_submit < b->queue.front()->res.t_submit; });
   for (Class* c : want) {
     c->est = estimate(s->o, *c);
+    if (c->est > s->o.hbm_budget) {
+      // larger than the whole budget on its own: refused, never built
+      c->state = Class::FAILED;
+      c->fail_status = LDGMG_ENOMEM;
+      s->st.build_failures++;
+      fail_queue(s, c);
+      continue;
+    }
     while (s->reserved + c->est > s->o.hbm_budget) {
       Class* victim = nullptr;
       for (auto& kv : s->classes) {
@@ -208,7 +220,7 @@ void plan(ldgmg_server* s) {
       s->st.evictions++;
       s->st.classes_resident--;
     }
-    if (s->reserved + c->est > s->o.hbm_budget && s->reserved > 0) break;   // wait for room, keep order
+    if (s->reserved + c->est > s->o.hbm_budget) break;   // wait for room, keep order
     c->state = Class::BUILDING;
     s->reserved += c->est;
     s->build_q.push_back(c);
@@ -445,6 +457,7 @@ ldgmg_status ldgmg_server_submit(ldgmg_server* s, const ldgmg_request* q, uint64
   s->st.submitted++;
   *ticket = r->id;
   plan(s);
+  s->cv_done.notify_all();   // plan may have completed requests (refused classes)
   return LDGMG_OK;
 }
 

@@ -91,6 +91,7 @@ _SIGS = {
     "ldgmg_hier_info": (_i, [_vp, _i, _P(_i), _P(_i), _P(_i64), _P(_i), _P(_i64), _P(_i64)]),
     "ldgmg_vcycle": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ldgmg_solve": (_i, [_vp, _vp, _d, _vp, _i, _P(_i), _P(_d), _vp]),
+    "ldgmg_krylov_apply": (_i, [_vp, _i, _vp, _vp, _vp]),
     "ldgmg_level_apply": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "ldgmg_level_smooth": (_i, [_vp, _i, _i, _vp, _vp, _vp, _i, _vp]),
     "ldgmg_level_apply_batched": (_i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
@@ -144,10 +145,25 @@ def selftest_bounded_wait(stream=None) -> int:
 NOALLOC_MAX_ELEMENTS = 16777216
 
 
-def project_kernel_noalloc(v, N, b, stream=None):
-    """ldgmg_project_kernel_noalloc: remove the constant mode from v (N*b FP64,
-    device) without any allocation in the library; see include/ldgmg.h."""
-    _check(_lib.ldgmg_project_kernel_noalloc(N, b, _ptr(v), _stream(stream)))
+def project_kernel_noalloc(v, N, b, offset=0, stream=None):
+    """ldgmg_project_kernel_noalloc: subtract the mean of v[offset + e*b],
+    e = 0..N-1, from those entries, in place, without any allocation in the
+    library (include/ldgmg.h).  offset = 0 projects a scalar vector; a Stokes
+    vector takes one call per field with offset = f * field_b.  v must be a
+    contiguous CUDA float64 tensor long enough for the N strided entries: the
+    C call cannot check its length, so this wrapper does."""
+    import torch
+    if not isinstance(v, torch.Tensor) or not v.is_cuda or v.dtype != torch.float64 or not v.is_contiguous():
+        raise LdgmgError(EINVAL, "v must be a contiguous CUDA float64 tensor")
+    N, b, offset = int(N), int(b), int(offset)
+    if N > NOALLOC_MAX_ELEMENTS:
+        # the library refuses the size before it touches v: let it say so
+        _check(_lib.ldgmg_project_kernel_noalloc(N, b, _ptr(v), _stream(stream)))
+    if N < 1 or b < 1 or offset < 0 or offset + (N - 1) * b + 1 > v.numel():
+        raise LdgmgError(EINVAL, f"v has {v.numel()} entries; N = {N}, b = {b}, offset = {offset} "
+                                 f"need {offset + (N - 1) * b + 1}")
+    ptr = ctypes.c_void_p(v.data_ptr() + 8 * offset)
+    _check(_lib.ldgmg_project_kernel_noalloc(N, b, ptr, _stream(stream)))
     return v
 
 
@@ -378,6 +394,18 @@ class Hierarchy:
             return x, it[0], rr[0], st
         return x, list(it), list(rr), st
 
+    def krylov_apply(self, x, nrhs, y=None, stream=None):
+        """y = A x with the outer CG's operator apply (ldgmg_krylov_apply); FP64
+        vectors [element][rhs][mode], nrhs right-hand sides."""
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()) or \
+                x.numel() != self.op.size * nrhs or y.shape != x.shape or y.dtype != x.dtype:
+            raise ValueError("x, y must be contiguous CUDA float64 tensors of N*b*nrhs entries")
+        _check(_lib.ldgmg_krylov_apply(self._h, nrhs, _ptr(x), _ptr(y), _stream(stream)))
+        return y
+
     def level_apply_batched(self, level, which, x, nrhs, y=None, stream=None):
         """y = M x for nrhs right-hand sides, float vectors [element][rhs][mode]."""
         import torch
@@ -437,18 +465,6 @@ class Hierarchy:
         if getattr(self, "_h", None):
             _lib.ldgmg_hier_free(self._h)
             self._h = None
-
-
-def bsr_to_dense(rp, col, vals):
-    """Dense matrix from an exported block-CSR (tests/inspection)."""
-    N = len(rp) - 1
-    b = vals.shape[1] if vals.ndim == 3 else 0
-    D = np.zeros((N * b, N * b))
-    for i in range(N):
-        for z in range(rp[i], rp[i + 1]):
-            j = col[z]
-            D[i * b:(i + 1) * b, j * b:(j + 1) * b] += vals[z]
-    return D
 
 
 # ---------------------------------------------------------------------------

@@ -11,6 +11,7 @@
 """
 import numpy as np
 import pytest
+from bsr_dense import bsr_to_dense
 
 from oracle import krylov, ldg
 from oracle import multigrid as mg
@@ -45,7 +46,7 @@ def test_tensor_core_apply_matches_stored_blocks(lib, d, n, p, R, prec):
     rng = np.random.default_rng(R)
     for which in (lib.MAT_A, lib.MAT_B, lib.MAT_BT):
         rp, col, vals = H.export_level(0, which)
-        M = lib.bsr_to_dense(rp, col, vals)
+        M = bsr_to_dense(rp, col, vals)
         xs = rng.standard_normal((R, N * b)).astype(np.float32)
         xb = torch.tensor(_batch_layout(xs, N, b), device="cuda")
         y = H.level_apply_batched(0, which, xb, R).cpu().numpy()

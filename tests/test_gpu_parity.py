@@ -16,6 +16,7 @@ Tolerances (relative, max-abs error over max-abs value unless stated):
 """
 import numpy as np
 import pytest
+from bsr_dense import bsr_to_dense
 
 from oracle import krylov, ldg
 from oracle import krylov as krylov_mod
@@ -135,10 +136,10 @@ def test_level_matrices_and_applies(lib, d, n, p, smoother, prec):
         x = random_vector(lv.N * lv.b, seed=l)
         for which, Mo in mats:
             rp, col, vals = H.export_level(l, which)
-            Md = lib.bsr_to_dense(rp, col, vals)
+            Md = bsr_to_dense(rp, col, vals)
             # FP16 storage scale: the power of two that puts the largest entry in [2^14, 2^15)
             fscale = 2.0 ** (15 - np.frexp(np.abs(Mo).max())[1])
-            ref_round = lib.bsr_to_dense(rp, col, _round(
+            ref_round = bsr_to_dense(rp, col, _round(
                 np.stack([Mo[i * lv.b:(i + 1) * lv.b, j * lv.b:(j + 1) * lv.b]
                           for i in range(lv.N) for j in col[rp[i]:rp[i + 1]]]), prec, fscale))
             # entries: stored value vs oracle value rounded to the storage type
@@ -385,3 +386,56 @@ def test_residual_history_and_eta_match_oracle(lib):
     assert ss == lib.OK and ks == kso and len(hs) == ks + 1
     hso = np.asarray(hso) / hso[0]
     assert np.abs(np.log10(hs) - np.log10(hso)).max() < 1e-5
+
+
+# The outer CG's operator apply (ldgmg_krylov_apply): double-FP32 single-RHS
+# (bsr_df1_kernel), double-FP32 multi-RHS (bsr_df_kernel), FP64 multi-RHS
+# block reuse (bsr_multi64_kernel), and the FP64 CUDA-core kernel for block
+# sizes the block-reuse kernels do not take.  Per-entry bounds against the
+# oracle's y = A x, relative to s_i = sum_j |a_ij| |x_j| (the scale of the
+# rounding of one row; the two independently assembled operators differ by
+# up to ~2^-46 of an entry):
+#   * double-FP32: 2^-42 s_i (the arithmetic keeps ~2^-44 to 2^-45 of s_i:
+#     products a_hi x_hi exact by FMA, cross terms and the dropped a_lo x_lo
+#     at ~2^-48, TwoSum accumulation);
+#   * FP64: 2^-44 s_i (k b <= 448 fused multiply-adds, gamma_448 = 2^-44.2).
+KRYLOV_APPLY_CASES = [
+    # d, n, p, mu_kind, precision, outer, max_rhs, R list, kernel exercised
+    (2, 6, 3, None, "fp32", "df", 1, [1], "df1"),
+    (2, 10, 3, "square", "fp32", "df", 1, [1], "df1"),
+    (3, 6, 3, None, "fp32", "df", 1, [1], "df1"),
+    (3, 4, 3, "square", "fp32", "df", 1, [1], "df1"),
+    (2, 6, 3, None, "fp32", "df", 64, [1, 5, 64], "df"),
+    (2, 10, 3, "square", "fp32", "df", 64, [5, 64], "df"),
+    (3, 4, 3, "square", "fp32", "df", 64, [1, 5, 64], "df"),
+    (2, 6, 3, "square", "fp32", "fp64", 64, [1, 5, 64], "multi64"),
+    (3, 4, 3, None, "fp32", "fp64", 64, [5, 64], "multi64"),
+    (2, 6, 2, "square", "fp32", "df", 5, [1, 5], "fp64 strided (b = 9)"),
+    (3, 4, 2, None, "fp32", "df", 5, [5], "fp64 strided (b = 27)"),
+    (2, 6, 3, None, "fp64", "df", 1, [1], "fp64 strided (FP64 hierarchy)"),
+]
+
+
+@pytest.mark.parametrize("d,n,p,mu_kind,prec,outer,max_rhs,Rs,kernel", KRYLOV_APPLY_CASES)
+def test_krylov_apply_elementwise_vs_oracle(lib, d, n, p, mu_kind, prec, outer, max_rhs, Rs, kernel):
+    mu = mu_for(mu_kind, d, n)
+    A = ldg.assemble(d, n, p, mu).A
+    N, b = A.nblocks, A.b
+    absA = abs(A.mat)
+    op = lib.Operator(d, n, p, mu)
+    h = lib.Hierarchy(op, precision=prec, outer=outer, max_rhs=max_rhs, smoother="jacobi", nu1=1, nu2=1)
+    bound = 2.0 ** -42 if kernel.startswith("df") else 2.0 ** -44
+    for R in Rs:
+        X = np.stack([random_vector(N * b, 100 + 7 * R + r) for r in range(R)])     # [rhs][element][mode]
+        Xb = X.reshape(R, N, b).transpose(1, 0, 2).copy()                              # [element][rhs][mode]
+        y = h.krylov_apply(cuda(Xb.reshape(-1)), R).cpu().numpy().reshape(N, R, b).transpose(1, 0, 2)
+        for r in range(R):
+            ref = A.mat @ X[r]
+            s = absA @ np.abs(X[r])
+            err = np.abs(y[r].reshape(-1) - ref)
+            worst = (err / s).max()
+            assert worst <= bound, (kernel, R, r, np.log2(worst))
+        # the arithmetic of a right-hand side does not depend on how many are applied
+        if R > 1:
+            y1 = h.krylov_apply(cuda(Xb[:, :1, :].reshape(-1)), 1).cpu().numpy()
+            assert np.array_equal(y1, y[0].reshape(-1))

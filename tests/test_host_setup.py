@@ -48,7 +48,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def _dense(rp, col, vals):
-    from paper_2412_12506_gb300.ldgmg import bsr_to_dense
+    from bsr_dense import bsr_to_dense
     return bsr_to_dense(rp, col, vals)
 
 

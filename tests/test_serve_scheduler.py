@@ -84,14 +84,25 @@ def test_fifo_across_classes_with_one_worker(lib):
     s.close()
 
 
-def test_oversized_class_is_admitted_alone(lib):
-    s = lib.Server(workers=1, max_batch=1, hbm_budget=1, simulate=True, simulate_solve_s=0.0)
-    t = s.submit(2, 16, 2, _rhs(2, 16, 2))
-    _, r = s.wait(t)
-    assert r["status"] == lib.OK
-    t2 = s.submit(2, 16, 1, _rhs(2, 16, 1))
-    _, r2 = s.wait(t2)
-    assert r2["status"] == lib.OK and s.stats()["evictions"] == 1
+def test_class_larger_than_the_budget_is_refused(lib):
+    """Admission by footprint holds for every class: one whose estimate alone
+    exceeds the budget is never built, its requests (queued and later ones)
+    complete with ENOMEM, and classes that fit are still served."""
+    probe = lib.Server(workers=1, max_batch=1, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.0)
+    probe.wait(probe.submit(2, 16, 1, _rhs(2, 16, 1)))
+    small = probe.stats()["bytes_resident"]
+    probe.close()
+    s = lib.Server(workers=1, max_batch=1, hbm_budget=small + small // 2, simulate=True, simulate_solve_s=0.0)
+    big = [s.submit(2, 64, 3, _rhs(2, 64, 3)) for _ in range(2)]
+    ok = s.submit(2, 16, 1, _rhs(2, 16, 1))
+    for t in big:
+        _, r = s.wait(t)
+        assert r["status"] == lib.ENOMEM and np.isnan(r["relres"])
+    assert s.wait(ok)[1]["status"] == lib.OK
+    _, r = s.wait(s.submit(2, 64, 3, _rhs(2, 64, 3)))
+    assert r["status"] == lib.ENOMEM
+    st = s.stats()
+    assert st["builds"] == 1 and st["build_failures"] == 1 and st["bytes_peak"] <= st["hbm_budget"]
     s.close()
 
 
