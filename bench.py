@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--dim", type=int, default=3)
     ap.add_argument("--precision", default="fp16", choices=["fp16", "fp32", "bf16", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--other-prec-steps", type=int, default=2,
+                    help="timed solves with each other V-cycle precision (0 disables)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-rhs", type=int, default=64, help="0 disables the batched section")
@@ -87,67 +89,165 @@ def parse():
     ap.add_argument("--stokes-n", type=int, default=128, help="0 disables the Stokes section")
     ap.add_argument("--stokes-steps", type=int, default=3)
     ap.add_argument("--stokes-tol", type=float, default=1e-9)
-    ap.add_argument("--serve-requests", type=int, default=3000, help="0 disables the serving section")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="0 disables the serving section")
     ap.add_argument("--serve-workers", type=int, default=4)
-    ap.add_argument("--serve-fp64-sample", type=int, default=200)
-    ap.add_argument("--section", default="all", choices=["all", "batched", "stokes", "serve", "tcapply"],
+    ap.add_argument("--serve-fp64-prefix", type=int, default=1500,
+                    help="requests of the same stream fed to the one-at-a-time FP64 server")
+    ap.add_argument("--circle", type=int, default=1, help="0 disables the seeded-circle section")
+    ap.add_argument("--circle-max-iter", type=int, default=200)
+    ap.add_argument("--section", default="all", choices=["all", "batched", "stokes", "serve", "tcapply", "circle"],
                     help="batched / stokes / serve: run only that section and print its object (profiling); "
                          "tcapply: only the batched section's dominant-kernel timing")
-    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--oracle-n", type=int, default=8)
-    ap.add_argument("--oracle-seconds", type=float, default=15.0)
+    ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-n", type=int, default=12)
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--oracle-rounds", type=int, default=2)
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle sample (runs in a fresh single-threaded process)
+# CPU oracle timing.  A worker process (OMP / BLAS single-threaded, no GPU)
+# builds the oracle's hierarchy for a bounded sample of the workload (the same
+# problem on an n^3 mesh with n = --oracle-n, default 12: levels 12, 6, 3, the
+# last three of the 48^3 hierarchy, same 3^3 dense bottom) and then, on
+# request, times solves single-threaded, or as independent solves on all host
+# cores (a fork pool sharing the hierarchy).  The worker starts before any GPU
+# work; the GPU arm lets it build while the GPU sections run and asks for the
+# timings afterwards, so the CPU numbers are not taken under GPU host load.
 # ---------------------------------------------------------------------------
 
-def oracle_sample(args):
-    import numpy as np
+def cpu_info():
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=20).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count(), "usable_cores": usable}
 
+
+_ORACLE = {}
+
+
+def _oracle_solve(seed):
     from oracle import krylov, ldg
-    from oracle import multigrid as mg
     from paper_2412_12506_gb300.inputs import random_rhs
+    P = _ORACLE
+    rhs = ldg.project_out_constant(random_rhs(P["N"], P["b"], seed=seed), P["d"], P["p"], P["N"])
+    t0 = time.perf_counter()
+    _, k, _ = krylov.pcg(P["A"], P["V"], rhs, tol=P["tol"])
+    return time.perf_counter() - t0, k
+
+
+def oracle_worker(args):
+    """--oracle-worker: build, print {"ready": setup_s}, then serve requests on
+    stdin -- "single SECONDS", "pool WORKERS ROUNDS", "quit" -- one JSON line each."""
+    import multiprocessing as mp
+
+    from oracle import multigrid as mg
     d, n, p = args.dim, args.oracle_n, args.p
-    N, b = n ** d, (p + 1) ** d
+    t0 = time.perf_counter()
     levels = mg.build_levels(d, n, p)
-    V = mg.VCycle(levels, "sai", 3, 3)
-    A = levels[0].A.mat
-    times, iters = [], []
-    t_end = time.perf_counter() + args.oracle_seconds
+    _ORACLE.update(d=d, p=p, N=n ** d, b=(p + 1) ** d, tol=args.tol, A=levels[0].A.mat,
+                   V=mg.VCycle(levels, "sai", 3, 3))
+    print(json.dumps({"ready": time.perf_counter() - t0, "n": n}), flush=True)
     seed = 0
-    while time.perf_counter() < t_end or not times:
-        rhs = ldg.project_out_constant(random_rhs(N, b, seed=seed), d, p, N)
-        t0 = time.perf_counter()
-        _, k, _ = krylov.pcg(A, V, rhs, tol=args.tol)
-        times.append(time.perf_counter() - t0)
-        iters.append(k)
-        seed += 1
-    t = float(np.median(times))
-    scale = (args.n / n) ** d          # work per solve grows with the element count
-    return {"solve_s": t, "solves": len(times), "iters": iters, "n": n, "scale": scale,
-            "value": 1.0 / (t * scale)}
+    for line in sys.stdin:
+        cmd = line.split()
+        if not cmd or cmd[0] == "quit":
+            break
+        if cmd[0] == "single":
+            t_end = time.perf_counter() + float(cmd[1])
+            times, iters = [], []
+            while time.perf_counter() < t_end or not times:
+                t, k = _oracle_solve(seed)
+                seed += 1
+                times.append(t)
+                iters.append(k)
+            print(json.dumps({"solves": len(times), "seconds": sum(times), "iters": iters}), flush=True)
+        elif cmd[0] == "pool":
+            workers, rounds = int(cmd[1]), int(cmd[2])
+            ctx = mp.get_context("fork")          # this process never touches a GPU
+            with ctx.Pool(workers) as pool:
+                pool.map(_oracle_solve, range(10 ** 6, 10 ** 6 + workers))       # warm-up round
+                walls, iters = [], []
+                for _ in range(rounds):
+                    t0 = time.perf_counter()
+                    res = pool.map(_oracle_solve, range(seed, seed + workers))
+                    walls.append(time.perf_counter() - t0)
+                    seed += workers
+                    iters += [k for _, k in res]
+            print(json.dumps({"workers": workers, "round_s": walls, "iters": iters}), flush=True)
 
 
-def run_oracle_subprocess(args):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--oracle-n", str(args.oracle_n),
-           "--oracle-seconds", str(args.oracle_seconds), "--n", str(args.n), "--p", str(args.p),
-           "--dim", str(args.dim), "--tol", str(args.tol)]
-    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
-    if out.returncode != 0:
-        raise RuntimeError("oracle sample failed:\n" + out.stderr[-2000:])
-    return json.loads(out.stdout.strip().splitlines()[-1])
+class OracleWorker:
+    def __init__(self, args):
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        cmd = [sys.executable, os.path.abspath(__file__), "--oracle-worker", "--oracle-n", str(args.oracle_n),
+               "--p", str(args.p), "--dim", str(args.dim), "--tol", str(args.tol)]
+        self.proc = subprocess.Popen(cmd, env=env, stdin=subprocess.PIPE, stdout=subprocess.PIPE, text=True)
+        self.ready = None
+
+    def ask(self, line=None):
+        if line is not None:
+            self.proc.stdin.write(line + "\n")
+            self.proc.stdin.flush()
+        out = self.proc.stdout.readline()
+        if not out:
+            raise RuntimeError("oracle worker exited")
+        return json.loads(out)
+
+    def wait_ready(self):
+        if self.ready is None:
+            self.ready = self.ask()
+        return self.ready
+
+    def close(self):
+        try:
+            self.proc.stdin.write("quit\n")
+            self.proc.stdin.flush()
+            self.proc.wait(timeout=60)
+        except Exception:
+            self.proc.kill()
 
 
-def cpu_baseline_obj(s, args):
-    return {"value": s["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"CPU oracle (numpy/scipy, FP64, 1 thread): PCG+SAI1 V-cycle solves of the same problem "
-                       f"on a {s['n']}^{args.dim} mesh (p={args.p}), {s['solves']} solves, median "
-                       f"{s['solve_s']:.3f} s/solve, iterations {sorted(set(s['iters']))}; scaled by the element "
-                       f"ratio {s['scale']:.0f} to {args.n}^{args.dim} (iteration counts are mesh independent)")}
+def cpu_baseline_obj(args, single, pool, ready, info):
+    """The oracle on all host cores (independent solves in a fork pool), scaled
+    by the element ratio to the workload; the single-threaded rate beside it."""
+    scale = (args.n / args.oracle_n) ** args.dim
+    per_round = pool["workers"] / (sorted(pool["round_s"])[len(pool["round_s"]) // 2])
+    one = single["solves"] / single["seconds"]
+    return {"value": per_round / scale, "unit": UNIT, "cores": pool["workers"], "kind": "oracle",
+            "sample": (f"CPU oracle (numpy/scipy, FP64): PCG + SAI1 V-cycle solves of the same problem on a "
+                       f"{args.oracle_n}^{args.dim} mesh (p = {args.p}, levels {args.oracle_n} .. 3, the last "
+                       f"three of the {args.n}^{args.dim} hierarchy), measured directly: "
+                       f"{len(pool['iters'])} solves as {pool['workers']} concurrent single-threaded "
+                       f"processes ({per_round:.3f} solves/s), {single['solves']} solves on one thread "
+                       f"({one:.3f} solves/s), iterations {sorted(set(pool['iters'] + single['iters']))}; "
+                       f"value = all-cores rate / {scale:.0f} (the element ratio to {args.n}^{args.dim}; "
+                       f"iteration counts are mesh independent); hierarchy setup {ready['ready']:.0f} s, "
+                       f"not timed"),
+            "measured": {"workload": f"poisson{args.dim}d_n{args.oracle_n}_p{args.p}_sai1",
+                         "solves_per_s_all_cores": per_round, "solves_per_s_one_thread": one,
+                         "scale_to_workload": 1.0 / scale},
+            "single_thread_value": one / scale, **info}
 
 
 # ---------------------------------------------------------------------------
@@ -243,10 +343,11 @@ class Clocks:
 
 def tc_apply_roofline(Hb, op, R, ldgmg, torch, dev, stream, reps=20):
     """The batched section's dominant kernel: the finest-level SAI B apply on the
-    tensor cores (3 untimed applies, then `reps` timed back to back).  One
-    apply is two launches: the split of X into its hi / lo operand images and
-    the tensor-core kernel; the time covers both, the algorithmic bytes are
-    those of Y = B X alone."""
+    tensor cores (3 untimed applies, then `reps` timed back to back).  With the
+    cached kernel (2D b = 16, max_rhs <= 64) one apply is one launch that reads
+    FP32 X itself; with the per-use kernel it is two launches, the split of X
+    into hi / lo operand images and the tensor-core kernel, and the time covers
+    both.  The algorithmic bytes are those of Y = B X alone."""
     b = op.b
     xv = torch.randn(op.size * R, dtype=torch.float32, device=dev)
     yv = torch.empty_like(xv)
@@ -266,7 +367,11 @@ def tc_apply_roofline(Hb, op, R, ldgmg, torch, dev, stream, reps=20):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm = peaks.get("hbm_gbs", 6800.0)
     tc_peak = peaks.get("bf16_tflops", 1900.0)
-    return {"bound": "hbm", "kernel": f"split_x_kernel + bsr_tc_kernel<{b}, fp32 split> finest-level B apply, {R} RHS",
+    strip, slots, lpr = Hb.tc_schedule
+    kname = (f"bsr_tc_cached_kernel<fp32 split> finest-level B apply, {R} RHS (strip width {strip}, {slots} x "
+             f"slots, {lpr:.2f} x_j loads per row)" if strip else
+             f"split_x_kernel + bsr_tc_kernel<{b}, fp32 split> finest-level B apply, {R} RHS")
+    return {"bound": "hbm", "kernel": kname,
             "achieved": bytes_ / (kms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
             "frac": bytes_ / (kms / 1e3) / 1e9 / hbm, "ms_per_launch": kms, "bytes_per_launch": bytes_,
             "tensor_TFLOPs": flops / (kms / 1e3) / 1e12, "tensor_peak_TFLOPs": tc_peak,
@@ -344,6 +449,64 @@ def run_batched(args, ldgmg, torch, np, dev, stream, barrier):
 # ---------------------------------------------------------------------------
 # two-phase Stokes with GMRES (Sec. 3.4.3)
 # ---------------------------------------------------------------------------
+
+def run_circle(args, ldgmg, torch, np, dev, stream, barrier):
+    """The interface workloads as configured with a seeded circle (centre in
+    [0.3, 0.7]^2, radius in [0.15, 0.3], element inside when its centroid is):
+    the 2D 256^2 p = 3 scalar problem with contrast 1e4 and 64 right-hand sides,
+    and the 2D 128^2 p = 2 stress-form Stokes problem with viscosity ratio 1e3.
+    Reports status (ENOTCONV when max_iter is hit), iterations and eta for each
+    smoother that is tried.  The headline lines use the paper's grid-aligned
+    inclusion instead: plain cell coarsening puts one polynomial across a
+    circle that cuts coarse cells, and the SAI smoother then degrades with the
+    contrast (the oracle shows the same on small meshes)."""
+    from paper_2412_12506_gb300.inputs import STOKES2D_128_P2 as W
+    from paper_2412_12506_gb300.inputs import circle_mu, fourier_force_rhs
+    out = {"geometry": "circle, seed 0: centre ~ U[0.3, 0.7]^2, radius ~ U[0.15, 0.3]"}
+    # scalar interface problem, 64 right-hand sides
+    n, p, R = args.batched_n, 3, min(args.batched_rhs, 64) or 64
+    mu = circle_mu(2, n, seed=0, mu_in=1e4)
+    op = ldgmg.Operator(2, n, p, mu)
+    gen = torch.Generator(device=dev).manual_seed(777)
+    B = op.project_kernel(torch.randn(R, op.size, dtype=torch.float64, device=dev, generator=gen))
+    scal = {}
+    for name, kw in (("sai1_fp32_batched", dict(smoother="sai", precision="fp32", max_rhs=R)),
+                     ("jacobi_fp32_batched", dict(smoother="jacobi", precision="fp32", max_rhs=R)),
+                     ("sai1_fp64_single", dict(smoother="sai", precision="fp64"))):
+        H = ldgmg.Hierarchy(op, nu1=3, nu2=3, max_iter=args.circle_max_iter, **kw)
+        rhs = B if kw.get("max_rhs", 1) > 1 else B[0].clone()
+        X = torch.empty_like(rhs)
+        t0 = time.time()
+        _, it, rr, st = H.solve(rhs, args.tol, x=X, check=False)
+        torch.cuda.synchronize()
+        its = it if isinstance(it, list) else [it]
+        rrs = rr if isinstance(rr, list) else [rr]
+        scal[name] = {"status": "ENOTCONV" if st == ldgmg.ENOTCONV else ("OK" if st == ldgmg.OK else str(st)),
+                      "iterations": [min(its), max(its)], "worst_relres": max(rrs), "eta": eta_of(H.history(0)),
+                      "seconds": time.time() - t0}
+        del H
+    out["interface2d_n%d_p3_circle1e4_%drhs" % (n, R)] = scal
+    # Stokes, stress form, viscosity 1 / 1e3 on the circle
+    ns = args.stokes_n
+    ops = ldgmg.Operator(2, ns, W.p, circle_mu(2, ns, seed=0, mu_in=W.mu_in), stokes=W.extra["gamma"])
+    rhs = torch.tensor(fourier_force_rhs(2, ns, W.p, W.extra["force_seed"], W.extra["force_modes"]),
+                       dtype=torch.float64, device=dev)
+    ops.project_kernel(rhs)
+    st_out = {}
+    for name, kw, tol in (("sai1_fgmres_fp32", dict(precision="fp32", krylov="fgmres"), args.stokes_tol),
+                          ("sai1_gmres_fp64_paper_form", dict(precision="fp64", krylov="gmres"), args.tol)):
+        H = ldgmg.Hierarchy(ops, smoother="sai", nu1=3, nu2=3, max_iter=args.circle_max_iter, **kw)
+        x = torch.empty_like(rhs)
+        t0 = time.time()
+        _, it, rr, st = H.solve(rhs, tol, x=x, check=False)
+        torch.cuda.synchronize()
+        st_out[name] = {"status": "ENOTCONV" if st == ldgmg.ENOTCONV else ("OK" if st == ldgmg.OK else str(st)),
+                        "tol": tol, "iterations": it, "true_relres": rr, "eta": eta_of(H.history(0)),
+                        "seconds": time.time() - t0}
+        del H
+    out["stokes2d_n%d_p2_stress_circle1000" % ns] = st_out
+    return out
+
 
 def run_stokes(args, ldgmg, torch, np, dev, stream, barrier):
     from paper_2412_12506_gb300.inputs import STOKES2D_128_P2 as W
@@ -511,43 +674,70 @@ def run_serve(args, ldgmg, torch, np, dev, stream, barrier):
     launches = ldgmg.kernel_launches() - l0
     srv.close()
     lat = np.array([r["t_end"] - r["t_submit"] for r in results]) * 1e3
+    queue = np.array([r["t_start"] - r["t_submit"] for r in results]) * 1e3
+    service = np.array([r["t_end"] - r["t_start"] for r in results]) * 1e3
     span = max(r["t_end"] for r in results) - min(r["t_submit"] for r in results)
     ok = sum(1 for r in results if r["status"] == ldgmg.OK and r["relres"] <= 1.05 * args.tol)
     batches = np.array([r["batch"] for r in results])
-    # FP64 one-at-a-time GPU solver on a sample of the same stream
-    sample = reqs[:args.serve_fp64_sample]
-    hier = {}
-    ms64 = []
-    for q in sample:
+    # The plain FP64 GPU solver, one request at a time (one worker, no
+    # batching, FP64 V-cycle), fed the same Poisson arrival stream (the same
+    # arrival times and right-hand sides) for its first `prefix` requests;
+    # latency includes its queueing.  The engine's latency over the same
+    # prefix is reported beside it.
+    prefix = min(len(reqs), args.serve_fp64_prefix)
+    s64 = ldgmg.Server(workers=1, max_batch=1, precision="fp64")
+    t0 = time.time()
+    warm = [s64.submit(c[0], c[1], c[2], rhs_of({"dim": c[0], "n": c[1], "p": c[2], "contrast": c[3],
+                                                 "rhs_seed": 0})[1], mu=mus[c], tol=args.tol) for c in classes]
+    for t in warm:
+        s64.wait(t)
+    build64_s = time.time() - t0
+    res64 = [None] * prefix
+    tk64 = [None] * prefix
+    ready64 = threading.Semaphore(0)
+
+    def waiter64():
+        for i in range(prefix):
+            ready64.acquire()
+            res64[i] = s64.wait(tk64[i])[1]
+
+    th = threading.Thread(target=waiter64)
+    th.start()
+    base = s64.clock()
+    for i in range(prefix):
+        q = reqs[i]
+        delay = base + arr[i] - s64.clock()
+        if delay > 0:
+            time.sleep(delay)
         c, r = rhs_of(q)
-        if c not in hier:
-            op = ldgmg.Operator(c[0], c[1], c[2], mus[c])
-            hier[c] = (op, ldgmg.Hierarchy(op, smoother="sai", precision="fp64"))
-        H = hier[c][1]
-        x = torch.empty(r.size, dtype=torch.float64)
-        rt = torch.from_numpy(r)
-        H.solve(rt, args.tol, x=x)                              # warm this class
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        H.solve(rt, args.tol, x=x)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64.append(e0.elapsed_time(e1))
-    del hier
+        tk64[i] = s64.submit(q["dim"], q["n"], q["p"], r, mu=mus[c], tol=args.tol)
+        ready64.release()
+    th.join()
+    s64.close()
+    lat64 = np.array([r["t_end"] - r["t_submit"] for r in res64]) * 1e3
+    svc64 = np.array([r["t_end"] - r["t_start"] for r in res64]) * 1e3
+    span64 = max(r["t_end"] for r in res64) - min(r["t_submit"] for r in res64)
+    ok64 = sum(1 for r in res64 if r["status"] == ldgmg.OK and r["relres"] <= 1.05 * args.tol)
+
+    def pct(v):
+        return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+
     return {
         "workload": f"serving_{len(reqs)}req_poisson_arrivals_{len(classes)}classes",
         "requests": len(reqs), "classes": len(classes), "workers": args.serve_workers, "max_batch": 32,
         "arrival_rate_per_s": rate, "closed_burst_capacity_per_s": capacity,
-        "solves_per_s": len(reqs) / span, "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                                                         "p99": float(np.percentile(lat, 99))},
+        "solves_per_s": len(reqs) / span, "latency_ms": pct(lat), "queue_ms": pct(queue), "service_ms": pct(service),
         "reached_tol": ok, "mean_batch": float(batches.mean()), "max_batch_seen": int(batches.max()),
         "class_builds_s": build_s, "builds": int(stats["builds"]), "evictions": int(stats["evictions"]),
         "hbm_resident_gb": stats["bytes_peak"] / 1e9, "gpu_launches": int(launches),
         "vcycle": "FP32 (batched tensor-core classes for b = 16 / 64), FP64 flexible CG",
-        "fp64_one_at_a_time": {"solves_per_s": 1e3 / float(np.mean(ms64)),
-                               "latency_ms": {"p50": float(np.percentile(ms64, 50)),
-                                              "p99": float(np.percentile(ms64, 99))},
-                               "sample": len(sample)},
+        "same_prefix": {"requests": prefix, "latency_ms": pct(lat[:prefix]), "queue_ms": pct(queue[:prefix]),
+                        "service_ms": pct(service[:prefix])},
+        "fp64_one_at_a_time": {"requests": prefix, "arrival_rate_per_s": rate,
+                               "solves_per_s": prefix / span64, "latency_ms": pct(lat64),
+                               "service_ms": pct(svc64), "reached_tol": ok64, "class_builds_s": build64_s,
+                               "how": "same arrival times and right-hand sides, one worker, no batching, FP64 "
+                                      "V-cycle and CG; latency includes queueing"},
     }
 
 
@@ -557,8 +747,8 @@ def run_serve(args, ldgmg, torch, np, dev, stream, barrier):
 
 def main():
     args = parse()
-    if args.oracle_sample:
-        print(json.dumps(oracle_sample(args)))
+    if args.oracle_worker:
+        oracle_worker(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -567,33 +757,57 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        s = oracle_sample(args) if os.environ.get("OMP_NUM_THREADS") == "1" else run_oracle_subprocess(args)
-        cb = cpu_baseline_obj(s, args)
+        # the CPU oracle on all host cores: each step is one round of
+        # independent single-threaded solves of the measured sample, one per core
+        info = cpu_info()
+        workers = max(1, info["usable_cores"])
+        w = OracleWorker(args)
+        ready = w.wait_ready()
+        w.proc.stdin.write(f"pool {workers} {args.warmup + args.steps}\n")
+        w.proc.stdin.flush()
+        pool = w.ask()
+        w.close()
+        walls = pool["round_s"][args.warmup:] if len(pool["round_s"]) > args.warmup else pool["round_s"]
+        total = sum(walls)
+        value = workers * len(walls) / total
+        scale = (args.n / args.oracle_n) ** args.dim
+        mwork = f"poisson{args.dim}d_n{args.oracle_n}_p{args.p}_sai1"
+        mat_gb = 3 * args.oracle_n ** args.dim * (2 * args.dim + 1) * (args.p + 1) ** (2 * args.dim) * 8 / 1e9
         print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": s["value"], "unit": UNIT, "n_gpus": 0,
-            "steps": s["solves"], "warmup": 0, "ms_per_step": s["solve_s"] * s["scale"] * 1e3,
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": len(walls), "warmup": args.warmup, "ms_per_step": total / len(walls) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"poisson{args.dim}d_n{args.n}_p{args.p}_sai1",
-                                             "inputs": "larger than L2"},
-            "cpu_baseline": cb,
-            "e2e": {"value": s["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+            "data": "synthetic",
+            "config": {"workload": mwork, "step": f"{workers} concurrent single-threaded oracle solves",
+                       "inputs": f"finest A, B, B^T {mat_gb:.2f} GB (FP64 block-CSR)"},
+            "scaled_to_workload": {"workload": f"poisson{args.dim}d_n{args.n}_p{args.p}_sai1",
+                                   "factor": 1.0 / scale, "value": value / scale,
+                                   "why": "element ratio; iteration counts are mesh independent"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": (f"CPU oracle (numpy/scipy, FP64) PCG + SAI1 V-cycle solves on a "
+                                        f"{args.oracle_n}^{args.dim} mesh, p = {args.p}, {workers} concurrent "
+                                        f"single-threaded processes per step; hierarchy setup "
+                                        f"{ready['ready']:.0f} s before the timed steps"), **info},
+            "iterations": sorted(set(pool["iters"])),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
-    if args.section in ("batched", "stokes", "serve", "tcapply"):
+    if args.section in ("batched", "stokes", "serve", "tcapply", "circle"):
         import numpy as np
         import torch
         torch.cuda.set_device(local_rank)
         from paper_2412_12506_gb300 import ldgmg
         dev = torch.device("cuda", local_rank)
-        fn = {"batched": run_batched, "stokes": run_stokes, "serve": run_serve, "tcapply": run_tcapply}[args.section]
+        fn = {"batched": run_batched, "stokes": run_stokes, "serve": run_serve, "tcapply": run_tcapply,
+              "circle": run_circle}[args.section]
         out = fn(args, ldgmg, torch, np, dev, torch.cuda.current_stream(), lambda: None)
         print(json.dumps(out))
         return
 
-    # the CPU oracle sample runs first, in a separate process, before any GPU work
-    cpu = None
+    # the CPU oracle worker starts first, in a separate process, before any GPU work
+    oracle_w = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(run_oracle_subprocess(args), args)
+        oracle_w = OracleWorker(args)
 
     import numpy as np
     import torch
@@ -670,6 +884,26 @@ def main():
         fp64 = {"solves_per_s": args.fp64_steps / (ms64 / 1e3), "p50_ms": float(np.median(lat64)),
                 "iterations": [k for k, _ in it64], "mixed_rel_err_vs_fp64": err}
 
+    # the other reduced V-cycle precisions of the same workload (FP32, BF16
+    # storage; FP32 accumulate), each against the FP64 solution of the same rhs
+    other_prec = {}
+    if args.other_prec_steps > 0 and fp64 is not None:
+        ref_rhs = rhs[(args.warmup + args.steps - 1) % len(rhs)]
+        for prec in ("fp32", "bf16", "fp16"):
+            if prec == args.precision:
+                continue
+            Hp = ldgmg.Hierarchy(op, smoother="sai", nu1=3, nu2=3, precision=prec)
+            xp = torch.empty_like(xs)
+            msp, latp, itp, _ = timed(Hp, args.other_prec_steps, 1, rhs, xp)
+            Hp.solve(ref_rhs, args.tol, x=xp)
+            op.project_kernel(xp)
+            errp = float(torch.linalg.norm(xp - x64) / torch.linalg.norm(x64))
+            other_prec[prec] = {"solves_per_s": args.other_prec_steps / (msp / 1e3), "p50_ms": float(np.median(latp)),
+                                "iterations": [k for k, _ in itp], "final_relres": max(r for _, r in itp),
+                                "rel_err_vs_fp64": errp, "hierarchy_gb": Hp.device_bytes / 1e9}
+            del Hp
+            torch.cuda.empty_cache()
+
     # e2e: the same solves through the C-ABI with pinned host buffers
     hrhs = [r.cpu().pin_memory() for r in rhs[:2]]
     hx = torch.empty(size, dtype=torch.float64).pin_memory()
@@ -729,9 +963,22 @@ def main():
     batched = run_batched(args, ldgmg, torch, np, dev, stream, barrier) if args.batched_rhs > 0 else None
     stokes = run_stokes(args, ldgmg, torch, np, dev, stream, barrier) if args.stokes_n > 0 else None
     serve = run_serve(args, ldgmg, torch, np, dev, stream, barrier) if args.serve_requests > 0 else None
+    circle = run_circle(args, ldgmg, torch, np, dev, stream, barrier) if args.circle else None
     if rank != 0:
         reps.close()
         return
+    cpu = None
+    if oracle_w is not None:
+        # GPU work is done: time the oracle on the host cores now
+        try:
+            ready = oracle_w.wait_ready()
+            single = oracle_w.ask(f"single {args.oracle_seconds}")
+            info = cpu_info()
+            pool = oracle_w.ask(f"pool {max(1, info['usable_cores'])} {args.oracle_rounds}")
+            cpu = cpu_baseline_obj(args, single, pool, ready, info)
+        except Exception as e:          # the CPU baseline is context; report why it is missing
+            cpu = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
+        oracle_w.close()
     dtype = {"fp16": "f16-stored/f32 V-cycle + f64 CG", "fp32": "f32 V-cycle + f64 CG",
              "bf16": "bf16-stored/f32 V-cycle + f64 CG", "fp64": "f64"}[args.precision]
     line = {
@@ -745,9 +992,10 @@ def main():
         "iterations": [k for k, _ in iters], "final_relres": max(rr for _, rr in iters),
         "eta": eta_of(H.history()),
         "fp64_path": fp64,
+        "other_precisions": other_prec,
         "spmv_fp64": {"ms": spmv_ms, "GB_per_s": spmv_bytes / (spmv_ms / 1e3) / 1e9,
                       "frac_of_hbm": spmv_bytes / (spmv_ms / 1e3) / 1e9 / peak},
-        "roofline": roofline, "batched": batched, "stokes": stokes, "serve": serve, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "roofline": roofline, "batched": batched, "stokes": stokes, "serve": serve, "circle": circle, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "setup_s": setup_s,
     }
     print(json.dumps(line))

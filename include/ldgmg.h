@@ -164,10 +164,19 @@ ldgmg_status ldgmg_op_device_bytes(const ldgmg_op* op, size_t* bytes);
 ldgmg_status ldgmg_hier_device_bytes(const ldgmg_hier* h, size_t* bytes);
 
 /* Launch shape chosen by the setup-time autotuner of the tensor-core apply
- * (batched hierarchies): CTAs per SM (0 when not tuned) and the level-0
- * smoother apply's time with max_rhs right-hand sides at that shape (ms).
- * The apply's result does not depend on the shape. */
+ * (batched hierarchies): CTAs per SM of the per-use kernel (0 when that
+ * kernel is not tuned: every matrix runs the cached kernel below) and the
+ * level-0 smoother apply's time with max_rhs right-hand sides at the chosen
+ * shape (ms).  The apply's result does not depend on the shape. */
 ldgmg_status ldgmg_hier_tuning(const ldgmg_hier* h, int* tc_ctas_per_sm, double* tc_ms);
+
+/* The cached tensor-core apply of batched 2D hierarchies with b = 16 and
+ * max_rhs <= 64 (one CTA per SM; rows in strips of `strip` element columns
+ * walked along y; converted x_j kept in shared-memory slots): the autotuned
+ * strip width (0 when the hierarchy does not use this kernel), the x slots
+ * per CTA and the x_j loads per block row of one level-0 smoother apply
+ * (each load reads x_j from HBM or L2 once). */
+ldgmg_status ldgmg_hier_tc_schedule(const ldgmg_hier* h, int* strip, int* x_slots, double* loads_per_row);
 
 /* Field structure: nfields = 1 (scalar) or dim + 1 (Stokes), field_b = (p+1)^dim
  * dofs per field and element (b = nfields * field_b). */

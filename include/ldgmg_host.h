@@ -52,6 +52,20 @@ ldgmg_status ldgmg_host_export(const ldgmg_host_hier* h, int level, int which, i
  * colours.  EINVAL on the bottom level or for other smoothers. */
 ldgmg_status ldgmg_host_colours(const ldgmg_host_hier* h, int level, int* colour, int* ncolours);
 
+/* Schedule of the cached tensor-core apply (2D meshes, b = 16) that the
+ * library builds for a block pattern (row_ptr: n*n + 1 entries, col), for
+ * rcap right-hand sides, storage prec (LDGMG_FP32 or LDGMG_BF16), `ctas` CTAs
+ * and strip width `strip`.  info[0..3] = CTAs used, x slots per CTA, strip
+ * width, most blocks in a row; *nloads = x_j loads of one apply.  rec (n*n
+ * records of 16 int32 in processing order: row, first block, first load,
+ * nnz | nld << 16, then 16 bytes of block slots and 16 bytes of load slots,
+ * 16 bytes unused), seg (CTAs + 1 step offsets) and ld_elem (nloads element
+ * indices) may be NULL.  EUNSUPPORTED with the reason when no schedule fits
+ * (the library then uses the per-use tensor-core kernel).  For tests. */
+ldgmg_status ldgmg_host_tc_plan(int n, const int64_t* row_ptr, const int32_t* col, int rcap, int prec, int ctas,
+                                int strip, int* info, int64_t* nloads, int32_t* rec, int32_t* seg,
+                                int32_t* ld_elem);
+
 void ldgmg_host_free(ldgmg_host_hier* h);
 
 #ifdef __cplusplus

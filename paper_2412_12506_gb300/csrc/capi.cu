@@ -99,10 +99,18 @@ static ldgmg_status dalloc(T** p, size_t bytes) { return dalloc_impl(p, bytes, t
 template <class T>
 static ldgmg_status dalloc_tmp(T** p, size_t bytes) { return dalloc_impl(p, bytes, false); }
 
+static void free_sched(TcSched& S) {
+  cudaFree(S.rec);
+  cudaFree(S.seg);
+  cudaFree(S.ld_elem);
+  S = TcSched();
+}
+
 static void free_mat(DevMat& M) {
   cudaFree(M.row_ptr);
   cudaFree(M.col);
   cudaFree(M.vals);
+  free_sched(M.sched);
   M = DevMat();
 }
 
@@ -199,6 +207,7 @@ struct ldgmg_hier {
   void* ximg = nullptr;          // tensor-core path: operand images of the vector being applied
   size_t ximg_bytes = 0;         // its capacity (level 0 at max_rhs; grown for wider inspection applies)
   double tc_ms = 0.0;            // its measured time on level 0 with max_rhs right-hand sides
+  int tc_L = 0;                  // cached tensor-core apply: autotuned strip width (0: not used)
   // residual history of the last solve: ||r_k||^2 of right-hand side r at
   // hist[k * R + r], k = 0..iters (device, CG) / host copy after the solve
   double* hist = nullptr;
@@ -234,6 +243,22 @@ static ldgmg_status apply_mat(ldgmg_hier* h, const DevMat& M, int mode, const vo
     a.col = M.col;
     a.vals = M.vals;
     if (!h) return fail(LDGMG_EINVAL, "tensor-core apply without its hierarchy");
+    a.x = static_cast<const float*>(x);
+    a.rhs = static_cast<const float*>(rhs);
+    a.xin = static_cast<const float*>(xin);
+    a.y = static_cast<float*>(y);
+    a.s = s;
+    a.mode = mode;
+    a.R = R;
+    a.es = R * b;
+    a.rs = b;
+    a.err = h->err;
+    if (M.sched.rec && R <= M.sched.rcap) {
+      // x operands converted inside the kernel, cached in shared memory (tc_cached.cu)
+      a.ximg = nullptr;
+      CK(bsr_apply_tc_cached(a, M.sched, M.prec, st));
+      return LDGMG_OK;
+    }
     const size_t need = x_image_bytes(M.nrows, R, int(b));
     if (need > h->ximg_bytes) {
       // only ldgmg_level_apply_batched can ask for more right-hand sides than
@@ -255,17 +280,7 @@ static ldgmg_status apply_mat(ldgmg_hier* h, const DevMat& M, int mode, const vo
     }
     CK(split_x_images(static_cast<const float*>(x), M.nrows, R, int(b), h->ximg, st));
     a.ximg = h->ximg;
-    a.x = static_cast<const float*>(x);
-    a.rhs = static_cast<const float*>(rhs);
-    a.xin = static_cast<const float*>(xin);
-    a.y = static_cast<float*>(y);
-    a.s = s;
-    a.mode = mode;
-    a.R = R;
-    a.es = R * b;
-    a.rs = b;
-    a.err = h ? h->err : nullptr;
-    a.ctas_per_sm = h ? h->tc_ctas : 0;
+    a.ctas_per_sm = h->tc_ctas;
     CK(bsr_apply_tc(a, M.b, M.prec, st));
     return LDGMG_OK;
   }
@@ -398,6 +413,15 @@ ldgmg_status ldgmg_selftest_bounded_wait(void* stream) {
   cudaFree(d_err);
   if (c != cudaSuccess) return fail(LDGMG_ECUDA, std::string("bounded-wait self-test: ") + cudaGetErrorString(c));
   if (e) return fail(LDGMG_ETIMEOUT, "bounded device wait gave up (self-test: expected)");
+  return LDGMG_OK;
+}
+
+ldgmg_status ldgmg_hier_tc_schedule(const ldgmg_hier* h, int* strip, int* x_slots, double* loads_per_row) {
+  if (!h) return fail(LDGMG_EINVAL, "null hierarchy");
+  const TcSched& S = h->lv.size() > 1 ? h->lv[0].S.sched : TcSched();
+  if (strip) *strip = S.rec ? h->tc_L : 0;
+  if (x_slots) *x_slots = S.rec ? S.S : 0;
+  if (loads_per_row) *loads_per_row = S.rec && h->lv[0].N ? double(S.nloads) / double(h->lv[0].N) : 0.0;
   return LDGMG_OK;
 }
 
@@ -633,6 +657,115 @@ static ldgmg_status tune_tc(ldgmg_hier* h, cudaStream_t st) {
   return status;
 }
 
+// Schedule of the cached tensor-core apply for M (2D, b = 16) with strip
+// width L, halving L while the plan does not fit; *ok = false leaves M on the
+// per-use kernel.  counted: the arrays belong to the hierarchy (false: a
+// tuning probe, freed by the caller).
+static ldgmg_status attach_sched(ldgmg_hier* h, DevMat& M, int dim, int n, int L, bool counted, cudaStream_t st,
+                                 bool* ok) {
+  *ok = false;
+  free_sched(M.sched);
+  if (!M.tc_image || M.b != 16 || h->Rmax > 64 || M.nrows == 0) return LDGMG_OK;
+  std::vector<int> rp32(size_t(M.nrows) + 1);
+  std::vector<int32_t> col(size_t(M.nnzb));
+  CK(cudaMemcpyAsync(rp32.data(), M.row_ptr, rp32.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (M.nnzb) CK(cudaMemcpyAsync(col.data(), M.col, col.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const std::vector<int64_t> rp(rp32.begin(), rp32.end());
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TcSchedHost H;
+  bool planned = false;
+  for (int l = L; l >= 1 && !planned; l /= 2)
+    planned = tc_sched_plan(dim, n, M.nrows, rp.data(), col.data(), h->Rmax, M.prec, sms, l, &H).empty();
+  if (!planned) return LDGMG_OK;
+  TcSched& S = M.sched;
+  auto alloc = [&](auto** p, size_t bytes) { return counted ? dalloc(p, bytes) : dalloc_tmp(p, bytes); };
+  if (alloc(&S.rec, H.rec.size()) != LDGMG_OK || alloc(&S.seg, H.seg.size() * sizeof(int)) != LDGMG_OK ||
+      alloc(&S.ld_elem, H.ld_elem.size() * sizeof(int)) != LDGMG_OK) {
+    free_sched(S);
+    return LDGMG_ENOMEM;
+  }
+  CK(cudaMemcpyAsync(S.rec, H.rec.data(), H.rec.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(S.seg, H.seg.data(), H.seg.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(S.ld_elem, H.ld_elem.data(), H.ld_elem.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  S.G = H.G;
+  S.S = H.S;
+  S.L = H.L;
+  S.kmax = H.kmax;
+  S.rcap = H.rcap;
+  S.nloads = H.nloads;
+  *ok = true;
+  return LDGMG_OK;
+}
+
+static bool needs_x_images(const ldgmg_hier* h) {
+  for (const DevLevel& D : h->lv)
+    for (const DevMat* M : {&D.A, &D.S, &D.ST})
+      if (M->tc_image && M->nrows > 0 && !M->sched.rec) return true;
+  return false;
+}
+
+// Autotuner of the cached tensor-core apply: times the level-0 smoother apply
+// with max_rhs right-hand sides (zeroed level vectors, median of 3 after one
+// warm-up) for strip widths 4, 8 and 16 and keeps the fastest, then attaches
+// the schedules of every tensor-core matrix at that width.  The result of
+// the apply does not depend on the width (a block row's MMAs are the same).
+static ldgmg_status setup_cached_tc(ldgmg_hier* h, cudaStream_t st) {
+  DevLevel& D = h->lv[0];
+  const int dim = h->op->host.dim;
+  if (h->lv.size() < 2 || !D.S.tc_image || D.b != 16 || h->Rmax > 64 || dim != 2) return LDGMG_OK;
+  const int R = h->Rmax;
+  const size_t bytes = size_t(D.N) * D.b * h->vsz * R;
+  CK(cudaMemsetAsync(D.rhs, 0, bytes, st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e30;
+  int best_L = 0;
+  ldgmg_status status = LDGMG_OK;
+  for (int L : {4, 8, 16}) {
+    bool ok = false;
+    status = attach_sched(h, D.S, dim, D.n, L, false, st, &ok);
+    if (status != LDGMG_OK) break;
+    if (!ok || D.S.sched.L != std::min(L, D.n)) continue;
+    std::vector<float> t;
+    for (int rep = 0; rep < 4 && status == LDGMG_OK; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) { status = fail(LDGMG_ECUDA, "tuner event"); break; }
+      status = apply_mat(h, D.S, M_Y, D.rhs, nullptr, nullptr, D.x, 1.0, R, st);
+      if (status != LDGMG_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        status = fail(LDGMG_ECUDA, "tuner timing");
+        break;
+      }
+      if (rep > 0) t.push_back(ms);
+    }
+    if (status != LDGMG_OK) break;
+    std::sort(t.begin(), t.end());
+    if (t[t.size() / 2] < best) {
+      best = t[t.size() / 2];
+      best_L = L;
+    }
+  }
+  free_sched(D.S.sched);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status == LDGMG_OK) status = check_err_flag(h, st);
+  if (status != LDGMG_OK || best_L == 0) return status;
+  h->tc_L = best_L;
+  h->tc_ms = best;
+  for (DevLevel& Dl : h->lv)
+    for (DevMat* M : {&Dl.A, &Dl.S, &Dl.ST}) {
+      bool ok = false;
+      CKS(attach_sched(h, *M, dim, Dl.n, best_L, true, st, &ok));
+    }
+  return LDGMG_OK;
+}
+
 ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, ldgmg_hier** out) {
   NvtxRange nvtx_("ldgmg_setup");
   g_err.clear();
@@ -683,6 +816,8 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
   sp.sai_level = o->sai_level;
   sp.balance = o->balance;
   sp.zeta = o->zeta;
+  // the SAI least-squares problems (one per distinct balanced column) on the device
+  sp.ls = [st](std::vector<LsProblem>& batch) { return sai_ls_device(batch, st); };
   const int nth = std::max(1u, std::thread::hardware_concurrency());
   for (int l = 0; l + 1 < nl; ++l) {
     HostLevel& L = l == 0 ? op->host : h->host[l];
@@ -782,15 +917,19 @@ ldgmg_status ldgmg_setup(ldgmg_op* op, const ldgmg_setup_opts* o, void* stream, 
     if (cudaMallocHost((void**)&h->hgs, size_t(m + 2) * sizeof(double)) != cudaSuccess)
       return bail(fail(LDGMG_ENOMEM, "cudaMallocHost"));
   }
-  if (batched) {
-    h->ximg_bytes = x_image_bytes(L0.N, h->Rmax, L0.b);
-    if (dalloc(&h->ximg, h->ximg_bytes) != LDGMG_OK) return bail(LDGMG_ENOMEM);
-  }
   if (cudaMemsetAsync(h->err, 0, sizeof(int), st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "memset"));
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(LDGMG_ECUDA, "setup sync"));
   if (batched) {
-    ldgmg_status s = tune_tc(h, st);
+    // cached tensor-core apply where a schedule fits (2D, b = 16), autotuned
+    // strip width; the per-use kernel with x images for every other matrix
+    ldgmg_status s = setup_cached_tc(h, st);
     if (s != LDGMG_OK) return bail(s);
+    if (needs_x_images(h)) {
+      h->ximg_bytes = x_image_bytes(L0.N, h->Rmax, L0.b);
+      if (dalloc(&h->ximg, h->ximg_bytes) != LDGMG_OK) return bail(LDGMG_ENOMEM);
+      s = tune_tc(h, st);
+      if (s != LDGMG_OK) return bail(s);
+    }
   }
   *out = h;
   return LDGMG_OK;

@@ -1151,16 +1151,21 @@ std::string setup_smoother(HostLevel& L, const SetupParams& sp, int nthreads) {
     cols[i].R = std::move(R);
     cols[i].key_id = it->second;
   }
-  // one balanced least-squares problem per distinct key
+  // one balanced least-squares problem per distinct key, in chunks (bounded
+  // host memory): W = [Atilde[R, S] | E[R, i]] built on the host threads,
+  // solved by sp.ls (the device) or by Householder QR on the host threads;
+  // rank-deficient ones take the minimum-norm solution on the host
   const int64_t nkeys = int64_t(keys.size());
   std::vector<std::vector<double>> sol(nkeys);
-  std::vector<char> ok(nkeys, 1);
-  parallel_for(nkeys, nthreads, [&](int64_t kid) {
+  auto build_W = [&](int64_t kid, LsProblem& P) {
     const int64_t i = rep[kid];
     const auto& S = cols[i].S;
     const auto& R = cols[i].R;
     const int m = int(R.size()) * b, nc = int(S.size()) * b;
-    std::vector<double> M(size_t(m) * nc, 0.0), Rhs(size_t(m) * b, 0.0), X;
+    P.m = m;
+    P.nc = nc;
+    P.nr = b;
+    P.W.assign(size_t(m) * (nc + b), 0.0);
     for (size_t ri = 0; ri < R.size(); ++ri)
       for (size_t kj = 0; kj < S.size(); ++kj) {
         const uint32_t id = A.find(R[ri], S[kj]);
@@ -1169,19 +1174,42 @@ std::string setup_smoother(HostLevel& L, const SetupParams& sp, int nthreads) {
         const double* ar = alpha.data() + size_t(R[ri]) * b;
         const double* ac = alpha.data() + size_t(S[kj]) * b;
         for (int c = 0; c < b; ++c) {
-          double* dst = M.data() + size_t(kj * b + c) * m + ri * b;
+          double* dst = P.W.data() + size_t(kj * b + c) * m + ri * b;
           for (int r = 0; r < b; ++r) dst[r] = (ar[r] * ac[c]) * blk[size_t(r) * b + c];
         }
       }
     size_t pos = 0;
     while (R[pos] != i) ++pos;
-    for (int c = 0; c < b; ++c) Rhs[size_t(c) * m + pos * b + c] = 1.0;
-    const std::vector<double> M0 = M, R0 = Rhs;
-    if (!householder_ls(M, m, nc, Rhs, b, X)) minnorm_ls(M0, m, nc, R0, b, X);
-    sol[kid] = std::move(X);  // nc x b column-major: Btilde[S, i]
-  });
-  for (int64_t k = 0; k < nkeys; ++k)
-    if (!ok[k]) return "rank-deficient SAI least-squares column (level n = " + std::to_string(L.n) + ")";
+    for (int c = 0; c < b; ++c) P.W[size_t(nc + c) * m + pos * b + c] = 1.0;
+  };
+  const size_t per = size_t(cols[rep[0]].R.size()) * b * (cols[rep[0]].S.size() * b + b) * sizeof(double);
+  const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nkeys, int64_t((size_t(1) << 30) / std::max<size_t>(per, 1))));
+  std::vector<LsProblem> batch;
+  for (int64_t k0 = 0; k0 < nkeys; k0 += chunk) {
+    const int64_t k1 = std::min(nkeys, k0 + chunk);
+    batch.assign(size_t(k1 - k0), LsProblem());
+    parallel_for(k1 - k0, nthreads, [&](int64_t t) { build_W(k0 + t, batch[size_t(t)]); });
+    if (sp.ls) {
+      const std::string err = sp.ls(batch);
+      if (!err.empty()) return err;
+    } else {
+      parallel_for(k1 - k0, nthreads, [&](int64_t t) {
+        LsProblem& P = batch[size_t(t)];
+        std::vector<double> M(P.W.begin(), P.W.begin() + size_t(P.m) * P.nc);
+        std::vector<double> Rhs(P.W.begin() + size_t(P.m) * P.nc, P.W.end());
+        P.ok = householder_ls(M, P.m, P.nc, Rhs, P.nr, P.X);
+      });
+    }
+    parallel_for(k1 - k0, nthreads, [&](int64_t t) {
+      LsProblem& P = batch[size_t(t)];
+      if (!P.ok) {
+        const std::vector<double> M0(P.W.begin(), P.W.begin() + size_t(P.m) * P.nc);
+        const std::vector<double> R0(P.W.begin() + size_t(P.m) * P.nc, P.W.end());
+        minnorm_ls(M0, P.m, P.nc, R0, P.nr, P.X);
+      }
+      sol[size_t(k0 + t)] = std::move(P.X);   // nc x b column-major: Btilde[S, i]
+    });
+  }
   // B_ki = alpha_k Btilde_ki alpha_i, pooled per (key, position)
   L.B = PBSR();
   L.B.pool.b = b;

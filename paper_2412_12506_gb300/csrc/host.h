@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -75,11 +76,26 @@ struct HostLevel {
   std::vector<int64_t> colour_ptr;
 };
 
+// One balanced SAI least-squares problem (Sec. 2.3.3): W = [M | Rhs], m rows,
+// nc + nr columns, column-major; the solution X (nc x nr, column-major)
+// minimises ||M X - Rhs||_F.  ok = false: M is numerically rank deficient
+// (|R_jj| <= 1e-12 max |R_jj| in its QR factor); the caller then takes the
+// minimum-norm solution.
+struct LsProblem {
+  int m = 0, nc = 0, nr = 0;
+  std::vector<double> W;
+  std::vector<double> X;
+  bool ok = false;
+};
+// Solves a batch of problems (fills X and ok); returns "" or an error message.
+typedef std::function<std::string(std::vector<LsProblem>&)> LsSolver;
+
 struct SetupParams {
   int smoother = 1;                // 0 Jacobi, 1 SAI, 2 multi-coloured Gauss-Seidel
   int sai_level = 1;
   int balance = 1;
   double zeta = 0.0;               // Stokes balancing (Sec. 3.3); <= 0: Table tab:zeta
+  LsSolver ls;                     // SAI least squares; empty: Householder QR on the host threads
 };
 
 // Table tab:zeta: tuned Stokes balancing value for (gamma, dim, p); 0.1 where

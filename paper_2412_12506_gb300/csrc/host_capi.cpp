@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "host.h"
+#include "kernels.h"
 
 using namespace ldgmg;
 
@@ -126,6 +127,25 @@ ldgmg_status ldgmg_host_export(const ldgmg_host_hier* h, int l, int which, int64
   if (col) std::copy(M->col.begin(), M->col.end(), col);
   if (vals)
     for (int64_t z = 0; z < M->nnzb(); ++z) std::memcpy(vals + z * bb, M->pool.get(M->id[z]), bb * sizeof(double));
+  return LDGMG_OK;
+}
+
+ldgmg_status ldgmg_host_tc_plan(int n, const int64_t* row_ptr, const int32_t* col, int rcap, int prec, int ctas,
+                                int strip, int* info, int64_t* nloads, int32_t* rec, int32_t* seg,
+                                int32_t* ld_elem) {
+  if (n < 1 || !row_ptr || !col || !info || !nloads) return herr(LDGMG_EINVAL, "null argument or bad size");
+  if (prec != LDGMG_FP32 && prec != LDGMG_BF16) return herr(LDGMG_EINVAL, "prec must be FP32 or BF16");
+  TcSchedHost H;
+  const std::string why = tc_sched_plan(2, n, int64_t(n) * n, row_ptr, col, rcap, prec, ctas, strip, &H);
+  if (!why.empty()) return herr(LDGMG_EUNSUPPORTED, why);
+  info[0] = H.G;
+  info[1] = H.S;
+  info[2] = H.L;
+  info[3] = H.kmax;
+  *nloads = H.nloads;
+  if (rec) std::memcpy(rec, H.rec.data(), H.rec.size());
+  if (seg) std::copy(H.seg.begin(), H.seg.end(), seg);
+  if (ld_elem) std::copy(H.ld_elem.begin(), H.ld_elem.begin() + H.nloads, ld_elem);
   return LDGMG_OK;
 }
 

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <string>
+#include <vector>
 
 namespace ldgmg {
 
@@ -16,6 +18,20 @@ enum Prec { P_FP64 = 0, P_FP32 = 1, P_BF16 = 2, P_FP16 = 3 };
 // tensor-core path (b = 16 or 64, tc_image = 1) have cs = b and are stored as
 // the BF16 operand images the tensor cores read (tc_image_offset below).
 inline int col_stride(int b) { return (b + 3) / 4 * 4; }
+// Schedule of the cached tensor-core apply (tc_cached.cu) of one matrix: the
+// processing order as 32-byte step records, the CTA ranges and the x loads,
+// all device arrays owned by the DevMat that holds it.
+struct TcSched {
+  int G = 0;                // CTAs (one per SM): CTA c takes steps [seg[c], seg[c + 1])
+  int S = 0;                // x slots per CTA
+  int L = 0;                // strip width (element columns)
+  int kmax = 0;             // most blocks in a row
+  int rcap = 0;             // most right-hand sides per call
+  int64_t nloads = 0;       // x_j loads per apply (all CTAs)
+  void* rec = nullptr;      // nrows step records
+  int* seg = nullptr;       // G + 1
+  int* ld_elem = nullptr;   // nloads + 32
+};
 struct DevMat {
   int64_t nrows = 0, nnzb = 0;
   int b = 0, cs = 0, prec = P_FP64;
@@ -24,6 +40,7 @@ struct DevMat {
   int* row_ptr = nullptr;   // nrows + 1
   int* col = nullptr;       // nnzb
   void* vals = nullptr;     // nnzb * b * b elements
+  TcSched sched;            // tensor-core images, 2D b = 16: cached apply schedule (rec == null: none)
 };
 
 // Epilogue of a block-row apply, acc_i = sum_j M_ij x_j:
@@ -80,6 +97,21 @@ int tc_max_ctas_per_sm(int b, int prec, int R);
 // prec: P_BF16 (2 MMAs per K step) or P_FP32 (3 MMAs: A_hi x_hi + A_hi x_lo + A_lo x_hi).
 // a.ximg must hold split_x_images(a.x) for the same R (a.x itself is not read).
 cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st);
+
+// Cached tensor-core apply (tc_cached.cu; 2D, b = 16, R <= 64, vectors
+// [element][rhs][mode] with es = R b, rs = b): the same arithmetic as
+// bsr_apply_tc without x images; a.ximg and a.ctas_per_sm are not used.
+// tc_sched_plan builds the host schedule for strip width L and G CTAs (or
+// returns why it cannot); the caller uploads it into a TcSched.
+struct TcSchedHost {
+  int G = 0, S = 0, L = 0, kmax = 0, rcap = 0;
+  int64_t nloads = 0;
+  std::vector<uint8_t> rec;
+  std::vector<int> seg, ld_elem;
+};
+std::string tc_sched_plan(int dim, int n, int64_t nrows, const int64_t* row_ptr, const int32_t* col, int rcap,
+                          int prec, int G, int L, TcSchedHost* out);
+cudaError_t bsr_apply_tc_cached(const BatchArgs& a, const TcSched& s, int prec, cudaStream_t st);
 
 // Operand images of a batched vector x ([element][rhs][mode], R right-hand
 // sides, b = 16 or 64) for the tensor-core apply: per element j the image of
@@ -190,6 +222,11 @@ cudaError_t bsr_apply_df1(const DevMat& M, const void* pairs, int mode, const do
 // FP64 apply with the same block reuse over R <= 64 right-hand sides (b = 16, 64)
 cudaError_t bsr_apply_multi64(const DevMat& M, int mode, const double* x, const double* rhs, double* y, int R,
                               cudaStream_t st);
+
+// Batched FP64 least squares of the SAI setup on the device (sai_ls.cu): fills
+// X and ok of every problem (host.h LsProblem); "" or an error message.
+struct LsProblem;
+std::string sai_ls_device(std::vector<LsProblem>& batch, cudaStream_t st);
 
 // launch-count bookkeeping for kernels defined in other translation units
 cudaError_t launched(int count = 1);

@@ -160,19 +160,19 @@ def zero_mean_rhs(N: int, b: int, seed: int, nfields: int = 1) -> np.ndarray:
 
 
 def serving_requests(count: int, seed: int):
-    """Request mix of the serving workload: 2D Poisson or interface problems
-    (meshes 16^2..256^2, p = 1..4, interface contrast 1e2 or 1e4 on the
-    inclusion (1/4, 3/4)^2) and 3D Poisson (8^3..32^3, p = 1..3), drawn
-    uniformly per field.  Returns a list of dicts with dim, n, p, contrast
-    (1 = Poisson) and a right-hand-side seed."""
+    """Request mix of the serving workload: 2D problems (meshes 16^2..256^2,
+    p = 1..4) and 3D problems (8^3..32^3, p = 1..3), each Poisson (contrast 1)
+    or an interface problem with contrast 1e2 or 1e4 on the inclusion
+    (1/4, 3/4)^d, drawn uniformly per field (3 in 4 requests are 2D).
+    Returns a list of dicts with dim, n, p, contrast and a right-hand-side
+    seed."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         if rng.random() < 0.75:
             dim, n, p = 2, int(rng.choice([16, 32, 64, 128, 256])), int(rng.integers(1, 5))
-            contrast = float(rng.choice([1.0, 1e2, 1e4]))
         else:
             dim, n, p = 3, int(rng.choice([8, 16, 32])), int(rng.integers(1, 4))
-            contrast = 1.0
+        contrast = float(rng.choice([1.0, 1e2, 1e4]))
         out.append({"dim": dim, "n": n, "p": p, "contrast": contrast, "rhs_seed": int(rng.integers(1 << 31))})
     return out

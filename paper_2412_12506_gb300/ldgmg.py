@@ -84,6 +84,7 @@ _SIGS = {
     "ldgmg_op_device_bytes": (_i, [_vp, _P(ctypes.c_size_t)]),
     "ldgmg_hier_device_bytes": (_i, [_vp, _P(ctypes.c_size_t)]),
     "ldgmg_hier_tuning": (_i, [_vp, _P(_i), _P(_d)]),
+    "ldgmg_hier_tc_schedule": (_i, [_vp, _P(_i), _P(_i), _P(_d)]),
     "ldgmg_solve_history": (_i, [_vp, _i, _vp, _i, _P(_i)]),
     "ldgmg_apply": (_i, [_vp, _vp, _vp, _i, _vp]),
     "ldgmg_project_kernel": (_i, [_vp, _vp, _i, _vp]),
@@ -111,6 +112,7 @@ _SIGS = {
                                    _P(_i64)]),
     "ldgmg_host_export": (_i, [_vp, _i, _i, _vp, _vp, _vp]),
     "ldgmg_host_colours": (_i, [_vp, _i, _vp, _P(_i)]),
+    "ldgmg_host_tc_plan": (_i, [_i, _vp, _vp, _i, _i, _i, _i, _vp, _P(_i64), _vp, _vp, _vp]),
     "ldgmg_host_free": (None, [_vp]),
     "ldgmg_server_create": (_i, [_P(ServerOpts), _P(_vp)]),
     "ldgmg_server_submit": (_i, [_vp, _P(Request), _P(ctypes.c_uint64)]),
@@ -265,6 +267,26 @@ class HostHierarchy:
             self._h = None
 
 
+def host_tc_plan(n, row_ptr, col, rcap=64, precision="fp32", ctas=152, strip=8):
+    """ldgmg_host_tc_plan: the cached tensor-core apply's schedule for a 2D
+    block pattern.  Returns a dict (ctas, slots, strip, kmax, nloads, rec as an
+    (n*n, 16) int32 array, seg, ld_elem)."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    cl = np.ascontiguousarray(col, dtype=np.int32)
+    info = np.zeros(4, np.int32)
+    nl = ctypes.c_int64()
+    args = (n, rp.ctypes.data_as(_vp), cl.ctypes.data_as(_vp), rcap, _PREC[precision], ctas, strip,
+            info.ctypes.data_as(_vp), ctypes.byref(nl))
+    _check(_lib.ldgmg_host_tc_plan(*args, None, None, None))
+    rec = np.zeros((n * n, 16), np.int32)
+    seg = np.zeros(int(info[0]) + 1, np.int32)
+    ld = np.zeros(max(nl.value, 1), np.int32)
+    _check(_lib.ldgmg_host_tc_plan(*args, rec.ctypes.data_as(_vp), seg.ctypes.data_as(_vp),
+                                   ld.ctypes.data_as(_vp)))
+    return dict(ctas=int(info[0]), slots=int(info[1]), strip=int(info[2]), kmax=int(info[3]), nloads=nl.value,
+                rec=rec, seg=seg, ld_elem=ld[:nl.value])
+
+
 # ---------------------------------------------------------------------------
 # device API
 # ---------------------------------------------------------------------------
@@ -356,6 +378,13 @@ class Hierarchy:
         c, t = ctypes.c_int(), ctypes.c_double()
         _check(_lib.ldgmg_hier_tuning(self._h, ctypes.byref(c), ctypes.byref(t)))
         return c.value, t.value
+
+    @property
+    def tc_schedule(self):
+        """Cached tensor-core apply: (strip width or 0, x slots per CTA, x_j loads per row)."""
+        L, S, lpr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(_lib.ldgmg_hier_tc_schedule(self._h, ctypes.byref(L), ctypes.byref(S), ctypes.byref(lpr)))
+        return L.value, S.value, lpr.value
 
     @property
     def vdtype(self):

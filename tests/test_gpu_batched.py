@@ -55,6 +55,52 @@ def test_tensor_core_apply_matches_stored_blocks(lib, d, n, p, R, prec):
         assert err < 1e-5, (which, err)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_cached_tensor_core_apply_against_stored_blocks_and_per_use_kernel(lib, prec):
+    """The cached kernel (max_rhs <= 64, 2D b = 16: one MMA per block on the
+    packed [x_hi; x_lo] operand) against the FP64 product of the exported
+    stored blocks (FP32 accumulation: 1e-5 of the largest entry) and against
+    the per-use kernel (taken for max_rhs > 64), on every level of an
+    interface hierarchy whose coarse rows have extra blocks.  Whole V-cycles
+    (all epilogues: plain, residual, update) are no less accurate against the
+    FP64 V-cycle than the per-use kernel's (the 1e4 contrast amplifies the
+    FP32 rounding of the applies to ~1e-3 in both).  A right-hand side applied
+    alone gives bit for bit its result in the 64-wide batch."""
+    from paper_2412_12506_gb300.inputs import square_mu
+    d, n, p = 2, 24, 3
+    op = lib.Operator(d, n, p, square_mu(d, n, 1e4))
+    Hc = lib.Hierarchy(op, smoother="sai", precision=prec, max_rhs=64, nu1=2, nu2=2)
+    Hu = lib.Hierarchy(op, smoother="sai", precision=prec, max_rhs=65, nu1=2, nu2=2)
+    H64 = lib.Hierarchy(op, smoother="sai", precision="fp64", max_rhs=64, nu1=2, nu2=2)
+    assert Hc.tc_schedule[0] > 0 and Hu.tc_schedule[0] == 0
+    rng = np.random.default_rng(9)
+    for R in (1, 7, 64):
+        for level in range(Hc.nlevels - 1):
+            inf = Hc.info(level)
+            N, b = inf["N"], inf["b"]
+            xs = rng.standard_normal((R, N * b)).astype(np.float32)
+            xb = torch.tensor(_batch_layout(xs, N, b).reshape(-1), device="cuda")
+            for which in (lib.MAT_A, lib.MAT_B, lib.MAT_BT):
+                yc = Hc.level_apply_batched(level, which, xb, R)
+                yu = Hu.level_apply_batched(level, which, xb, R)
+                rp, col, vals = Hc.export_level(level, which)
+                ref = _batch_layout((bsr_to_dense(rp, col, vals) @ xs.astype(np.float64).T).T, N, b).reshape(-1)
+                scale = np.abs(ref).max()
+                assert np.abs(yc.cpu().numpy() - ref).max() <= 1e-5 * scale, (R, level, which)
+                assert float((yc - yu).abs().max()) <= 2e-5 * scale, (R, level, which)
+                if R == 64:
+                    y1 = Hc.level_apply_batched(level, which, xb.view(N, R, b)[:, :1, :].contiguous().view(-1), 1)
+                    assert torch.equal(y1.view(N, b), yc.view(N, R, b)[:, 0, :]), (level, which)
+        X = torch.tensor(rng.standard_normal((R, op.size)), device="cuda")
+        op.project_kernel(X)
+        V64 = H64.vcycle(X)
+        ec = float((Hc.vcycle(X) - V64).abs().max() / V64.abs().max())
+        eu = float((Hu.vcycle(X) - V64).abs().max() / V64.abs().max())
+        print(f"\nR = {R}: V-cycle error vs FP64, cached {ec:.2e}, per-use {eu:.2e}")
+        assert ec <= 2.0 * eu + 1e-6
+    torch.cuda.synchronize()
+
+
 def test_stacked_apply_and_vcycle_equal_single(lib):
     d, n, p = 2, 8, 3
     op = lib.Operator(d, n, p)
@@ -124,16 +170,18 @@ def test_multi_rhs_without_tensor_cores_and_limits(lib):
     assert e.value.status == lib.EUNSUPPORTED
 
 def test_autotuned_launch_shape_does_not_change_results(lib):
-    """The setup-time autotuner picks the tensor-core apply's CTAs per SM by
-    timing; the apply's result does not depend on it, so two hierarchies that
-    may have tuned differently give bitwise equal solves."""
+    """The setup-time autotuner picks the tensor-core apply's shape by timing
+    (the cached kernel's strip width for 2D b = 16, CTAs per SM of the per-use
+    kernel otherwise); the apply's result does not depend on it, so two
+    hierarchies that may have tuned differently give bitwise equal solves."""
     d, n, p, R = 2, 32, 3, 16
     N, b = n * n, (p + 1) ** 2
     op = lib.Operator(d, n, p)
     H1 = lib.Hierarchy(op, smoother="sai", precision="fp32", max_rhs=R)
     H2 = lib.Hierarchy(op, smoother="sai", precision="fp32", max_rhs=R)
     c1, t1 = H1.tuning
-    assert c1 >= 1 and t1 > 0.0
+    strip, slots, lpr = H1.tc_schedule
+    assert strip in (4, 8, 16) and slots >= 8 and 1.0 <= lpr < 5.0 and t1 > 0.0
     rhs = np.stack([ldg.project_out_constant(random_rhs(N, b, seed=80 + r), d, p, N) for r in range(R)])
     X1, k1, _, s1 = H1.solve(torch.tensor(rhs, device="cuda"))
     X2, k2, _, s2 = H2.solve(torch.tensor(rhs, device="cuda"))

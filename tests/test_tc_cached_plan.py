@@ -1,0 +1,122 @@
+"""The library's schedule of the cached tensor-core apply (ldgmg_host_tc_plan,
+csrc/tc_cached.cu), checked on the CPU against the rules the kernel relies on.
+
+Per CTA the kernel converts x_j into the slot each load names and reads, for
+every stored block, the slot its record names; before it writes the slots of
+row s it waits only for the MMAs of row s - 5.  Replaying the records here
+checks that every block reads a slot holding its column's x_j at that row,
+that a load never overwrites a slot read by one of the 4 rows before it (or by
+its own row), that every row is processed once, and how many x_j loads an apply
+makes per row (the HBM reads of x it costs).
+"""
+import numpy as np
+import pytest
+
+from paper_2412_12506_gb300.inputs import square_mu
+
+LAG = 5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2412_12506_gb300 import ldgmg
+    return ldgmg
+
+
+def replay(plan, row_ptr, col, n):
+    rec = plan["rec"]
+    N = n * n
+    rows = rec[:, 0]
+    assert sorted(rows.tolist()) == list(range(N))
+    ld = plan["ld_elem"]
+    seg = plan["seg"]
+    assert seg[0] == 0 and seg[-1] == N and np.all(np.diff(seg) > 0)
+    S = plan["slots"]
+    loads = 0
+    for c in range(plan["ctas"]):
+        content = [-1] * S
+        last = [-10 ** 9] * S
+        for s in range(seg[c], seg[c + 1]):
+            r = rec[s]
+            row, z0, ld0 = int(r[0]), int(r[1]), int(r[2])
+            nnz, nld = int(r[3]) & 0xFFFF, int(r[3]) >> 16
+            bslot = r[4:8].view(np.uint8)
+            lslot = r[8:12].view(np.uint8)
+            assert z0 == row_ptr[row] and nnz == row_ptr[row + 1] - row_ptr[row]
+            assert nld <= nnz
+            for t in range(nld):
+                sl = int(lslot[t])
+                assert sl < S
+                assert last[sl] <= s - LAG, f"slot {sl} overwritten at row {s}, read at row {last[sl]}"
+                content[sl] = int(ld[ld0 + t])
+            for t in range(nnz):
+                sl = int(bslot[t])
+                assert content[sl] == col[z0 + t], f"row {row} block {t} reads slot {sl}"
+                last[sl] = s
+            loads += nld
+    assert loads == plan["nloads"]
+    return loads / N
+
+
+def strip_order_ok(plan, n):
+    L = plan["strip"]
+    order = []
+    for x0 in range(0, n, L):
+        for y in range(n):
+            order += [x0 + i + n * y for i in range(min(L, n - x0))]
+    return plan["rec"][:, 0].tolist() == order
+
+
+@pytest.mark.parametrize("n,smoother,ell,mu", [(32, "sai", 1, None), (32, "sai", 1, "square"), (16, "sai", 2, None),
+                                               (24, "jacobi", 1, "square")])
+def test_library_schedules_replay_correctly(lib, n, smoother, ell, mu):
+    d, p = 2, 3
+    mu_v = square_mu(d, n, 1e4) if mu else None
+    H = lib.HostHierarchy(d, n, p, mu_v, smoother=smoother, sai_level=ell, nu1=1, nu2=1)
+    mats = [lib.MAT_A, lib.MAT_B, lib.MAT_BT] if smoother == "sai" else [lib.MAT_A, lib.MAT_D]
+    checked = 0
+    for level in range(H.nlevels - 1):
+        nl = H.info(level)["n"]
+        for which in mats:
+            rp, col, _ = H.export(level, which)
+            for strip, ctas in [(8, 152), (4, 7), (16, 1)]:
+                try:
+                    plan = lib.host_tc_plan(nl, rp, col, rcap=64, ctas=ctas, strip=strip)
+                except lib.LdgmgError as e:
+                    assert e.status == lib.EUNSUPPORTED
+                    continue
+                assert strip_order_ok(plan, nl)
+                per_row = replay(plan, rp, col, nl)
+                if which == lib.MAT_D:
+                    assert per_row == 1.0
+                checked += 1
+    assert checked > 0
+
+
+def test_finest_level_reads_x_about_once(lib):
+    """5-point rows in strips of 8: each x_j is loaded (8 + 2) / 8 times per apply
+    plus the cold start of each CTA's range, against 5 reads with one copy per
+    use (and a separate split pass)."""
+    n = 256
+    H = lib.HostHierarchy(2, 16, 3, smoother="jacobi", nu1=1, nu2=1)   # any hierarchy: the pattern below is built here
+    N = n * n
+    e = np.arange(N)
+    x, y = e % n, e // n
+    nb = np.stack([e, (x + 1) % n + n * y, (x - 1) % n + n * y, x + n * ((y + 1) % n), x + n * ((y - 1) % n)], 1)
+    nb.sort(axis=1)
+    rp = np.arange(0, 5 * N + 1, 5, dtype=np.int64)
+    plan = lib.host_tc_plan(n, rp, nb.reshape(-1).astype(np.int32), rcap=64, ctas=152, strip=8)
+    per_row = replay(plan, rp, nb.reshape(-1), n)
+    assert plan["slots"] >= 24
+    assert per_row < 1.35, per_row
+    del H
+
+
+def test_plan_limits(lib):
+    rp = np.array([0, 1], np.int64)
+    with pytest.raises(lib.LdgmgError) as e:
+        lib.host_tc_plan(1, rp, np.zeros(1, np.int32), rcap=65)
+    assert e.value.status == lib.EUNSUPPORTED
+    rp = np.arange(0, 17 * 4 + 1, 17, dtype=np.int64)                 # 17 blocks in a row
+    with pytest.raises(lib.LdgmgError):
+        lib.host_tc_plan(2, rp, np.tile(np.arange(4, dtype=np.int32), 17)[:68], rcap=8)
