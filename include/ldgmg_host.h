@@ -54,8 +54,8 @@ ldgmg_status ldgmg_host_colours(const ldgmg_host_hier* h, int level, int* colour
 
 /* Schedule of the cached tensor-core apply (2D meshes, b = 16) that the
  * library builds for a block pattern (row_ptr: n*n + 1 entries, col), for
- * rcap right-hand sides, storage prec (LDGMG_FP32 or LDGMG_BF16), `ctas` CTAs
- * and strip width `strip`.  info[0..3] = CTAs used, x slots per CTA, strip
+ * rcap right-hand sides, storage prec (LDGMG_FP32 or LDGMG_BF16), `ctas` SMs
+ * (two CTAs each) and strip width `strip`.  info[0..3] = CTAs used, x slots per CTA, strip
  * width, most blocks in a row; *nloads = x_j loads of one apply.  rec (n*n
  * records of 16 int32 in processing order: row, first block, first load,
  * nnz | nld << 16, then 16 bytes of block slots and 16 bytes of load slots,

@@ -22,7 +22,7 @@ inline int col_stride(int b) { return (b + 3) / 4 * 4; }
 // processing order as 32-byte step records, the CTA ranges and the x loads,
 // all device arrays owned by the DevMat that holds it.
 struct TcSched {
-  int G = 0;                // CTAs (one per SM): CTA c takes steps [seg[c], seg[c + 1])
+  int G = 0;                // CTAs (two per SM): CTA c takes steps [seg[c], seg[c + 1])
   int S = 0;                // x slots per CTA
   int L = 0;                // strip width (element columns)
   int kmax = 0;             // most blocks in a row
@@ -99,10 +99,10 @@ int tc_max_ctas_per_sm(int b, int prec, int R);
 cudaError_t bsr_apply_tc(const BatchArgs& a, int b, int prec, cudaStream_t st);
 
 // Cached tensor-core apply (tc_cached.cu; 2D, b = 16, R <= 64, vectors
-// [element][rhs][mode] with es = R b, rs = b): the same arithmetic as
-// bsr_apply_tc without x images; a.ximg and a.ctas_per_sm are not used.
-// tc_sched_plan builds the host schedule for strip width L and G CTAs (or
-// returns why it cannot); the caller uploads it into a TcSched.
+// [element][rhs][mode] with es = R b, rs = b): the products of bsr_apply_tc
+// (plus x_lo A_lo) without x images; a.ximg and a.ctas_per_sm are not used.
+// tc_sched_plan builds the host schedule for strip width L on G SMs (two
+// CTAs each), or returns why it cannot; the caller uploads it into a TcSched.
 struct TcSchedHost {
   int G = 0, S = 0, L = 0, kmax = 0, rcap = 0;
   int64_t nloads = 0;

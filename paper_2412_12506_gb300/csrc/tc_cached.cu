@@ -17,16 +17,33 @@
 //     lo * lo term.
 //   * Rows are processed in strip order: strips of L element columns, each
 //     walked along y, so a row's neighbours x_{i +- 1}, x_{i +- n} were mostly
-//     needed a few rows earlier.  Each CTA (one per SM) takes a contiguous
-//     range of that order.
+//     needed a few rows earlier.
 //   * The CTA keeps S converted x_j in shared-memory slots.  A host-built
 //     schedule says, per row, which x_j to load and convert into which slot
 //     and which slot each block of the row reads; every x_j is read from HBM
 //     about (L + 2) / L times per apply instead of once by a separate split
 //     pass plus once per use.
-//   * FP32 x_j, the row's A_ij images and the rhs / xin row of the fused
-//     epilogue arrive by bulk async copies into rings of stages.
+//   * FP32 x_j and the row's A_ij images arrive by bulk async copies into
+//     rings of stages.  Two CTAs run on each SM (the tensor core overlaps
+//     the MMA streams of different CTAs, not those of one), each taking a
+//     contiguous range of the strip order.
 // The result of a right-hand side does not depend on the others nor on R.
+//
+// Warp roles (two CTAs of 480 threads per SM), hand-offs by mbarriers only;
+// each of the two copy streams runs as far ahead as its own ring allows:
+//   warp 0      copies the row's A blocks with its schedule record;
+//   warp 10     copies the raw x_j of the schedule's loads;
+//   warp 1      issues the MMAs of every row, all blocks of a row into one of
+//               4 TMEM accumulators, and commits the row;
+//   warps 2..5  convert raw x_j into the slot the schedule names, once every
+//               row that last read that slot has completed (the schedule
+//               guarantees that row is at least kLag rows back);
+//   warps 6..9, 11..14  read a finished accumulator and apply the fused
+//               epilogue (reading the rhs / xin row itself, one row ahead),
+//               the first group for even rows, the second for odd.
+// Every wait is bounded; a role that gives up raises the CTA's abort flag,
+// the others leave their waits, the CTA drains its own copies and MMAs
+// (bounded) and exits with the error flag set.
 #include "kernels.h"
 #include "tc_ptx.cuh"
 
@@ -61,25 +78,29 @@ constexpr int kB = 16;                  // block size
 constexpr int kKQ = kB / 8;             // core matrices along K
 constexpr int kMmaM = 128;              // MMA rows: hi and lo parts of 64 right-hand sides
 constexpr uint32_t kSlotBytes = kMmaM * kB * 2;   // one x_j operand: 128 rows of 16 BF16
-constexpr int kNS = 10;                 // A stages = step-done barriers
-constexpr int kNAcc = 6;                // TMEM accumulators (32 columns each)
-constexpr uint32_t kTmemCols = 256;     // allocation: kNAcc * 32 rounded up to a power of two
-constexpr int kLag = 5;                 // the converter writes row s's slots after row s - kLag completes
+// Two CTAs per SM: the tensor core overlaps the MMA streams of different CTAs
+// (one CTA's MMAs into one accumulator run at ~80 cycles each, two CTAs at
+// ~40 per SM), so the rings below are sized to fit two CTAs in shared memory.
+constexpr int kCtasPerSm = 2;
+constexpr int kNS = 5;                  // A stages = step-done barriers (> kNAcc, > kLag)
+constexpr int kNAcc = 4;                // TMEM accumulators, one per row in flight
+constexpr uint32_t kAccCols = 32;       // columns of one accumulator
+constexpr uint32_t kTmemCols = 128;     // kNAcc * kAccCols
+constexpr int kLag = 2;                 // the converter writes row s's slots after row s - kLag completes
 constexpr int kNX = kNS;                // x-ready barriers
-constexpr int kNRaw = 8;                // raw x_j stages
-constexpr int kNRhs = 6;                // rhs / xin row stages
-constexpr int kThreads = 416;
+constexpr int kNRaw = 3;                // raw x_j stages
+constexpr int kThreads = 480;
 constexpr int kConvThreads = 128;
 constexpr int kEpiThreads = 128;
 constexpr uint32_t kRecBytes = 64;
 constexpr uint32_t kRecPad = 128;       // record slot at the end of a stage (keeps stages 128-byte aligned)
-constexpr uint32_t kSmemCap = 227 * 1024;
+constexpr uint32_t kSmemCap = (228 * 1024) / kCtasPerSm - 1024;   // dynamic shared memory per CTA
 constexpr uint32_t kCtrlBytes = 1024;
 constexpr int kMaxBlocksPerRow = 16;
 static_assert(kLag < kNS && kLag < kNX && kNAcc < kNS && kNAcc % 2 == 0,
-              "barrier rings must be deeper than the leads they bound; each issuer keeps its accumulators");
-static_assert(kNAcc * 32 <= int(kTmemCols) && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM allocation");
-static_assert((2 * kNS + kNX + kNAcc + 2 * kNRaw + 2 * kNRhs) * 8 + 8 <= int(kCtrlBytes), "control words");
+              "barrier rings must be deeper than the leads they bound; each epilogue group keeps its accumulators");
+static_assert(kNAcc * kAccCols <= kTmemCols && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM allocation");
+static_assert((2 * kNS + kNX + kNAcc + 2 * kNRaw) * 8 + 8 <= int(kCtrlBytes), "control words");
 
 struct CachedArgs {
   BatchArgs a;
@@ -90,14 +111,14 @@ struct CachedArgs {
   int kmax;               // stage room in blocks
   int need_rhs;           // the epilogue reads a.rhs (M_RES) or a.xin (M_AXPY)
   // shared-memory plan (byte offsets)
-  uint32_t off_a, off_raw, off_rhs, off_ctrl;
-  uint32_t stage_a, stage_rhs, raw_bytes;
+  uint32_t off_a, off_raw, off_ctrl;
+  uint32_t stage_a, raw_bytes;
 };
 
 __device__ __forceinline__ uint32_t parity_of(int64_t use, int ring) { return uint32_t(use / ring) & 1u; }
 
 template <bool SPLIT>
-__global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs ca) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) bsr_tc_cached_kernel(CachedArgs ca) {
   constexpr uint32_t IMG1 = kB * kB * 2;
   constexpr uint32_t IMG = IMG1 * (SPLIT ? 2 : 1);
   // N = 32 for FP32 storage: the block's hi and lo images side by side (the
@@ -114,17 +135,13 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
   auto astage = [&](int k) { return smem + ca.off_a + uint32_t(k) * ca.stage_a; };
   auto arec = [&](int k) { return reinterpret_cast<const TcStep*>(astage(k) + uint32_t(ca.kmax) * IMG); };
   auto raw = [&](int q) { return reinterpret_cast<const float*>(smem + ca.off_raw + uint32_t(q) * ca.raw_bytes); };
-  auto rstage = [&](int r) { return smem + ca.off_rhs + uint32_t(r) * ca.stage_rhs; };
-  auto rrec = [&](int r) { return reinterpret_cast<const TcStep*>(rstage(r) + ca.stage_rhs - kRecPad); };
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + ca.off_ctrl);   // A stage landed
   uint64_t* done = full + kNS;                                         // row's MMAs complete (commit)
   uint64_t* xready = done + kNS;                                       // row's slots written (converters)
   uint64_t* accempty = xready + kNX;                                   // accumulator read (epilogue)
   uint64_t* rawfull = accempty + kNAcc;
   uint64_t* rawempty = rawfull + kNRaw;
-  uint64_t* rhsfull = rawempty + kNRaw;
-  uint64_t* rhsempty = rhsfull + kNRhs;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rhsempty + kNRhs);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(rawempty + kNRaw);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s0 = ca.seg[blockIdx.x], s1 = ca.seg[blockIdx.x + 1];
@@ -142,14 +159,10 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
       mbar_init(done + i, 1);
       mbar_init(xready + i, kConvThreads);
     }
-    for (int i = 0; i < kNAcc; ++i) mbar_init(accempty + i, kEpiThreads);
+    for (int i = 0; i < kNAcc; ++i) mbar_init(accempty + i, kEpiThreads);   // one epilogue group per row
     for (int i = 0; i < kNRaw; ++i) {
       mbar_init(rawfull + i, 1);
       mbar_init(rawempty + i, kConvThreads);
-    }
-    for (int i = 0; i < kNRhs; ++i) {
-      mbar_init(rhsfull + i, 1);
-      mbar_init(rhsempty + i, kEpiThreads);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -208,35 +221,6 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
       };
       drain(full, kNS, nA);
     }
-  } else if (warp == 11) {
-    // ---- rhs copier: the epilogue's rhs / xin row and the step record
-    int64_t nRh = 0;
-    bool ok = true;
-    int wb = s0 - 64, rowv = 0;          // lane l: row of step wb + l
-    for (int s = s0; s < s1; ++s) {
-      const int i = s - s0, rs = i % kNRhs;
-      if (s - wb >= 32) {
-        wb = s;
-        rowv = s + lane < s1 ? ca.rec[s + lane].row : 0;
-      }
-      const int row = __shfl_sync(0xffffffffu, rowv, s - wb);
-      bool w = true;
-      if (lane == 0 && i >= kNRhs) w = wait_or_abort(rhsempty + rs, parity_of(i - kNRhs, kNRhs), abort_flag, a.err);
-      if (!__shfl_sync(0xffffffffu, w ? 1 : 0, 0)) { ok = false; break; }
-      if (lane == 0) {
-        mbar_arrive_expect_tx(rhsfull + rs, (ca.need_rhs ? xrow_bytes : 0u) + kRecBytes);
-        if (ca.need_rhs) {
-          const float* v = a.mode == M_RES ? a.rhs : a.xin;
-          bulk_g2s(rstage(rs), v + int64_t(row) * a.es, xrow_bytes, rhsfull + rs);
-        }
-        bulk_g2s(rstage(rs) + ca.stage_rhs - kRecPad, ca.rec + s, kRecBytes, rhsfull + rs);
-      }
-      ++nRh;
-    }
-    __syncwarp();
-    if (lane == 0 && (!ok || *abort_flag))
-      for (int e = 0; e < kNRhs && e < nRh; ++e)
-        mbar_wait_bounded(rhsfull + e, parity_of(e + kNRhs * ((nRh - 1 - e) / kNRhs), kNRhs));
   } else if (warp == 10) {
     // ---- raw x copier: the CTA's loads in schedule order into the raw ring
     const int kbeg = nsteps > 0 ? ca.rec[s0].ld0 : 0;
@@ -265,21 +249,23 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
     if (lane == 0 && (!ok || *abort_flag))
       for (int e = 0; e < kNRaw && e < nraw; ++e)
         mbar_wait_bounded(rawfull + e, parity_of(e + kNRaw * ((nraw - 1 - e) / kNRaw), kNRaw));
-  } else if (warp == 1 || warp == 12) {
-    // ---- MMA issuers: warp 1 takes the even rows, warp 12 the odd ones (one
-    // issuing thread is latency bound on its own instruction stream).  The
-    // descriptors of slot 0 / stage block 0 are built once; a slot or block
-    // offset is a multiple of 16 bytes added to the address field.
-    const int par = warp == 1 ? 0 : 1;
+  } else if (warp == 1) {
+    // ---- MMA issuer.  One thread issues every row, all blocks of a row into
+    // one accumulator: consecutive MMAs into the same accumulator run at about
+    // a third of the cost of MMAs that switch accumulators (measured), so the
+    // rows are not interleaved.  The descriptors of slot 0 / stage block 0
+    // are built once; a slot or block offset is a multiple of 16 bytes added
+    // to the address field.
     bool ok = true;
     int last_done = -1;
     if (lane == 0) {
       const uint64_t dx = make_sdesc(smem_u32(xs), 128u, SBO);
       constexpr uint64_t sunit = kSlotBytes >> 4;
-      for (int i = par; i < nsteps; i += 2) {
+      for (int i = 0; i < nsteps; ++i) {
         const int ks = i % kNS, acc = i % kNAcc;
+        // x-ready of row i implies its A stage has landed: the converters
+        // waited for that stage (the record) before they arrived
         if (!wait_or_abort(xready + (i % kNX), parity_of(i, kNX), abort_flag, a.err) ||
-            !wait_or_abort(full + ks, parity_of(i, kNS), abort_flag, a.err) ||
             (i >= kNAcc && !wait_or_abort(accempty + acc, parity_of(i - kNAcc, kNAcc), abort_flag, a.err))) {
           ok = false;
           break;
@@ -289,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
         const int nnz = rc->nnz;
         const uint4 sw = *reinterpret_cast<const uint4*>(rc->slot);
         const uint32_t words[4] = {sw.x, sw.y, sw.z, sw.w};
-        const uint32_t d = tmem + uint32_t(acc) * 32u;
+        const uint32_t d = tmem + uint32_t(acc) * kAccCols;
         const uint64_t da = make_sdesc(smem_u32(astage(ks)), 128u, SBO);
         // one MMA per block: [x hi; x lo] (128 rows) times [A hi | A lo]^T
 #pragma unroll
@@ -306,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
       if (!ok && last_done >= 0) mbar_wait_bounded(done + (last_done % kNS), parity_of(last_done, kNS));
     }
     __syncwarp();
-  } else if (warp < 6) {
+  } else if (warp >= 2 && warp < 6) {
     // ---- converters: raw FP32 x_j -> BF16 hi / lo operand images in its slot
     const int ct = tid - 64;
     int64_t nraw = 0;
@@ -358,33 +344,66 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
       mbar_arrive(xready + (i % kNX));
     }
   } else {
-    // ---- epilogue (warps 6..9): warp w reads TMEM lanes 32 * (w % 4) .. + 31.
-    // Lane rho holds the hi (rho % 8 < 4) or lo part of right-hand side
-    // 4 (rho / 8) + rho % 4 in columns 0..15 (times A hi) and, for FP32
-    // storage, 16..31 (times A lo); lanes rho and rho ^ 4 add up.
+    // ---- epilogue: warps 6..9 take the even rows, warps 11..14 the odd ones;
+    // warp w reads TMEM lanes 32 * (w % 4) .. + 31.  Lane rho holds the hi
+    // (rho % 8 < 4) or lo part of right-hand side 4 (rho / 8) + rho % 4 in 32
+    // columns: 0..15 times A hi, 16..31 (FP32 storage) times A lo.  The two
+    // halves add up in the lane, then lanes rho and rho ^ 4.  The rows'
+    // records are read a warp window at a time; the rhs / xin row of the
+    // group's next row is loaded while the current one is finished.
     const int quad = warp & 3;
     const int rho = quad * 32 + lane;
     const int m = 4 * (rho >> 3) + (rho & 3);  // this lane's right-hand side
-    const bool writer = (rho & 4) == 0;
+    const bool writer = (rho & 4) == 0 && m < R;
+    const int egrp = warp < 10 ? 0 : 1;
     const float sc = float(a.s);
-    for (int i = 0; i < nsteps; ++i) {
-      const int rs = i % kNRhs, ks = i % kNS, acc = i % kNAcc;
-      const bool w1 = wait_or_abort(rhsfull + rs, parity_of(i, kNRhs), abort_flag, a.err);
-      const bool w2 = w1 && wait_or_abort(done + ks, parity_of(i, kNS), abort_flag, a.err);
-      if (__any_sync(0xffffffffu, !w2)) break;
+    const bool need = ca.need_rhs != 0;
+    const float* vsrc = a.mode == M_RES ? a.rhs : a.xin;
+    uint32_t wrow = 0, wcnt = 0;               // lane l: row and counts of the group's row kb + l
+    int kb = -64;
+    auto rec_of = [&](int k, int& row, int& nnz) {      // warp-uniform
+      if (k - kb >= 32) {
+        kb = k;
+        const int t = egrp + 2 * (k + lane);
+        if (t < nsteps) {
+          const uint4 v = *reinterpret_cast<const uint4*>(ca.rec + s0 + t);
+          wrow = v.x;
+          wcnt = v.w;
+        }
+      }
+      row = int(__shfl_sync(0xffffffffu, wrow, k - kb));
+      nnz = int(__shfl_sync(0xffffffffu, wcnt, k - kb) & 0xFFFFu);
+    };
+    auto load_row = [&](int row, float4* dst) {
+      const float4* src = reinterpret_cast<const float4*>(vsrc + int64_t(row) * a.es + int64_t(m) * a.rs);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = src[q];
+    };
+    float4 cur[4], nxt[4];
+    int row_c = 0, nnz_c = 0;
+    if (egrp < nsteps) {
+      rec_of(0, row_c, nnz_c);
+      if (need && writer) load_row(row_c, cur);
+    }
+    for (int i = egrp, k = 0; i < nsteps; i += 2, ++k) {
+      const int ks = i % kNS, acc = i % kNAcc;
+      int row_n = 0, nnz_n = 0;
+      if (i + 2 < nsteps) {
+        rec_of(k + 1, row_n, nnz_n);
+        if (need && writer) load_row(row_n, nxt);
+      }
+      const bool w = wait_or_abort(done + ks, parity_of(i, kNS), abort_flag, a.err);
+      if (__any_sync(0xffffffffu, !w)) break;
       tc_fence_after();
-      const TcStep* rc = rrec(rs);
-      const int64_t row = rc->row;
-      const bool empty_row = rc->nnz == 0;
       float v[16];
-      if (!empty_row) {
-        const uint32_t ta = tmem + (uint32_t(quad * 32) << 16) + uint32_t(acc) * 32u;
+      if (nnz_c > 0) {
+        const uint32_t ta = tmem + (uint32_t(quad * 32) << 16) + uint32_t(acc) * kAccCols;
         tmem_ld16(ta, v);
         if (SPLIT) {
-          float w[16];
-          tmem_ld16(ta + 16u, w);
+          float w2[16];
+          tmem_ld16(ta + 16u, w2);
 #pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] += w[e];
+          for (int e = 0; e < 16; ++e) v[e] += w2[e];
         }
       } else {
 #pragma unroll
@@ -392,27 +411,29 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
       }
 #pragma unroll
       for (int e = 0; e < 16; ++e) v[e] += __shfl_xor_sync(0xffffffffu, v[e], 4);
-      if (writer && m < R) {
-        const int64_t o = row * a.es + int64_t(m) * a.rs;
-        const float* rr = reinterpret_cast<const float*>(rstage(rs)) + m * kB;
+      if (writer) {
+        float4* yo = reinterpret_cast<float4*>(a.y + int64_t(row_c) * a.es + int64_t(m) * a.rs);
 #pragma unroll
-        for (int q = 0; q < 16; q += 4) {
-          float4 y = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+        for (int q = 0; q < 4; ++q) {
+          float4 y = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
           if (a.mode == M_RES) {
-            const float4 r4 = *reinterpret_cast<const float4*>(rr + q);
+            const float4 r4 = cur[q];
             y = make_float4(r4.x - y.x, r4.y - y.y, r4.z - y.z, r4.w - y.w);
           } else if (a.mode == M_AXPY) {
-            const float4 xi = *reinterpret_cast<const float4*>(rr + q);
+            const float4 xi = cur[q];
             y = make_float4(xi.x + sc * y.x, xi.y + sc * y.y, xi.z + sc * y.z, xi.w + sc * y.w);
           } else if (a.mode != M_Y) {
             y = make_float4(sc * y.x, sc * y.y, sc * y.z, sc * y.w);
           }
-          *reinterpret_cast<float4*>(a.y + o + q) = y;
+          yo[q] = y;
         }
       }
       tc_fence_before();
       mbar_arrive(accempty + acc);
-      mbar_arrive(rhsempty + rs);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+      row_c = row_n;
+      nnz_c = nnz_n;
     }
   }
 
@@ -429,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1) bsr_tc_cached_kernel(CachedArgs c
 // Shared-memory plan of one CTA for R right-hand sides, kmax blocks per row
 // and S x slots (byte offsets into the dynamic shared memory).
 struct CachedPlan {
-  uint32_t off_a, stage_a, off_raw, raw_bytes, off_rhs, stage_rhs, off_ctrl, total;
+  uint32_t off_a, stage_a, off_raw, raw_bytes, off_ctrl, total;
 };
 
 CachedPlan cached_plan(int R, int kmax, bool split, int S) {
@@ -440,9 +461,7 @@ CachedPlan cached_plan(int R, int kmax, bool split, int S) {
   p.stage_a = uint32_t(kmax) * img + kRecPad;
   p.off_raw = p.off_a + kNS * p.stage_a;
   p.raw_bytes = up(uint32_t(R) * kB * 4);
-  p.off_rhs = p.off_raw + kNRaw * p.raw_bytes;
-  p.stage_rhs = up(uint32_t(R) * kB * 4) + kRecPad;
-  p.off_ctrl = p.off_rhs + kNRhs * p.stage_rhs;
+  p.off_ctrl = p.off_raw + kNRaw * p.raw_bytes;
   p.total = p.off_ctrl + kCtrlBytes;
   return p;
 }
@@ -450,7 +469,7 @@ CachedPlan cached_plan(int R, int kmax, bool split, int S) {
 // most x slots that fit for (R, kmax)
 int cached_slots(int R, int kmax, bool split) {
   int S = 0;
-  while (S < 255 && cached_plan(R, kmax, split, S + 1).total <= kSmemCap - 1024) ++S;
+  while (S < 255 && cached_plan(R, kmax, split, S + 1).total <= kSmemCap) ++S;
   return S;
 }
 
@@ -460,7 +479,7 @@ cudaError_t launch_cached(const CachedArgs& ca, uint32_t smem, int grid, cudaStr
   static cudaError_t cfg = cudaSuccess;
   std::call_once(once, [] {
     cfg = cudaFuncSetAttribute(bsr_tc_cached_kernel<SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               int(kSmemCap - 1024));
+                               int(kSmemCap));
   });
   if (cfg != cudaSuccess) return cfg;
   bsr_tc_cached_kernel<SPLIT><<<unsigned(grid), kThreads, smem, st>>>(ca);
@@ -497,7 +516,7 @@ std::string tc_sched_plan(int dim, int n, int64_t nrows, const int64_t* row_ptr,
     for (int y = 0; y < n; ++y)
       for (int i = 0; i < w; ++i) order.push_back(int32_t(x0 + i + int64_t(n) * y));
   }
-  const int g = int(std::max<int64_t>(1, std::min<int64_t>(G, nrows / 8)));
+  const int g = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(G) * kCtasPerSm, nrows / 8)));
   out->G = g;
   out->S = S;
   out->L = L;
@@ -597,7 +616,7 @@ cudaError_t bsr_apply_tc_cached(const BatchArgs& a, const TcSched& sc, int prec,
   if (!split && prec != P_BF16) return cudaErrorInvalidValue;
   if (a.nrows == 0) return cudaSuccess;
   const CachedPlan p = cached_plan(a.R, sc.kmax, split, sc.S);
-  if (p.total > kSmemCap - 1024) return cudaErrorInvalidValue;
+  if (p.total > kSmemCap) return cudaErrorInvalidValue;
   CachedArgs ca;
   ca.a = a;
   ca.rec = static_cast<const TcStep*>(sc.rec);
@@ -608,10 +627,8 @@ cudaError_t bsr_apply_tc_cached(const BatchArgs& a, const TcSched& sc, int prec,
   ca.need_rhs = (a.mode == M_RES || a.mode == M_AXPY) ? 1 : 0;
   ca.off_a = p.off_a;
   ca.off_raw = p.off_raw;
-  ca.off_rhs = p.off_rhs;
   ca.off_ctrl = p.off_ctrl;
   ca.stage_a = p.stage_a;
-  ca.stage_rhs = p.stage_rhs;
   ca.raw_bytes = p.raw_bytes;
   return split ? launch_cached<true>(ca, p.total, sc.G, st) : launch_cached<false>(ca, p.total, sc.G, st);
 }

@@ -106,6 +106,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// non-blocking test of an mbarrier phase (no suspend: the fast path of the
+// waits below when the phase has already completed)
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // bounded wait on an mbarrier phase; returns false if it gave up
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   unsigned spins = 0;
@@ -117,6 +131,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // bounded wait that also gives up as soon as another role of the CTA has;
 // giving up raises the CTA's abort flag and the caller-visible error flag
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err) {
+  if (mbar_test_wait(bar, parity)) return true;
   unsigned spins = 0;
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;

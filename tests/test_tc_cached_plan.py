@@ -3,9 +3,9 @@ csrc/tc_cached.cu), checked on the CPU against the rules the kernel relies on.
 
 Per CTA the kernel converts x_j into the slot each load names and reads, for
 every stored block, the slot its record names; before it writes the slots of
-row s it waits only for the MMAs of row s - 5.  Replaying the records here
+row s it waits only for the MMAs of row s - 2.  Replaying the records here
 checks that every block reads a slot holding its column's x_j at that row,
-that a load never overwrites a slot read by one of the 4 rows before it (or by
+that a load never overwrites a slot read by one of the row before it (or by
 its own row), that every row is processed once, and how many x_j loads an apply
 makes per row (the HBM reads of x it costs).
 """
@@ -14,7 +14,7 @@ import pytest
 
 from paper_2412_12506_gb300.inputs import square_mu
 
-LAG = 5
+LAG = 2
 
 
 @pytest.fixture(scope="module")
@@ -94,9 +94,10 @@ def test_library_schedules_replay_correctly(lib, n, smoother, ell, mu):
 
 
 def test_finest_level_reads_x_about_once(lib):
-    """5-point rows in strips of 8: each x_j is loaded (8 + 2) / 8 times per apply
-    plus the cold start of each CTA's range, against 5 reads with one copy per
-    use (and a separate split pass)."""
+    """5-point rows in strips of 8: each x_j is loaded about (8 + 2) / 8 times per
+    apply plus the cold start of each CTA's range (and reloads a 16-slot cache
+    cannot avoid), against 5 reads with one copy per use and a separate split
+    pass."""
     n = 256
     H = lib.HostHierarchy(2, 16, 3, smoother="jacobi", nu1=1, nu2=1)   # any hierarchy: the pattern below is built here
     N = n * n
@@ -107,8 +108,8 @@ def test_finest_level_reads_x_about_once(lib):
     rp = np.arange(0, 5 * N + 1, 5, dtype=np.int64)
     plan = lib.host_tc_plan(n, rp, nb.reshape(-1).astype(np.int32), rcap=64, ctas=152, strip=8)
     per_row = replay(plan, rp, nb.reshape(-1), n)
-    assert plan["slots"] >= 24
-    assert per_row < 1.35, per_row
+    assert plan["slots"] >= 16
+    assert per_row < 1.6, per_row
     del H
 
 

@@ -1,23 +1,23 @@
 """The hand-off protocol of the cached tensor-core apply (csrc/tc_cached.cu),
 modelled on the CPU.
 
-Seven roles share rings of stages and hand work on through mbarriers waited
-on by phase parity: three copiers, each as far ahead as its own ring allows
-(A stage with the step record; the schedule's raw x_j loads; the epilogue's
-rhs row with the record), two MMA issuers (even and odd rows; one commit per
-row into the step-done ring; six TMEM accumulators; each issuer's MMAs
-complete in its issue order), the converters (raw x_j -> the schedule's slot
+Six roles share rings of stages and hand work on through mbarriers waited
+on by phase parity: two copiers, each as far ahead as its own ring allows
+(A stage with the step record; the schedule's raw x_j loads), the MMA issuer
+(one commit per row into the step-done ring; four TMEM accumulators; MMAs
+complete in issue order), the converters (raw x_j -> the schedule's slot
 once every row up to LAG back has completed -- it waits for row i - LAG at
-row i, so the waits of earlier rows cover the rest; one arrival of all 128 threads per row) and the
-epilogue.  The schedule is planned here by the rule the library's planner
-enforces (a load takes a free slot, else the slot needed again furthest
-ahead among those whose last reader is at least LAG rows back).  The model
-replays the kernel's per-role waits, arrivals and commits under random
-interleavings, with bulk copies landing and MMAs completing at random later
-times, and checks: no deadlock; every parity wait unambiguous; an MMA reads
-slots that hold the x_j its blocks need, an A stage holding its own row; no
-slot, raw, A or rhs stage overwritten while a reader may still use it; the
-epilogue reads finished products from an accumulator not yet reused.
+row i, so the waits of earlier rows cover the rest; one arrival of all 128
+threads per row) and two epilogue groups (even and odd rows).  The schedule
+is planned here by the rule the library's planner enforces (a load takes a
+free slot, else the slot needed again furthest ahead among those whose last
+reader is at least LAG rows back).  The model replays the kernel's per-role
+waits, arrivals and commits under random interleavings, with bulk copies
+landing and MMAs completing at random later times, and checks: no deadlock;
+every parity wait unambiguous; an MMA reads slots that hold the x_j its
+blocks need, an A stage holding its own row; no slot, raw or A stage
+overwritten while a reader may still use it; the epilogue reads finished
+products from an accumulator not yet reused.
 """
 import random
 
@@ -25,7 +25,7 @@ import pytest
 
 from test_tc_pipeline_protocol import Barrier
 
-NS, NACC, LAG, NX, NRAW, NRHS = 10, 6, 5, 10, 8, 6
+NS, NACC, LAG, NX, NRAW = 5, 4, 2, 5, 3
 
 
 def plan(rows, S):
@@ -77,11 +77,8 @@ def simulate(rows, S, seed, drop=None):
     accempty = [Barrier(128) for _ in range(NACC)]
     rawfull = [Barrier(1) for _ in range(NRAW)]
     rawempty = [Barrier(128) for _ in range(NRAW)]
-    rhsfull = [Barrier(1) for _ in range(NRHS)]
-    rhsempty = [Barrier(128) for _ in range(NRHS)]
     astage = [None] * NS        # step whose A blocks / record a stage holds
     rawst = [None] * NRAW       # load index a raw stage holds
-    rhsst = [None] * NRHS
     slot = [None] * S           # element a slot holds
     pending = {0: [], 1: []}    # per issuer: issued rows whose MMAs have not completed, in order
     row_slots = {}              # row -> slots its MMAs read
@@ -115,19 +112,11 @@ def simulate(rows, S, seed, drop=None):
             copies.append(("a", ks, i, full[ks]))
             yield
 
-    def rhs_copier():
+    def mma():
         for i in range(n):
-            rs = i % NRHS
-            if i >= NRHS and drop != "copier_rhsempty":
-                yield from wait(rhsempty[rs], i // NRHS - 1)
-            rhsfull[rs].arrive_expect_tx(1)
-            copies.append(("rhs", rs, i, rhsfull[rs]))
-
-    def mma(par):
-        for i in range(par, n, 2):
             ks, acc = i % NS, i % NACC
             yield from wait(xready[i % NX], i // NX)
-            yield from wait(full[ks], i // NS)
+            # no wait for the A stage: the converters waited for it before x-ready
             if i >= NACC and drop != "mma_accempty":
                 yield from wait(accempty[acc], i // NACC - 1)
             assert astage[ks] == i, "MMA sees another row's A stage"
@@ -137,7 +126,7 @@ def simulate(rows, S, seed, drop=None):
             for j, sl in zip(rows[i], sched[i][1]):
                 assert slot[sl] == j, f"row {i} reads slot {sl} holding {slot[sl]}, needs {j}"
             row_slots[i] = set(sched[i][1])
-            pending[par].append(i)
+            pending[0].append(i)
 
     def converter():
         nraw = 0
@@ -161,21 +150,19 @@ def simulate(rows, S, seed, drop=None):
                 nraw += 1
             xready[i % NX].arrive(128)
 
-    def epilogue():
-        for i in range(n):
-            rs, ks, acc = i % NRHS, i % NS, i % NACC
-            yield from wait(rhsfull[rs], i // NRHS)
+    def epilogue(par):
+        for i in range(par, n, 2):
+            ks, acc = i % NS, i % NACC
             yield from wait(done[ks], i // NS)
             assert i in done_rows, "epilogue before its row's MMAs completed"
-            assert rhsst[rs] == i and acc_owner[acc] == i
+            assert acc_owner[acc] == i
             epi_done.add(i)
             accempty[acc].arrive(128)
-            rhsempty[rs].arrive(128)
 
-    roles = [copier(), mma(0), mma(1), converter(), epilogue(), raw_copier(), rhs_copier()]
-    alive = [True] * 7
+    roles = [copier(), mma(), converter(), epilogue(0), epilogue(1), raw_copier()]
+    alive = [True] * 6
     for _ in range(10 ** 6):
-        choices = [r for r in range(7) if alive[r]]
+        choices = [r for r in range(6) if alive[r]]
         if copies:
             choices.append("copy")
         for q in (0, 1):
@@ -188,10 +175,8 @@ def simulate(rows, S, seed, drop=None):
             kind, idx, val, bar = copies.pop(rnd.randrange(len(copies)))
             if kind == "a":
                 astage[idx] = val
-            elif kind == "raw":
-                rawst[idx] = val
             else:
-                rhsst[idx] = val
+                rawst[idx] = val
             bar.complete_tx(1)
         elif isinstance(c, tuple):
             r = pending[c[1]].pop(0)        # each issuer's MMAs complete in issue order
@@ -226,7 +211,7 @@ def strip_rows(n, L, extra=0, rnd=None):
     return rows
 
 
-@pytest.mark.parametrize("n,L,S", [(16, 4, 24), (16, 8, 33), (12, 8, 33), (8, 16, 33), (4, 4, 16), (2, 2, 8),
+@pytest.mark.parametrize("n,L,S", [(16, 4, 16), (16, 8, 33), (12, 8, 16), (8, 16, 33), (4, 4, 16), (2, 2, 8),
                                    (16, 8, 20)])
 def test_strip_schedules(n, L, S):
     planned = 0
@@ -248,12 +233,12 @@ def test_rows_with_extra_couplings_and_empty_rows():
 
 
 def test_plan_refuses_a_ring_too_small_for_the_lag():
-    """Six rows of five blocks need up to 5 + 5 * 3 slots at once."""
-    assert plan(strip_rows(16, 8), 12) is None
+    """Three rows of five blocks need up to 5 + 2 * 3 slots at once."""
+    assert plan(strip_rows(16, 8), 6) is None
     assert plan(strip_rows(16, 8), 33) is not None
 
 
-@pytest.mark.parametrize("drop", ["copier_done", "copier_rhsempty", "mma_accempty", "conv_lag", "raw_empty"])
+@pytest.mark.parametrize("drop", ["copier_done", "mma_accempty", "conv_lag", "raw_empty"])
 def test_model_catches_a_dropped_wait(drop):
     """Leaving out any reuse wait is caught on some schedule (the checks are
     not vacuous)."""
@@ -261,7 +246,7 @@ def test_model_catches_a_dropped_wait(drop):
     rows = strip_rows(8, 4)
     for seed in range(150):
         try:
-            simulate(rows, 18 if drop == "conv_lag" else 33, seed, drop=drop)
+            simulate(rows, 10 if drop == "conv_lag" else 33, seed, drop=drop)
         except AssertionError:
             caught += 1
     assert caught > 0
