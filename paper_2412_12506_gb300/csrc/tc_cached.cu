@@ -34,7 +34,7 @@
 //   warp 0      copies the row's A blocks with its schedule record;
 //   warp 10     copies the raw x_j of the schedule's loads;
 //   warp 1      issues the MMAs of every row, all blocks of a row into one of
-//               4 TMEM accumulators, and commits the row;
+//               8 TMEM accumulators, and commits the row;
 //   warps 2..5  convert raw x_j into the slot the schedule names, once every
 //               row that last read that slot has completed (the schedule
 //               guarantees that row is at least kLag rows back);
@@ -82,12 +82,13 @@ constexpr uint32_t kSlotBytes = kMmaM * kB * 2;   // one x_j operand: 128 rows o
 // (one CTA's MMAs into one accumulator run at ~80 cycles each, two CTAs at
 // ~40 per SM), so the rings below are sized to fit two CTAs in shared memory.
 constexpr int kCtasPerSm = 2;
-constexpr int kNS = 5;                  // A stages = step-done barriers (> kNAcc, > kLag)
-constexpr int kNAcc = 4;                // TMEM accumulators, one per row in flight
+constexpr int kNS = 5;                  // A stages (shared memory)
+constexpr int kND = 16;                 // step-done barriers (> kNAcc, > kLag, >= kNS)
+constexpr int kNAcc = 8;                // TMEM accumulators, one per row in flight
 constexpr uint32_t kAccCols = 32;       // columns of one accumulator
-constexpr uint32_t kTmemCols = 128;     // kNAcc * kAccCols
+constexpr uint32_t kTmemCols = 256;     // kNAcc * kAccCols (two CTAs: the whole TMEM)
 constexpr int kLag = 2;                 // the converter writes row s's slots after row s - kLag completes
-constexpr int kNX = kNS;                // x-ready barriers
+constexpr int kNX = kND;                // x-ready barriers
 constexpr int kNRaw = 3;                // raw x_j stages
 constexpr int kThreads = 480;
 constexpr int kConvThreads = 128;
@@ -97,10 +98,10 @@ constexpr uint32_t kRecPad = 128;       // record slot at the end of a stage (ke
 constexpr uint32_t kSmemCap = (228 * 1024) / kCtasPerSm - 1024;   // dynamic shared memory per CTA
 constexpr uint32_t kCtrlBytes = 1024;
 constexpr int kMaxBlocksPerRow = 16;
-static_assert(kLag < kNS && kLag < kNX && kNAcc < kNS && kNAcc % 2 == 0,
+static_assert(kLag < kND && kLag < kNX && kNAcc < kND && kNS <= kND && kNAcc % 2 == 0,
               "barrier rings must be deeper than the leads they bound; each epilogue group keeps its accumulators");
 static_assert(kNAcc * kAccCols <= kTmemCols && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM allocation");
-static_assert((2 * kNS + kNX + kNAcc + 2 * kNRaw) * 8 + 8 <= int(kCtrlBytes), "control words");
+static_assert((kNS + kND + kNX + kNAcc + 2 * kNRaw) * 8 + 8 <= int(kCtrlBytes), "control words");
 
 struct CachedArgs {
   BatchArgs a;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) bsr_tc_cached_kernel(Cac
   auto raw = [&](int q) { return reinterpret_cast<const float*>(smem + ca.off_raw + uint32_t(q) * ca.raw_bytes); };
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + ca.off_ctrl);   // A stage landed
   uint64_t* done = full + kNS;                                         // row's MMAs complete (commit)
-  uint64_t* xready = done + kNS;                                       // row's slots written (converters)
+  uint64_t* xready = done + kND;                                       // row's slots written (converters)
   uint64_t* accempty = xready + kNX;                                   // accumulator read (epilogue)
   uint64_t* rawfull = accempty + kNAcc;
   uint64_t* rawempty = rawfull + kNRaw;
@@ -154,8 +155,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) bsr_tc_cached_kernel(Cac
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int i = 0; i < kNS; ++i) {
-      mbar_init(full + i, 1);
+    for (int i = 0; i < kNS; ++i) mbar_init(full + i, 1);
+    for (int i = 0; i < kND; ++i) {
       mbar_init(done + i, 1);
       mbar_init(xready + i, kConvThreads);
     }
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) bsr_tc_cached_kernel(Cac
       // the row's A_ij images and its record (the record also tells the
       // converters which loads precede the row)
       const int ks = i % kNS;
-      if (i >= kNS && !wait0(done + ks, parity_of(i - kNS, kNS))) { ok = false; break; }
+      if (i >= kNS && !wait0(done + ((i - kNS) % kND), parity_of(i - kNS, kND))) { ok = false; break; }
       if (lane == 0) {
         mbar_arrive_expect_tx(full + ks, uint32_t(nnz) * IMG + kRecBytes);
         if (nnz > 0)
@@ -285,11 +286,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) bsr_tc_cached_kernel(Cac
             mma_bf16(d, dx + sl * sunit, da + uint64_t(t) * (IMG >> 4), IDESC, t > 0 ? 1u : 0u);
           }
         }
-        mma_commit(done + ks);
+        mma_commit(done + (i % kND));
         last_done = i;
       }
       // after giving up: bounded wait for the MMAs already issued (the last commit covers them)
-      if (!ok && last_done >= 0) mbar_wait_bounded(done + (last_done % kNS), parity_of(last_done, kNS));
+      if (!ok && last_done >= 0) mbar_wait_bounded(done + (last_done % kND), parity_of(last_done, kND));
     }
     __syncwarp();
   } else if (warp >= 2 && warp < 6) {
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) bsr_tc_cached_kernel(Cac
       const int nld = rc->nld;
       // every row <= i - kLag has completed: this wait covers row i - kLag, the
       // waits of the earlier rows cover the rows before it (whichever issuer)
-      if (i >= kLag && !wait_or_abort(done + ((i - kLag) % kNS), parity_of(i - kLag, kNS), abort_flag, a.err)) break;
+      if (i >= kLag && !wait_or_abort(done + ((i - kLag) % kND), parity_of(i - kLag, kND), abort_flag, a.err)) break;
       bool ok = true;
       for (int t = 0; t < nld; ++t) {
         const int q = int(nraw % kNRaw);
@@ -386,13 +387,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) bsr_tc_cached_kernel(Cac
       if (need && writer) load_row(row_c, cur);
     }
     for (int i = egrp, k = 0; i < nsteps; i += 2, ++k) {
-      const int ks = i % kNS, acc = i % kNAcc;
+      const int kd = i % kND, acc = i % kNAcc;
       int row_n = 0, nnz_n = 0;
       if (i + 2 < nsteps) {
         rec_of(k + 1, row_n, nnz_n);
         if (need && writer) load_row(row_n, nxt);
       }
-      const bool w = wait_or_abort(done + ks, parity_of(i, kNS), abort_flag, a.err);
+      const bool w = wait_or_abort(done + kd, parity_of(i, kND), abort_flag, a.err);
       if (__any_sync(0xffffffffu, !w)) break;
       tc_fence_after();
       float v[16];

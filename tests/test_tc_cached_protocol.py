@@ -4,7 +4,7 @@ modelled on the CPU.
 Six roles share rings of stages and hand work on through mbarriers waited
 on by phase parity: two copiers, each as far ahead as its own ring allows
 (A stage with the step record; the schedule's raw x_j loads), the MMA issuer
-(one commit per row into the step-done ring; four TMEM accumulators; MMAs
+(one commit per row into the step-done ring; eight TMEM accumulators; MMAs
 complete in issue order), the converters (raw x_j -> the schedule's slot
 once every row up to LAG back has completed -- it waits for row i - LAG at
 row i, so the waits of earlier rows cover the rest; one arrival of all 128
@@ -25,7 +25,8 @@ import pytest
 
 from test_tc_pipeline_protocol import Barrier
 
-NS, NACC, LAG, NX, NRAW = 5, 4, 2, 5, 3
+NS, ND, NACC, LAG, NRAW = 5, 16, 8, 2, 3
+NX = ND
 
 
 def plan(rows, S):
@@ -65,14 +66,14 @@ def plan(rows, S):
     return out
 
 
-def simulate(rows, S, seed, drop=None):
+def simulate(rows, S, seed, drop=None, slow_epilogue=False):
     sched = plan(rows, S)
     if sched is None:
         return False
     rnd = random.Random(seed)
     n = len(rows)
     full = [Barrier(1) for _ in range(NS)]
-    done = [Barrier(1) for _ in range(NS)]
+    done = [Barrier(1) for _ in range(ND)]
     xready = [Barrier(128) for _ in range(NX)]
     accempty = [Barrier(128) for _ in range(NACC)]
     rawfull = [Barrier(1) for _ in range(NRAW)]
@@ -105,7 +106,7 @@ def simulate(rows, S, seed, drop=None):
         for i in range(n):
             ks = i % NS
             if i >= NS and drop != "copier_done":
-                yield from wait(done[ks], i // NS - 1)
+                yield from wait(done[(i - NS) % ND], (i - NS) // ND)
             if i >= NS:
                 assert (i - NS) in done_rows, "A stage overwritten while an MMA may read it"
             full[ks].arrive_expect_tx(1)
@@ -135,7 +136,7 @@ def simulate(rows, S, seed, drop=None):
             yield from wait(full[ks], i // NS)
             assert astage[ks] == i
             if i >= LAG and drop != "conv_lag":
-                yield from wait(done[(i - LAG) % NS], (i - LAG) // NS)
+                yield from wait(done[(i - LAG) % ND], (i - LAG) // ND)
             # the invariant the planner relies on: every row <= i - LAG has completed
             assert all(r in done_rows for r in range(max(0, i - LAG - 3), i - LAG + 1)), \
                 f"row {i}'s slots written before the rows up to {i - LAG} completed"
@@ -152,8 +153,8 @@ def simulate(rows, S, seed, drop=None):
 
     def epilogue(par):
         for i in range(par, n, 2):
-            ks, acc = i % NS, i % NACC
-            yield from wait(done[ks], i // NS)
+            acc = i % NACC
+            yield from wait(done[i % ND], i // ND)
             assert i in done_rows, "epilogue before its row's MMAs completed"
             assert acc_owner[acc] == i
             epi_done.add(i)
@@ -170,7 +171,10 @@ def simulate(rows, S, seed, drop=None):
                 choices.append(("mma", q))
         if not choices:
             break
-        c = rnd.choice(choices)
+        # slow_epilogue: the epilogue roles are picked 20 times less often, so
+        # the MMAs run far ahead of them (the accumulator reuse is exercised)
+        weights = [0.05 if (slow_epilogue and c in (3, 4)) else 1.0 for c in choices]
+        c = rnd.choices(choices, weights)[0]
         if c == "copy":
             kind, idx, val, bar = copies.pop(rnd.randrange(len(copies)))
             if kind == "a":
@@ -181,7 +185,7 @@ def simulate(rows, S, seed, drop=None):
         elif isinstance(c, tuple):
             r = pending[c[1]].pop(0)        # each issuer's MMAs complete in issue order
             done_rows.add(r)
-            done[r % NS].arrive()
+            done[r % ND].arrive()
         else:
             try:
                 next(roles[c])
@@ -217,7 +221,7 @@ def test_strip_schedules(n, L, S):
     planned = 0
     for seed in range(40):
         rows = strip_rows(n, L)[: random.Random(seed).randint(1, n * n)]
-        planned += simulate(rows, S, seed)
+        planned += simulate(rows, S, seed, slow_epilogue=seed % 2 == 1)
     assert planned > 0
 
 
@@ -246,7 +250,7 @@ def test_model_catches_a_dropped_wait(drop):
     rows = strip_rows(8, 4)
     for seed in range(150):
         try:
-            simulate(rows, 10 if drop == "conv_lag" else 33, seed, drop=drop)
+            simulate(rows, 10 if drop == "conv_lag" else 33, seed, drop=drop, slow_epilogue=drop == "mma_accempty")
         except AssertionError:
             caught += 1
     assert caught > 0
