@@ -729,6 +729,7 @@ def run_serve(args, ldgmg, torch, np, dev, stream, barrier):
         "solves_per_s": len(reqs) / span, "latency_ms": pct(lat), "queue_ms": pct(queue), "service_ms": pct(service),
         "reached_tol": ok, "mean_batch": float(batches.mean()), "max_batch_seen": int(batches.max()),
         "class_builds_s": build_s, "builds": int(stats["builds"]), "evictions": int(stats["evictions"]),
+        "precision_fallbacks": int(stats["precision_fallbacks"]),
         "hbm_resident_gb": stats["bytes_peak"] / 1e9, "gpu_launches": int(launches),
         "vcycle": "FP32 (batched tensor-core classes for b = 16 / 64), FP64 flexible CG",
         "same_prefix": {"requests": prefix, "latency_ms": pct(lat[:prefix]), "queue_ms": pct(queue[:prefix]),

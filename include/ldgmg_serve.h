@@ -22,6 +22,10 @@
  *     one for Stokes (GMRES).  Requests that arrive while a class is running
  *     join its next call.  Different classes run concurrently on different
  *     streams.
+ *   - Precision fallback.  When a solve of a class with a reduced-precision
+ *     V-cycle ends with LDGMG_ENOTCONV (the V-cycle too inexact for the
+ *     class, e.g. a large coefficient contrast in 3D), the class is rebuilt
+ *     once with an FP64 V-cycle and its requests are solved again.
  *   - Determinism.  Every right-hand side of a batched solve keeps its own
  *     Krylov scalars and its arithmetic does not depend on the other
  *     right-hand sides (ldgmg_solve), so a request's result is the same
@@ -84,6 +88,7 @@ typedef struct {
   size_t bytes_resident;    /* device bytes of resident classes (measured after build) */
   size_t bytes_peak;
   size_t hbm_budget;
+  uint64_t precision_fallbacks;   /* classes rebuilt with an FP64 V-cycle after a reduced-precision ENOTCONV */
 } ldgmg_server_stats;
 
 /* Start the server's scheduler, builder and worker threads.  Errors: EINVAL,

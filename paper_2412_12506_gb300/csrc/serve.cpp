@@ -79,6 +79,7 @@ struct Class {
   ldgmg_op* op = nullptr;
   ldgmg_hier* h = nullptr;
   int rmax = 1;             // right-hand sides per solve call of this class
+  int prec = -1;            // V-cycle precision of this class (-1: the server's); LDGMG_FP64 after a fallback
   bool busy = false;
   size_t est = 0, bytes = 0;
   double last_use = 0.0;
@@ -129,9 +130,10 @@ size_t estimate(const ldgmg_server_opts& o, const Class& c) {
   int per_row = 2 * d + 1;                        // face-neighbour stencil
   if (k.stokes == 1) per_row = d == 2 ? 7 : 13;   // stress form couples diagonal neighbours
   const int sai_rows = o.setup.sai_level == 2 ? (d == 2 ? 13 : 25) : per_row;
-  const double es = double(esize(o.setup.vcycle_precision));
+  const int prec = c.prec >= 0 ? c.prec : o.setup.vcycle_precision;
+  const double es = double(esize(prec));
   const int rmax = c.rmax;
-  const double vs = o.setup.vcycle_precision == LDGMG_FP64 ? 8.0 : 4.0;
+  const double vs = prec == LDGMG_FP64 ? 8.0 : 4.0;
   double total = 0.0;
   total += double(c.N) * per_row * b * b * 8.0 * 2.0;   // FP64 A (+ double-FP32 copy)
   int n = k.n;
@@ -265,6 +267,7 @@ void builder_loop(ldgmg_server* s) {
     const std::vector<double> mu = c->mu;
     ldgmg_setup_opts so = s->o.setup;
     so.max_rhs = c->rmax;
+    if (c->prec >= 0) so.vcycle_precision = c->prec;
     const bool simulate = s->o.simulate != 0;
     lk.unlock();
     ldgmg_op* op = nullptr;
@@ -353,6 +356,26 @@ void worker_loop(ldgmg_server* s, int wid) {
     }
     lk.lock();
     const double t_end = s->now();
+    if (status == LDGMG_ENOTCONV && !simulate && c->prec != LDGMG_FP64 &&
+        s->o.setup.vcycle_precision != LDGMG_FP64) {
+      // A reduced-precision V-cycle too inexact for this class (large
+      // coefficient contrast): rebuild the class once with an FP64 V-cycle
+      // and solve these requests again, ahead of the class's later ones.
+      for (int r = R - 1; r >= 0; --r) c->queue.push_front(j.reqs[size_t(r)]);
+      free_class(c);
+      s->reserved -= c->bytes;
+      c->bytes = 0;
+      c->prec = LDGMG_FP64;
+      c->state = Class::EMPTY;
+      c->busy = false;
+      s->st.classes_resident--;
+      s->st.precision_fallbacks++;
+      s->st.solve_calls++;
+      s->idle_workers++;
+      plan(s);
+      s->cv_done.notify_all();
+      continue;
+    }
     for (int r = 0; r < R; ++r) {
       auto& q = j.reqs[r];
       q->res.status = status;

@@ -70,7 +70,8 @@ class ServerStats(ctypes.Structure):
                 ("evictions", ctypes.c_uint64), ("build_failures", ctypes.c_uint64),
                 ("solve_calls", ctypes.c_uint64), ("max_batch_seen", ctypes.c_int),
                 ("classes_resident", ctypes.c_int), ("bytes_resident", ctypes.c_size_t),
-                ("bytes_peak", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t)]
+                ("bytes_peak", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t),
+                ("precision_fallbacks", ctypes.c_uint64)]
 
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double

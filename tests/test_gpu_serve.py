@@ -108,3 +108,24 @@ def test_admission_under_a_small_budget(lib):
     stats = s.stats()
     assert stats["evictions"] >= 1 and stats["bytes_peak"] <= int(one * 1.5)
     s.close()
+
+
+def test_reduced_precision_class_falls_back_to_fp64(lib):
+    """A 3D p = 3 interface class with contrast 1e4 does not converge with an
+    FP32 V-cycle (its SAI blocks span the contrast); the engine rebuilds that
+    class once with an FP64 V-cycle and solves its requests again, so every
+    request still reaches the tolerance.  A class that converges in FP32 keeps
+    its FP32 hierarchy."""
+    d, n, p = 3, 16, 3
+    N, b = n ** d, (p + 1) ** d
+    mu = square_mu(d, n, mu_in=1e4)
+    s = lib.Server(workers=2, max_batch=4, precision="fp32", max_iter=200)
+    rhs = [ldg.project_out_constant(random_rhs(N, b, seed=300 + k), d, p, N) for k in range(3)]
+    tickets = [s.submit(d, n, p, r, mu=mu, tol=1e-10) for r in rhs]
+    t_ok = s.submit(2, 16, 2, ldg.project_out_constant(random_rhs(256, 9, seed=9), 2, 2, 256), tol=1e-10)
+    for t in tickets:
+        _, r = s.wait(t)
+        assert r["status"] == lib.OK and r["relres"] <= 1.05e-10, r
+    assert s.wait(t_ok)[1]["status"] == lib.OK
+    assert s.stats()["precision_fallbacks"] == 1
+    s.close()

@@ -21,7 +21,9 @@ def _rhs(dim, n, p, stokes=None):
 
 
 def test_all_requests_complete_and_batch_per_class(lib):
-    s = lib.Server(workers=2, max_batch=8, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.01,
+    # simulated solves slower than the submissions (which copy up to 13 MB of
+    # right-hand side each), so that requests queue up behind running solves
+    s = lib.Server(workers=2, max_batch=8, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.05,
                    precision="fp32")
     tickets = []
     # scalar classes take batches (capped at 2^22 dofs per call: the 256^2 p = 4
