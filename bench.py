@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--stokes-tol", type=float, default=1e-9)
     ap.add_argument("--serve-requests", type=int, default=10000, help="0 disables the serving section")
     ap.add_argument("--serve-workers", type=int, default=4)
+    ap.add_argument("--serve-group-dofs", type=int, default=32768,
+                    help="scalar classes with at most this many unknowns are solved in grouped calls")
     ap.add_argument("--serve-fp64-prefix", type=int, default=1000,
                     help="requests of the same stream fed to the one-at-a-time FP64 server")
     ap.add_argument("--circle", type=int, default=1, help="0 disables the seeded-circle section")
@@ -627,21 +629,64 @@ def run_serve(args, ldgmg, torch, np, dev, stream, barrier):
             pool[key] = zero_mean_rhs(q["n"] ** q["dim"], (q["p"] + 1) ** q["dim"], seed=q["rhs_seed"] % 3)
         return c, pool[key]
 
-    srv = ldgmg.Server(workers=args.serve_workers, max_batch=32, precision="fp32")
+    def submit(srv, q):
+        c, r = rhs_of(q)
+        return srv.submit(q["dim"], q["n"], q["p"], r, mu=mus[c], tol=args.tol)
+
+    def build_all(srv):
+        t0 = time.time()
+        warm = [submit(srv, {"dim": c[0], "n": c[1], "p": c[2], "contrast": c[3], "rhs_seed": 0}) for c in classes]
+        for t in warm:
+            srv.wait(t)
+        return time.time() - t0
+
+    def open_stream(srv, count, arr):
+        """Submit reqs[:count] at the arrival times arr (seconds after the
+        start), collect the results; returns them with the kernel launches."""
+        results = [None] * count
+        tickets = [None] * count
+        ready = threading.Semaphore(0)
+
+        def waiter():
+            for i in range(count):
+                ready.acquire()
+                results[i] = srv.wait(tickets[i])[1]
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        l0 = ldgmg.kernel_launches()
+        base = srv.clock()
+        for i in range(count):
+            delay = base + arr[i] - srv.clock()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[i] = submit(srv, reqs[i])
+            ready.release()
+        th.join()
+        return results, ldgmg.kernel_launches() - l0
+
+    def summary(res, launches):
+        lat = np.array([r["t_end"] - r["t_submit"] for r in res]) * 1e3
+        queue = np.array([r["t_start"] - r["t_submit"] for r in res]) * 1e3
+        service = np.array([r["t_end"] - r["t_start"] for r in res]) * 1e3
+        span = max(r["t_end"] for r in res) - min(r["t_submit"] for r in res)
+        ok = sum(1 for r in res if r["status"] == ldgmg.OK and r["relres"] <= 1.05 * args.tol)
+        batches = np.array([r["batch"] for r in res])
+        return {"requests": len(res), "solves_per_s": len(res) / span, "latency_ms": pct(lat), "queue_ms": pct(queue),
+                "service_ms": pct(service), "reached_tol": ok, "mean_batch": float(batches.mean()),
+                "max_batch_seen": int(batches.max()), "gpu_launches_per_request": launches / len(res)}
+
+    def pct(v):
+        return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+
+    gd = args.serve_group_dofs
+    srv = ldgmg.Server(workers=args.serve_workers, max_batch=32, precision="fp32", group_dofs=gd)
     l0 = ldgmg.kernel_launches()
     # warm: build every class once (the hierarchy cache), then a closed burst to size the stream
-    t0 = time.time()
-    warm = [srv.submit(c[0], c[1], c[2], rhs_of({"dim": c[0], "n": c[1], "p": c[2], "contrast": c[3],
-                                                  "rhs_seed": 0})[1], mu=mus[c], tol=args.tol) for c in classes]
-    for t in warm:
-        srv.wait(t)
-    build_s = time.time() - t0
+    build_s = build_all(srv)
     burst = reqs[:min(len(reqs), 1000)]
     t0 = time.time()
-    tk = []
-    for q in burst:
-        c, r = rhs_of(q)
-        tk.append(srv.submit(q["dim"], q["n"], q["p"], r, mu=mus[c], tol=args.tol))
+    tk = [submit(srv, q) for q in burst]
     for t in tk:
         srv.wait(t)
     capacity = len(burst) / (time.time() - t0)
@@ -650,96 +695,54 @@ def run_serve(args, ldgmg, torch, np, dev, stream, barrier):
     # burst keeps every class's queue long, so it batches more than an open
     # stream does and overstates the capacity the stream sees)
     arr = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs)))
-    results = [None] * len(reqs)
-    tickets = [None] * len(reqs)
-    ready = threading.Semaphore(0)
-
-    def waiter():
-        for i in range(len(reqs)):
-            ready.acquire()
-            results[i] = srv.wait(tickets[i])[1]
-
-    th = threading.Thread(target=waiter)
-    th.start()
-    base = srv.clock()
-    for i, q in enumerate(reqs):
-        delay = base + arr[i] - srv.clock()
-        if delay > 0:
-            time.sleep(delay)
-        c, r = rhs_of(q)
-        tickets[i] = srv.submit(q["dim"], q["n"], q["p"], r, mu=mus[c], tol=args.tol)
-        ready.release()
-    th.join()
+    results, launches = open_stream(srv, len(reqs), arr)
     stats = srv.stats()
-    launches = ldgmg.kernel_launches() - l0
+    total_launches = ldgmg.kernel_launches() - l0
     srv.close()
-    lat = np.array([r["t_end"] - r["t_submit"] for r in results]) * 1e3
-    queue = np.array([r["t_start"] - r["t_submit"] for r in results]) * 1e3
-    service = np.array([r["t_end"] - r["t_start"] for r in results]) * 1e3
-    span = max(r["t_end"] for r in results) - min(r["t_submit"] for r in results)
-    ok = sum(1 for r in results if r["status"] == ldgmg.OK and r["relres"] <= 1.05 * args.tol)
-    batches = np.array([r["batch"] for r in results])
-    # The plain FP64 GPU solver, one request at a time (one worker, no
-    # batching, FP64 V-cycle), fed the same Poisson arrival stream (the same
-    # arrival times and right-hand sides) for its first `prefix` requests;
-    # latency includes its queueing.  The engine's latency over the same
-    # prefix is reported beside it.
+    main = summary(results, launches)
+    small = [i for i, q in enumerate(reqs) if q["n"] ** q["dim"] * (q["p"] + 1) ** q["dim"] <= gd]
     prefix = min(len(reqs), args.serve_fp64_prefix)
+    # The same engine without grouped calls (every class its own calls), the
+    # same arrival times and right-hand sides for the stream's first `prefix`
+    # requests.
+    s1 = ldgmg.Server(workers=args.serve_workers, max_batch=32, precision="fp32", group_dofs=0)
+    build_all(s1)
+    res1, launches1 = open_stream(s1, prefix, arr)
+    s1.close()
+    # The plain FP64 GPU solver, one request at a time (one worker, no
+    # batching, FP64 V-cycle), fed the same Poisson arrival stream for the
+    # same prefix; latency includes its queueing.
     s64 = ldgmg.Server(workers=1, max_batch=1, precision="fp64")
-    t0 = time.time()
-    warm = [s64.submit(c[0], c[1], c[2], rhs_of({"dim": c[0], "n": c[1], "p": c[2], "contrast": c[3],
-                                                 "rhs_seed": 0})[1], mu=mus[c], tol=args.tol) for c in classes]
-    for t in warm:
-        s64.wait(t)
-    build64_s = time.time() - t0
-    res64 = [None] * prefix
-    tk64 = [None] * prefix
-    ready64 = threading.Semaphore(0)
-
-    def waiter64():
-        for i in range(prefix):
-            ready64.acquire()
-            res64[i] = s64.wait(tk64[i])[1]
-
-    th = threading.Thread(target=waiter64)
-    th.start()
-    base = s64.clock()
-    for i in range(prefix):
-        q = reqs[i]
-        delay = base + arr[i] - s64.clock()
-        if delay > 0:
-            time.sleep(delay)
-        c, r = rhs_of(q)
-        tk64[i] = s64.submit(q["dim"], q["n"], q["p"], r, mu=mus[c], tol=args.tol)
-        ready64.release()
-    th.join()
+    build64_s = build_all(s64)
+    res64, launches64 = open_stream(s64, prefix, arr)
     s64.close()
-    lat64 = np.array([r["t_end"] - r["t_submit"] for r in res64]) * 1e3
-    svc64 = np.array([r["t_end"] - r["t_start"] for r in res64]) * 1e3
-    span64 = max(r["t_end"] for r in res64) - min(r["t_submit"] for r in res64)
-    ok64 = sum(1 for r in res64 if r["status"] == ldgmg.OK and r["relres"] <= 1.05 * args.tol)
+    sp = [i for i in small if i < prefix]
 
-    def pct(v):
-        return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
+    def small_lat(res):
+        return pct(np.array([res[i]["t_end"] - res[i]["t_submit"] for i in sp]) * 1e3) if sp else None
 
-    return {
+    out = {
         "workload": f"serving_{len(reqs)}req_poisson_arrivals_{len(classes)}classes",
         "requests": len(reqs), "classes": len(classes), "workers": args.serve_workers, "max_batch": 32,
-        "arrival_rate_per_s": rate, "closed_burst_capacity_per_s": capacity,
-        "solves_per_s": len(reqs) / span, "latency_ms": pct(lat), "queue_ms": pct(queue), "service_ms": pct(service),
-        "reached_tol": ok, "mean_batch": float(batches.mean()), "max_batch_seen": int(batches.max()),
+        "group_dofs": gd, "arrival_rate_per_s": rate, "closed_burst_capacity_per_s": capacity,
+        "small_requests": len(small),
         "class_builds_s": build_s, "builds": int(stats["builds"]), "evictions": int(stats["evictions"]),
         "precision_fallbacks": int(stats["precision_fallbacks"]),
-        "hbm_resident_gb": stats["bytes_peak"] / 1e9, "gpu_launches": int(launches),
+        "group_calls": int(stats["group_calls"]), "group_requests": int(stats["group_requests"]),
+        "hbm_resident_gb": stats["bytes_peak"] / 1e9, "gpu_launches": int(total_launches),
         "vcycle": "FP32 (batched tensor-core classes for b = 16 / 64), FP64 flexible CG",
-        "same_prefix": {"requests": prefix, "latency_ms": pct(lat[:prefix]), "queue_ms": pct(queue[:prefix]),
-                        "service_ms": pct(service[:prefix])},
-        "fp64_one_at_a_time": {"requests": prefix, "arrival_rate_per_s": rate,
-                               "solves_per_s": prefix / span64, "latency_ms": pct(lat64),
-                               "service_ms": pct(svc64), "reached_tol": ok64, "class_builds_s": build64_s,
-                               "how": "same arrival times and right-hand sides, one worker, no batching, FP64 "
-                                      "V-cycle and CG; latency includes queueing"},
     }
+    out.update(main)
+    out["same_prefix"] = dict(summary(results[:prefix], float("nan")), small_latency_ms=small_lat(results))
+    out["same_prefix"].pop("gpu_launches_per_request")
+    out["ungrouped_same_prefix"] = dict(summary(res1, launches1), small_latency_ms=small_lat(res1),
+                                        how="the same engine with group_dofs = 0 (one call per class), "
+                                            "same arrival times and right-hand sides")
+    out["fp64_one_at_a_time"] = dict(summary(res64, launches64), small_latency_ms=small_lat(res64),
+                                     arrival_rate_per_s=rate, class_builds_s=build64_s,
+                                     how="same arrival times and right-hand sides, one worker, no batching, "
+                                         "FP64 V-cycle and CG; latency includes queueing")
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -249,6 +249,47 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
  * length; at most cap values are written (relres may be NULL). */
 ldgmg_status ldgmg_solve_history(const ldgmg_hier* h, int rhs, double* relres, int cap, int* count);
 
+/* ---- grouped solve: many small problems in one launch --------------------
+ * A group workspace holds the device and pinned host memory of grouped
+ * solves (grown on demand, kept between calls).  Use it from one thread at a
+ * time; free with ldgmg_group_free. */
+typedef struct ldgmg_group ldgmg_group;
+ldgmg_status ldgmg_group_create(ldgmg_group** out);
+void ldgmg_group_free(ldgmg_group* g);
+
+/* Solve `count` independent single-right-hand-side problems A_i x_i = rhs_i,
+ * each on its own hierarchy h[i] (hierarchies may differ in mesh, degree,
+ * coefficient field, smoother and V-cycle precision, and may repeat), with
+ * one kernel launch per cluster size (at most four launches): every problem
+ * is a whole CG solve (Sec. 2.2, the V-cycle of Algorithm 1 as the
+ * preconditioner) run on the device by one thread-block cluster of 1, 2, 4
+ * or 8 CTAs (ldgmg_group_cluster), with no host round trip inside it.  The
+ * method, stopping test (||rhs - A x|| <= tol[i] ||rhs||, FP64 residual
+ * confirmation with a reduced-precision V-cycle) and max_iter are those of
+ * ldgmg_solve on h[i] with one right-hand side; results agree with it to
+ * rounding (sums are taken in another order).  Eligible hierarchies: scalar
+ * operators solved by CG whose blocks are not tensor-core images (max_rhs =
+ * 1, or a block size / precision without the batched path), at most 12
+ * levels; others -> EUNSUPPORTED.  The call reads the hierarchies' matrices
+ * only (never their vectors), so several group calls may share a hierarchy.
+ *   rhs[i], x[i]  N_i*b_i doubles each, device or host pointers (host ones are
+ *                 staged through the workspace); the x[i] must not overlap.
+ *   tol[i] > 0.
+ *   iters, relres, status  host arrays of count entries (may be NULL): the
+ *                 iteration count, the true final relative residual and the
+ *                 status of problem i (OK; ENOTCONV at max_iter or on a
+ *                 non-finite residual, x written; EINVAL for non-finite rhs).
+ * Returns OK when every problem converged, else the first failing problem's
+ * status (the others are still solved).  Synchronises `stream`. */
+ldgmg_status ldgmg_solve_group(ldgmg_group* g, int count, ldgmg_hier* const* h, const double* const* rhs,
+                               double* const* x, const double* tol, int* iters, double* relres,
+                               ldgmg_status* status, void* stream);
+
+/* Cluster size (CTAs) a grouped solve gives hierarchy h: 1, 2, 4 or 8 by the
+ * entries of its finest operator (about 2^18 per CTA); 0 if h is not
+ * eligible for grouped solves. */
+ldgmg_status ldgmg_group_cluster(const ldgmg_hier* h, int* cluster);
+
 /* y = A x with the operator apply of the outer CG (Sec. 2.2: the residual
  * update q = A p of every CG iteration), exactly as ldgmg_solve runs it on this
  * hierarchy: the double-FP32 kernels (outer_apply DF; one right-hand side or

@@ -22,6 +22,13 @@
  *     one for Stokes (GMRES).  Requests that arrive while a class is running
  *     join its next call.  Different classes run concurrently on different
  *     streams.
+ *   - Grouped small problems.  Scalar classes with at most group_dofs
+ *     unknowns are built with one right-hand side per call and solved
+ *     together with the queued requests of every other such class: one
+ *     ldgmg_solve_group call (one kernel launch per cluster size, each
+ *     problem a whole solve on one thread-block cluster) takes up to
+ *     group_max of the oldest small requests, whatever their class.  Several
+ *     grouped calls may read the same class at once.
  *   - Precision fallback.  When a solve of a class with a reduced-precision
  *     V-cycle ends with LDGMG_ENOTCONV (the V-cycle too inexact for the
  *     class, e.g. a large coefficient contrast in 3D), the class is rebuilt
@@ -56,6 +63,9 @@ typedef struct {
                                testing the scheduler on machines without a GPU. */
   double simulate_solve_s;  /* simulate = 1: seconds per simulated solve call */
   ldgmg_setup_opts setup;   /* options of every hierarchy (max_rhs is set by the server) */
+  size_t group_dofs;        /* scalar classes with N*b <= group_dofs are solved in grouped calls
+                               (ldgmg_solve_group); 0 = none */
+  int group_max;            /* requests per grouped call, 1..65536; 0 = 512 */
 } ldgmg_server_opts;
 
 typedef struct {
@@ -74,7 +84,7 @@ typedef struct {
   int iters;
   double relres;            /* true final relative residual (ldgmg_solve) */
   double t_submit, t_start, t_end;   /* seconds on the server clock (ldgmg_server_clock) */
-  int batch;                /* right-hand sides in the solve call that served the request */
+  int batch;                /* right-hand sides (grouped calls: problems) in the call that served it */
   int worker;               /* worker (stream) index that ran it */
 } ldgmg_result;
 
@@ -82,13 +92,15 @@ typedef struct {
   uint64_t submitted, completed;
   uint64_t builds, evictions;
   uint64_t build_failures;  /* classes whose build failed or that admission refused (too large) */
-  uint64_t solve_calls;     /* ldgmg_solve calls; completed / solve_calls = mean batch */
+  uint64_t solve_calls;     /* ldgmg_solve and ldgmg_solve_group calls; completed / solve_calls = mean batch */
   int max_batch_seen;
   int classes_resident;
   size_t bytes_resident;    /* device bytes of resident classes (measured after build) */
   size_t bytes_peak;
   size_t hbm_budget;
   uint64_t precision_fallbacks;   /* classes rebuilt with an FP64 V-cycle after a reduced-precision ENOTCONV */
+  uint64_t group_calls;     /* ldgmg_solve_group calls (counted in solve_calls too) */
+  uint64_t group_requests;  /* requests served by them */
 } ldgmg_server_stats;
 
 /* Start the server's scheduler, builder and worker threads.  Errors: EINVAL,

@@ -1539,6 +1539,266 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
 }
 
 // ---------------------------------------------------------------------------
+// grouped solves (group.cu): many small problems, one launch per cluster size
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+struct ldgmg_group {
+  char* dev = nullptr;       // descriptors, staged vectors, per-problem work space
+  size_t dev_cap = 0;
+  char* host = nullptr;      // pinned mirror of the descriptor and staging regions
+  size_t host_cap = 0;
+};
+
+static std::string group_ineligible(const ldgmg_hier* h) {
+  if (h->batched) return "a tensor-core (batched) hierarchy";
+  if (h->gmres) return "a GMRES (Stokes) hierarchy";
+  if (h->op->host.nf != 1) return "a multi-field operator";
+  if (h->lv.size() > size_t(kGroupMaxLevels)) return "more than 12 levels";
+  return "";
+}
+
+// about 2^18 finest-operator entries per CTA of the cluster
+static int group_cluster_of(const ldgmg_hier* h) {
+  const double w = double(h->op->A.nnzb) * h->op->A.b * h->op->A.b;
+  int c = 1;
+  while (c < 8 && w > double(c) * double(1 << 18)) c *= 2;
+  return c;
+}
+
+static GroupMat group_mat(const DevMat& M) {
+  GroupMat g;
+  g.row_ptr = M.row_ptr;
+  g.col = M.col;
+  g.vals = M.vals;
+  g.prec = M.prec;
+  g.cs = M.cs;
+  g.inv_scale = 1.0 / M.scale;
+  return g;
+}
+
+// descriptor of hierarchy h; colour pointers of Gauss-Seidel levels are
+// appended to cptr (their device copy will start at cptr_dev + cptr.size()
+// at entry); returns the level-vector entries one problem needs
+static int64_t group_problem(const ldgmg_hier* h, GroupProblem& P, std::vector<int>& cptr, const int* cptr_dev) {
+  std::memset(&P, 0, sizeof P);
+  const HostLevel& L0 = h->op->host;
+  P.dim = L0.dim;
+  P.q = L0.p + 1;
+  P.nl = int(h->lv.size());
+  P.smoother = h->o.smoother == LDGMG_SAI ? G_SAI : (h->o.smoother == LDGMG_JACOBI ? G_JACOBI : G_GS);
+  P.pre_bt = h->o.pre_form == LDGMG_FORM_BT;
+  P.post_bt = h->o.post_form == LDGMG_FORM_BT;
+  P.nu1 = h->o.nu1;
+  P.nu2 = h->o.nu2;
+  P.vprec = h->vprec;
+  P.flexible = h->prec != P_FP64;
+  P.max_iter = h->o.max_iter;
+  P.omega = h->o.omega;
+  P.P = h->P1d;
+  P.pinv = h->pinv;
+  P.nbot = h->nbot;
+  P.A0 = group_mat(h->op->A);
+  P.n0 = L0.N * L0.b;
+  int64_t off = 0;
+  for (int l = 0; l < P.nl; ++l) {
+    const DevLevel& D = h->lv[l];
+    GroupLevel& G = P.lv[l];
+    G.N = D.N;
+    G.n = D.n;
+    G.b = D.b;
+    G.A = group_mat(D.A);
+    G.S = group_mat(D.S);
+    G.ST = group_mat(D.ST);
+    if (P.smoother == G_GS && l + 1 < P.nl) {
+      G.crows = D.crows;
+      G.ncolours = int(D.cptr.size()) - 1;
+      G.cptr = cptr_dev + cptr.size();
+      for (int64_t v : D.cptr) cptr.push_back(int(v));
+    }
+    G.voff = off;
+    off += 3 * D.N * D.b;
+  }
+  return off;
+}
+
+static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+extern "C" {
+
+ldgmg_status ldgmg_group_create(ldgmg_group** out) {
+  g_err.clear();
+  if (!out) return fail(LDGMG_EINVAL, "null argument");
+  *out = new (std::nothrow) ldgmg_group();
+  return *out ? LDGMG_OK : fail(LDGMG_ENOMEM, "host allocation");
+}
+
+void ldgmg_group_free(ldgmg_group* g) {
+  if (!g) return;
+  cudaFree(g->dev);
+  cudaFreeHost(g->host);
+  delete g;
+}
+
+ldgmg_status ldgmg_group_cluster(const ldgmg_hier* h, int* cluster) {
+  g_err.clear();
+  if (!h || !cluster) return fail(LDGMG_EINVAL, "null argument");
+  *cluster = group_ineligible(h).empty() ? group_cluster_of(h) : 0;
+  return LDGMG_OK;
+}
+
+ldgmg_status ldgmg_solve_group(ldgmg_group* g, int count, ldgmg_hier* const* hs, const double* const* rhs,
+                               double* const* x, const double* tol, int* iters, double* relres,
+                               ldgmg_status* status, void* stream) {
+  NvtxRange nvtx_("ldgmg_solve_group");
+  g_err.clear();
+  if (!g) return fail(LDGMG_EINVAL, "null group");
+  if (count < 0 || count > (1 << 20)) return fail(LDGMG_EINVAL, "count must be in 0..2^20");
+  if (count == 0) return LDGMG_OK;
+  if (!hs || !rhs || !x || !tol) return fail(LDGMG_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  // distinct hierarchies, eligibility, cluster sizes
+  std::map<const ldgmg_hier*, int> pid;
+  std::vector<const ldgmg_hier*> uniq;
+  std::vector<int> item_prob(count), item_c(count);
+  std::vector<char> hb(count), hx(count);
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !rhs[i] || !x[i]) return fail(LDGMG_EINVAL, "null hierarchy or vector of problem " + std::to_string(i));
+    if (!(tol[i] > 0.0)) return fail(LDGMG_EINVAL, "tol must be positive");
+    auto it = pid.find(hs[i]);
+    if (it == pid.end()) {
+      const std::string why = group_ineligible(hs[i]);
+      if (!why.empty()) return fail(LDGMG_EUNSUPPORTED, "grouped solves do not take " + why);
+      it = pid.emplace(hs[i], int(uniq.size())).first;
+      uniq.push_back(hs[i]);
+    }
+    item_prob[i] = it->second;
+    item_c[i] = group_cluster_of(hs[i]);
+    hb[i] = is_host_ptr(rhs[i]);
+    hx[i] = is_host_ptr(x[i]);
+  }
+  const int np = int(uniq.size());
+  // launch order: by cluster size
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return item_c[a] < item_c[b]; });
+  // descriptors (the cptr device address is fixed once the layout is known, so
+  // take the sizes in a first pass)
+  std::vector<GroupProblem> probs(static_cast<size_t>(np));
+  std::vector<int> cptr;
+  std::vector<int64_t> lvec(np), n0(np);
+  std::vector<int> vsz(np);
+  for (int k = 0; k < np; ++k) {
+    lvec[k] = group_problem(uniq[k], probs[k], cptr, nullptr);
+    n0[k] = probs[k].n0;
+    vsz[k] = probs[k].vprec == 0 ? 8 : 4;
+  }
+  // layout: region H2D [probs | items | cptr | staged rhs], region D2H [outs | staged x],
+  // then per-problem work space (level vectors, CG vectors)
+  size_t off = 0;
+  const size_t o_probs = off;
+  off = align256(off + sizeof(GroupProblem) * np);
+  const size_t o_items = off;
+  off = align256(off + sizeof(GroupItem) * count);
+  const size_t o_cptr = off;
+  off = align256(off + sizeof(int) * cptr.size());
+  std::vector<size_t> o_b(count, 0), o_x(count, 0), o_lv(count), o_cg(count);
+  for (int i = 0; i < count; ++i)
+    if (hb[i]) {
+      o_b[i] = off;
+      off = align256(off + size_t(n0[item_prob[i]]) * 8);
+    }
+  const size_t h2d_end = off;
+  const size_t o_outs = off;
+  off = align256(off + sizeof(GroupOut) * count);
+  for (int i = 0; i < count; ++i)
+    if (hx[i]) {
+      o_x[i] = off;
+      off = align256(off + size_t(n0[item_prob[i]]) * 8);
+    }
+  const size_t d2h_end = off;
+  for (int i = 0; i < count; ++i) {
+    const int k = item_prob[i];
+    o_lv[i] = off;
+    off = align256(off + size_t(lvec[k]) * vsz[k]);
+    o_cg[i] = off;
+    off = align256(off + size_t(n0[k]) * 4 * 8);
+  }
+  const size_t total = off;
+  if (total > g->dev_cap) {
+    CK(cudaStreamSynchronize(st));
+    cudaFree(g->dev);
+    g->dev = nullptr;
+    g->dev_cap = 0;
+    const size_t want = total + total / 4;
+    CK(cudaMalloc(&g->dev, want));
+    g->dev_cap = want;
+  }
+  if (d2h_end > g->host_cap) {
+    cudaFreeHost(g->host);
+    g->host = nullptr;
+    g->host_cap = 0;
+    const size_t want = d2h_end + d2h_end / 4;
+    CK(cudaMallocHost(&g->host, want));
+    g->host_cap = want;
+  }
+  char* D = g->dev;
+  char* H = g->host;
+  // descriptors with their device addresses
+  cptr.clear();
+  for (int k = 0; k < np; ++k) group_problem(uniq[k], probs[k], cptr, reinterpret_cast<const int*>(D + o_cptr));
+  std::memcpy(H + o_probs, probs.data(), sizeof(GroupProblem) * np);
+  if (!cptr.empty()) std::memcpy(H + o_cptr, cptr.data(), sizeof(int) * cptr.size());
+  GroupItem* items = reinterpret_cast<GroupItem*>(H + o_items);
+  for (int j = 0; j < count; ++j) {
+    const int i = order[j];
+    const int k = item_prob[i];
+    GroupItem& I = items[j];
+    std::memset(&I, 0, sizeof I);
+    I.prob = k;
+    I.b = hb[i] ? reinterpret_cast<const double*>(D + o_b[i]) : rhs[i];
+    I.x = hx[i] ? reinterpret_cast<double*>(D + o_x[i]) : x[i];
+    I.tol = tol[i];
+    I.lvec = D + o_lv[i];
+    I.cg = reinterpret_cast<double*>(D + o_cg[i]);
+    I.out = reinterpret_cast<GroupOut*>(D + o_outs) + j;
+    if (hb[i]) std::memcpy(H + o_b[i], rhs[i], size_t(n0[k]) * 8);
+  }
+  CK(cudaMemcpyAsync(D, H, h2d_end, cudaMemcpyHostToDevice, st));
+  const GroupProblem* dprobs = reinterpret_cast<const GroupProblem*>(D + o_probs);
+  const GroupItem* ditems = reinterpret_cast<const GroupItem*>(D + o_items);
+  for (int j0 = 0; j0 < count;) {
+    int j1 = j0;
+    while (j1 < count && item_c[order[j1]] == item_c[order[j0]]) ++j1;
+    CK(group_solve(dprobs, ditems + j0, j1 - j0, item_c[order[j0]], st));
+    j0 = j1;
+  }
+  CK(cudaMemcpyAsync(H + o_outs, D + o_outs, d2h_end - o_outs, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const GroupOut* outs = reinterpret_cast<const GroupOut*>(H + o_outs);
+  ldgmg_status result = LDGMG_OK;
+  std::string msg;
+  for (int j = 0; j < count; ++j) {
+    const int i = order[j];
+    const GroupOut& o = outs[j];
+    const ldgmg_status si = o.status == 0 ? LDGMG_OK : (o.status == 3 ? LDGMG_EINVAL : LDGMG_ENOTCONV);
+    if (iters) iters[i] = o.iters;
+    if (relres) relres[i] = o.relres;
+    if (status) status[i] = si;
+    if (hx[i]) std::memcpy(x[i], H + o_x[i], size_t(n0[item_prob[i]]) * 8);
+    if (si != LDGMG_OK && result == LDGMG_OK) {
+      result = si;
+      msg = "problem " + std::to_string(i) +
+            (o.status == 3 ? ": rhs contains NaN or Inf"
+                           : (o.status == 2 ? ": CG breakdown (non-finite residual)" : ": max_iter reached"));
+    }
+  }
+  if (result != LDGMG_OK) return fail(result, msg);
+  return LDGMG_OK;
+}
+
+// ---------------------------------------------------------------------------
 // per-level entry points
 // ---------------------------------------------------------------------------
 

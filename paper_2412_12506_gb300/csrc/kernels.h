@@ -228,6 +228,60 @@ cudaError_t bsr_apply_multi64(const DevMat& M, int mode, const double* x, const 
 struct LsProblem;
 std::string sai_ls_device(std::vector<LsProblem>& batch, cudaStream_t st);
 
+// Grouped solve (group.cu): many independent single-right-hand-side scalar
+// problems, of any mix of classes, in one launch.  Each problem is a whole
+// preconditioned CG solve (Sec. 2.2; the V-cycle of Algorithm 1 as the
+// preconditioner, FP64 outer operator) run by one thread-block cluster of
+// `cluster` CTAs, which synchronise with cluster barriers between steps; no
+// host round trip inside a solve.  Descriptors live in device memory.
+constexpr int kGroupMaxLevels = 12;
+enum { G_SAI = 0, G_JACOBI = 1, G_GS = 2 };
+struct GroupMat {
+  const int* row_ptr;
+  const int* col;
+  const void* vals;     // column-major blocks, column stride cs, storage precision prec
+  int prec;
+  int cs;
+  double inv_scale;     // 1 / storage scale
+};
+struct GroupLevel {
+  int64_t N;            // elements
+  int n, b, ncolours, pad;
+  GroupMat A, S, ST;    // operator; smoother (B or D^-1); B^T (SAI)
+  const int* crows;     // Gauss-Seidel: element rows grouped by colour
+  const int* cptr;      // device, ncolours + 1
+  int64_t voff;         // rhs, x, r of this level at voff, voff + N b, voff + 2 N b (vector entries)
+};
+struct GroupProblem {
+  int dim, q, nl, smoother, pre_bt, post_bt, nu1, nu2;
+  int vprec;            // level vectors: 0 double (FP64 storage), 1 float
+  int flexible;         // flexible CG (reduced-precision V-cycle)
+  int max_iter, pad;
+  double omega;
+  const double* P;      // 2 q^2 one-dimensional injection matrices
+  const double* pinv;   // bottom pseudo-inverse, nbot x nbot row-major
+  int64_t nbot;
+  GroupMat A0;          // FP64 finest operator of the outer CG
+  int64_t n0;           // unknowns N_0 b
+  GroupLevel lv[kGroupMaxLevels];
+};
+struct GroupOut {
+  int iters;
+  int status;           // 0 converged, 1 max_iter reached, 2 non-finite residual, 3 non-finite rhs
+  double relres;        // true ||b - A x|| / ||b||
+};
+struct GroupItem {
+  int prob, pad;
+  const double* b;      // device FP64 right-hand side, [element][mode]
+  double* x;            // device FP64 solution
+  double tol;
+  void* lvec;           // level vectors of this item (double or float)
+  double* cg;           // r, z, p, q: 4 n0 doubles
+  GroupOut* out;
+};
+// items[0 .. count) all run with clusters of `cluster` CTAs (1, 2, 4 or 8)
+cudaError_t group_solve(const GroupProblem* probs, const GroupItem* items, int count, int cluster, cudaStream_t st);
+
 // launch-count bookkeeping for kernels defined in other translation units
 cudaError_t launched(int count = 1);
 

@@ -4,12 +4,15 @@
 //
 // All scheduling state lives under one mutex.  Scheduling is event driven:
 // every event that can make progress possible (a submit, a finished build, a
-// finished solve) calls plan() with the mutex held.  plan() (1) fails the
-// queues of classes whose build failed, (2) admits classes with queued
-// requests in the order of their oldest request, evicting idle classes
-// least-recently-used first while the footprint does not fit, and (3) hands
-// the oldest ready, idle class with queued requests to an idle worker
-// together with as many of its requests as one solve call takes.
+// finished solve) calls plan() with the mutex held.  plan() (0) rebuilds
+// classes marked for an FP64 V-cycle once no running call reads them, (1)
+// fails the queues of classes whose build failed, (2) admits classes with
+// queued requests in the order of their oldest request, evicting idle
+// classes least-recently-used first while the footprint does not fit, and
+// (3) hands work to idle workers, oldest waiting request first: a large
+// class's call takes as many of its own requests as one solve call takes; a
+// small class's request starts a grouped call (ldgmg_solve_group) that takes
+// the oldest queued requests of every ready small class.
 #include "ldgmg_serve.h"
 
 #include <cuda_runtime.h>
@@ -80,14 +83,18 @@ struct Class {
   ldgmg_hier* h = nullptr;
   int rmax = 1;             // right-hand sides per solve call of this class
   int prec = -1;            // V-cycle precision of this class (-1: the server's); LDGMG_FP64 after a fallback
-  bool busy = false;
+  bool small = false;       // solved in grouped calls together with other small classes
+  int users = 0;            // requests of running calls that read the class (grouped calls may share it)
+  bool rebuild_fp64 = false;   // rebuild with an FP64 V-cycle once no call reads it
   size_t est = 0, bytes = 0;
   double last_use = 0.0;
   std::deque<std::shared_ptr<Req>> queue;
 };
 
 struct Job {
-  Class* c = nullptr;
+  Class* c = nullptr;                 // per-class call
+  bool grouped = false;               // grouped call: cls[r] is the class of reqs[r]
+  std::vector<Class*> cls;
   std::vector<std::shared_ptr<Req>> reqs;
 };
 
@@ -184,6 +191,20 @@ void fail_queue(ldgmg_server* s, Class* c) {
 
 // Called with s->mu held; the caller wakes waiters (cv_done) afterwards.
 void plan(ldgmg_server* s) {
+  // (0) classes marked for an FP64 rebuild that no running call reads any more
+  for (auto& kv : s->classes) {
+    Class* c = kv.second.get();
+    if (c->state == Class::READY && c->rebuild_fp64 && c->users == 0) {
+      free_class(c);
+      s->reserved -= c->bytes;
+      c->bytes = 0;
+      c->prec = LDGMG_FP64;
+      c->rebuild_fp64 = false;
+      c->state = Class::EMPTY;
+      s->st.classes_resident--;
+      s->st.precision_fallbacks++;
+    }
+  }
   // (1) failed builds: their queued requests complete with the build status
   for (auto& kv : s->classes) {
     Class* c = kv.second.get();
@@ -211,7 +232,7 @@ void plan(ldgmg_server* s) {
       Class* victim = nullptr;
       for (auto& kv : s->classes) {
         Class* v = kv.second.get();
-        if (v->state == Class::READY && !v->busy && v->queue.empty() && (!victim || v->last_use < victim->last_use))
+        if (v->state == Class::READY && v->users == 0 && v->queue.empty() && (!victim || v->last_use < victim->last_use))
           victim = v;
       }
       if (!victim) break;
@@ -228,24 +249,45 @@ void plan(ldgmg_server* s) {
     s->build_q.push_back(c);
     s->cv_build.notify_one();
   }
-  // (3) dispatch to idle workers, oldest waiting request first
+  // (3) dispatch to idle workers, oldest waiting request first.  A small
+  // class's request starts a grouped call that takes the oldest queued
+  // requests of all ready small classes; any other class runs one call at a
+  // time with as many of its own requests as one call takes.
+  auto ready = [](const Class* c) { return c->state == Class::READY && !c->rebuild_fp64 && !c->queue.empty(); };
   while (s->idle_workers > 0) {
     Class* best = nullptr;
     for (auto& kv : s->classes) {
       Class* c = kv.second.get();
-      if (c->state != Class::READY || c->busy || c->queue.empty()) continue;
+      if (!ready(c) || (!c->small && c->users > 0)) continue;
       if (!best || c->queue.front()->res.t_submit < best->queue.front()->res.t_submit) best = c;
     }
     if (!best) break;
     Job j;
-    j.c = best;
-    const size_t cap = size_t(best->rmax);
-    const double tol = best->queue.front()->tol;
-    while (!best->queue.empty() && j.reqs.size() < cap && best->queue.front()->tol == tol) {
-      j.reqs.push_back(best->queue.front());
-      best->queue.pop_front();
+    if (best->small) {
+      j.grouped = true;
+      std::vector<Class*> cand;
+      for (auto& kv : s->classes)
+        if (kv.second->small && ready(kv.second.get())) cand.push_back(kv.second.get());
+      while (j.reqs.size() < size_t(s->o.group_max)) {
+        Class* o = nullptr;
+        for (Class* c : cand)
+          if (!c->queue.empty() && (!o || c->queue.front()->res.t_submit < o->queue.front()->res.t_submit)) o = c;
+        if (!o) break;
+        j.reqs.push_back(o->queue.front());
+        j.cls.push_back(o);
+        o->queue.pop_front();
+        o->users++;
+      }
+    } else {
+      j.c = best;
+      const size_t cap = size_t(best->rmax);
+      const double tol = best->queue.front()->tol;
+      while (!best->queue.empty() && j.reqs.size() < cap && best->queue.front()->tol == tol) {
+        j.reqs.push_back(best->queue.front());
+        best->queue.pop_front();
+      }
+      best->users++;
     }
-    best->busy = true;
     s->idle_workers--;
     s->work_q.push_back(std::move(j));
     s->cv_work.notify_one();
@@ -314,8 +356,41 @@ void builder_loop(ldgmg_server* s) {
   if (st) cudaStreamDestroy(st);
 }
 
+// A grouped call: every request on its own class's hierarchy, one
+// ldgmg_solve_group call.  Called without the mutex; fills iters / relres /
+// status per request.
+void run_grouped(ldgmg_server* s, ldgmg_group** grp, const Job& j, cudaStream_t st, std::vector<int>& iters,
+                 std::vector<double>& relres, std::vector<ldgmg_status>& sts) {
+  const int R = int(j.reqs.size());
+  if (s->o.simulate) {
+    std::this_thread::sleep_for(std::chrono::duration<double>(s->o.simulate_solve_s));
+    return;
+  }
+  if (!*grp && ldgmg_group_create(grp) != LDGMG_OK) {
+    std::fill(sts.begin(), sts.end(), LDGMG_ENOMEM);
+    return;
+  }
+  std::vector<ldgmg_hier*> hs(R);
+  std::vector<const double*> bs(R);
+  std::vector<double*> xs(R);
+  std::vector<double> tols(R);
+  for (int r = 0; r < R; ++r) {
+    hs[r] = j.cls[r]->h;
+    bs[r] = j.reqs[r]->rhs.data();
+    xs[r] = j.reqs[r]->x_host;
+    tols[r] = j.reqs[r]->tol;
+  }
+  const ldgmg_status unset = ldgmg_status(-1);
+  std::fill(sts.begin(), sts.end(), unset);
+  const ldgmg_status all =
+      ldgmg_solve_group(*grp, R, hs.data(), bs.data(), xs.data(), tols.data(), iters.data(), relres.data(), sts.data(), st);
+  for (auto& v : sts)
+    if (v == unset) v = all;     // the call failed before solving
+}
+
 void worker_loop(ldgmg_server* s, int wid) {
   cudaStream_t st = nullptr;
+  ldgmg_group* grp = nullptr;     // grouped-call work space of this worker
   double *hb = nullptr, *hx = nullptr;   // pinned staging for the stacked right-hand sides
   size_t cap = 0;
   const bool simulate = s->o.simulate != 0;
@@ -329,6 +404,50 @@ void worker_loop(ldgmg_server* s, int wid) {
     Class* c = j.c;
     const double t_start = s->now();
     lk.unlock();
+    if (j.grouped) {
+      const int R = int(j.reqs.size());
+      std::vector<int> iters(R, 0);
+      std::vector<double> relres(R, std::numeric_limits<double>::quiet_NaN());
+      std::vector<ldgmg_status> sts(R, LDGMG_OK);
+      run_grouped(s, &grp, j, st, iters, relres, sts);
+      lk.lock();
+      const double t_end = s->now();
+      int served = 0;
+      // requests whose reduced-precision solve did not converge go back to the
+      // front of their class's queue (in order); the class is rebuilt with an
+      // FP64 V-cycle once no running call reads it
+      for (int r = R - 1; r >= 0; --r) {
+        Class* k = j.cls[size_t(r)];
+        auto& q = j.reqs[size_t(r)];
+        if (sts[r] == LDGMG_ENOTCONV && !simulate && k->prec != LDGMG_FP64 &&
+            s->o.setup.vcycle_precision != LDGMG_FP64) {
+          k->queue.push_front(q);
+          k->rebuild_fp64 = true;
+          continue;
+        }
+        q->res.status = sts[r];
+        q->res.iters = iters[r];
+        q->res.relres = relres[r];
+        q->res.t_start = t_start;
+        q->res.t_end = t_end;
+        q->res.batch = R;
+        q->res.worker = wid;
+        complete(s, q);
+        ++served;
+      }
+      for (Class* k : j.cls) {
+        k->users--;
+        k->last_use = t_end;
+      }
+      s->st.solve_calls++;
+      s->st.group_calls++;
+      s->st.group_requests += uint64_t(served);
+      s->st.max_batch_seen = std::max(s->st.max_batch_seen, R);
+      s->idle_workers++;
+      plan(s);
+      s->cv_done.notify_all();
+      continue;
+    }
     const int R = int(j.reqs.size());
     const size_t n = size_t(c->N) * c->b;
     std::vector<int> iters(R, 0);
@@ -367,7 +486,7 @@ void worker_loop(ldgmg_server* s, int wid) {
       c->bytes = 0;
       c->prec = LDGMG_FP64;
       c->state = Class::EMPTY;
-      c->busy = false;
+      c->users--;
       s->st.classes_resident--;
       s->st.precision_fallbacks++;
       s->st.solve_calls++;
@@ -387,7 +506,7 @@ void worker_loop(ldgmg_server* s, int wid) {
       q->res.worker = wid;
       complete(s, q);
     }
-    c->busy = false;
+    c->users--;
     c->last_use = t_end;
     s->st.solve_calls++;
     s->st.max_batch_seen = std::max(s->st.max_batch_seen, R);
@@ -396,6 +515,7 @@ void worker_loop(ldgmg_server* s, int wid) {
     s->cv_done.notify_all();
   }
   lk.unlock();
+  if (grp) ldgmg_group_free(grp);
   if (hb) cudaFreeHost(hb);
   if (hx) cudaFreeHost(hx);
   if (st) cudaStreamDestroy(st);
@@ -411,9 +531,11 @@ ldgmg_status ldgmg_server_create(const ldgmg_server_opts* o, ldgmg_server** out)
   if (o->workers < 1 || o->workers > 16) return serr(LDGMG_EINVAL, "workers must be in 1..16");
   if (o->max_batch < 1 || o->max_batch > 64) return serr(LDGMG_EINVAL, "max_batch must be in 1..64");
   if (o->simulate && !(o->simulate_solve_s >= 0.0)) return serr(LDGMG_EINVAL, "simulate_solve_s");
+  if (o->group_max < 0 || o->group_max > 65536) return serr(LDGMG_EINVAL, "group_max must be in 0..65536");
   auto* s = new (std::nothrow) ldgmg_server();
   if (!s) return serr(LDGMG_ENOMEM, "host allocation");
   s->o = *o;
+  if (s->o.group_max == 0) s->o.group_max = 512;
   s->t0 = Clock::now();
   if (s->o.hbm_budget == 0) {
     if (s->o.simulate) {
@@ -467,8 +589,13 @@ ldgmg_status ldgmg_server_submit(ldgmg_server* s, const ldgmg_request* q, uint64
     // Scalar classes take up to max_batch right-hand sides per call (tensor
     // cores where the hierarchy supports them, else the CUDA-core kernels),
     // capped so that a call holds at most 2^22 dofs; GMRES classes take one.
+    // Small scalar classes (at most group_dofs unknowns, CG) take one
+    // right-hand side per hierarchy and are solved in grouped calls.
     const int64_t cap = std::max<int64_t>(1, (int64_t(1) << 22) / (N * b));
-    c->rmax = q->stokes < 0 ? int(std::min<int64_t>(s->o.max_batch, cap)) : 1;
+    const int kr = s->o.setup.krylov;
+    c->small = q->stokes < 0 && size_t(N) * size_t(b) <= s->o.group_dofs &&
+               (kr == LDGMG_KRYLOV_AUTO || kr == LDGMG_KRYLOV_CG);
+    c->rmax = q->stokes < 0 && !c->small ? int(std::min<int64_t>(s->o.max_batch, cap)) : 1;
     it = s->classes.emplace(k, std::move(c)).first;
   }
   r->id = s->next_id++;

@@ -50,7 +50,8 @@ class SetupOpts(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("simulate", ctypes.c_int), ("simulate_solve_s", ctypes.c_double), ("setup", SetupOpts)]
+                ("simulate", ctypes.c_int), ("simulate_solve_s", ctypes.c_double), ("setup", SetupOpts),
+                ("group_dofs", ctypes.c_size_t), ("group_max", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -71,7 +72,8 @@ class ServerStats(ctypes.Structure):
                 ("solve_calls", ctypes.c_uint64), ("max_batch_seen", ctypes.c_int),
                 ("classes_resident", ctypes.c_int), ("bytes_resident", ctypes.c_size_t),
                 ("bytes_peak", ctypes.c_size_t), ("hbm_budget", ctypes.c_size_t),
-                ("precision_fallbacks", ctypes.c_uint64)]
+                ("precision_fallbacks", ctypes.c_uint64), ("group_calls", ctypes.c_uint64),
+                ("group_requests", ctypes.c_uint64)]
 
 
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -115,6 +117,10 @@ _SIGS = {
     "ldgmg_host_colours": (_i, [_vp, _i, _vp, _P(_i)]),
     "ldgmg_host_tc_plan": (_i, [_i, _vp, _vp, _i, _i, _i, _i, _vp, _P(_i64), _vp, _vp, _vp]),
     "ldgmg_host_free": (None, [_vp]),
+    "ldgmg_group_create": (_i, [_P(_vp)]),
+    "ldgmg_group_free": (None, [_vp]),
+    "ldgmg_solve_group": (_i, [_vp, _i, _P(_vp), _P(_vp), _P(_vp), _P(_d), _P(_i), _P(_d), _P(_i), _vp]),
+    "ldgmg_group_cluster": (_i, [_vp, _P(_i)]),
     "ldgmg_server_create": (_i, [_P(ServerOpts), _P(_vp)]),
     "ldgmg_server_submit": (_i, [_vp, _P(Request), _P(ctypes.c_uint64)]),
     "ldgmg_server_wait": (_i, [_vp, ctypes.c_uint64, _P(Result)]),
@@ -497,6 +503,49 @@ class Hierarchy:
             self._h = None
 
 
+class Group:
+    """Workspace of grouped solves (ldgmg_solve_group): many small problems,
+    each on its own hierarchy, solved in one launch per cluster size."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(_lib.ldgmg_group_create(ctypes.byref(h)))
+        self._h = h
+
+    @staticmethod
+    def cluster(hier) -> int:
+        """CTAs per problem a grouped solve gives this hierarchy (0: not eligible)."""
+        c = ctypes.c_int()
+        _check(_lib.ldgmg_group_cluster(hier._h, ctypes.byref(c)))
+        return c.value
+
+    def solve(self, problems, stream=None, check=True):
+        """problems: list of (hierarchy, rhs, x, tol); rhs / x FP64 tensors of
+        N*b entries (CUDA or CPU).  Returns (iterations, relres, statuses) lists."""
+        n = len(problems)
+        hs = (_vp * n)(*[p[0]._h.value for p in problems])
+        for hier, rhs, x, _ in problems:
+            if rhs.numel() != hier.op.size or x.numel() != hier.op.size:
+                raise ValueError("rhs and x must hold N*b entries of their hierarchy")
+            if not (rhs.is_contiguous() and x.is_contiguous()) or rhs.element_size() != 8 or x.element_size() != 8:
+                raise ValueError("rhs and x must be contiguous float64 tensors")
+        bs = (_vp * n)(*[p[1].data_ptr() for p in problems])
+        xs = (_vp * n)(*[p[2].data_ptr() for p in problems])
+        tols = (_d * n)(*[float(p[3]) for p in problems])
+        it = (_i * n)()
+        rr = (_d * n)()
+        stv = (_i * n)()
+        st = _lib.ldgmg_solve_group(self._h, n, hs, bs, xs, tols, it, rr, stv, _stream(stream))
+        if check and st != OK:
+            _check(st)
+        return list(it), list(rr), list(stv)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.ldgmg_group_free(self._h)
+            self._h = None
+
+
 # ---------------------------------------------------------------------------
 # serving engine (include/ldgmg_serve.h)
 # ---------------------------------------------------------------------------
@@ -505,10 +554,12 @@ class Server:
     """Continuous-batching solve server (ldgmg_server_*).  submit() copies the
     inputs and returns a ticket; wait(ticket) returns (x, result dict)."""
 
-    def __init__(self, workers=4, max_batch=32, hbm_budget=0, simulate=False, simulate_solve_s=0.0, **opts):
+    def __init__(self, workers=4, max_batch=32, hbm_budget=0, simulate=False, simulate_solve_s=0.0,
+                 group_dofs=0, group_max=0, **opts):
         o = ServerOpts()
         o.hbm_budget, o.workers, o.max_batch = int(hbm_budget), workers, max_batch
         o.simulate, o.simulate_solve_s = int(bool(simulate)), simulate_solve_s
+        o.group_dofs, o.group_max = int(group_dofs), int(group_max)
         o.setup = make_opts(**opts)
         h = ctypes.c_void_p()
         _check(_lib.ldgmg_server_create(ctypes.byref(o), ctypes.byref(h)))

@@ -129,3 +129,40 @@ def test_reduced_precision_class_falls_back_to_fp64(lib):
     assert s.wait(t_ok)[1]["status"] == lib.OK
     assert s.stats()["precision_fallbacks"] == 1
     s.close()
+
+
+def test_grouped_small_classes(lib):
+    """Small scalar classes (group_dofs) are served by grouped calls; each
+    result meets tol and is bitwise the same alone and in a mixed group (a
+    problem's arithmetic depends only on its own class and data)."""
+    small = [(2, 16, 1, None), (2, 16, 2, "square"), (3, 8, 1, None), (2, 32, 4, "square"), (2, 16, 3, None)]
+    s = lib.Server(workers=2, max_batch=16, precision="fp32", group_dofs=32768, group_max=64)
+    alone = {}
+    for ci, (d, n, p, mk) in enumerate(small):
+        x, r = s.wait(s.submit(d, n, p, _rhs(d, n, p, None, 200 + ci), mu=_mu(d, n, mk)))
+        assert r["status"] == lib.OK and r["relres"] <= 1.05e-10 and r["batch"] == 1, r
+        alone[ci] = x.copy()
+    order = []
+    rng = np.random.default_rng(1)
+    for k in range(60):
+        ci = int(rng.integers(len(small) + 1))
+        if ci == len(small):       # a larger class with its own calls
+            order.append((ci, False, s.submit(2, 64, 3, _rhs(2, 64, 3, None, 3000 + k))))
+            continue
+        d, n, p, mk = small[ci]
+        same = k % 4 == 0
+        seed = 200 + ci if same else 2000 + k
+        order.append((ci, same, s.submit(d, n, p, _rhs(d, n, p, None, seed), mu=_mu(d, n, mk))))
+    nsmall = len(small) + sum(1 for ci, _, _ in order if ci < len(small))
+    batches = []
+    for ci, same, t in order:
+        x, r = s.wait(t)
+        assert r["status"] == lib.OK and r["relres"] <= 1.05e-10, r
+        if ci < len(small):
+            batches.append(r["batch"])
+        if same:
+            assert np.array_equal(x, alone[ci]), ci
+    st_ = s.stats()
+    assert st_["group_requests"] == nsmall
+    assert st_["group_calls"] < nsmall and max(batches) > 1
+    s.close()

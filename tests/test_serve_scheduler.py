@@ -123,3 +123,42 @@ def test_bad_requests(lib):
         lib.Server(workers=0, simulate=True)
     with pytest.raises(lib.LdgmgError):
         lib.Server(max_batch=65, simulate=True)
+
+
+def test_small_classes_share_grouped_calls(lib):
+    # classes with at most group_dofs unknowns are served together: one grouped
+    # call takes the oldest queued requests of every ready small class (up to
+    # group_max); larger classes keep their own calls
+    s = lib.Server(workers=1, max_batch=8, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.05,
+                   group_dofs=4096, group_max=6, precision="fp32")
+    small = [(2, 16, 1), (2, 16, 2), (3, 8, 1), (2, 32, 1)]      # 1024, 2304, 4096, 4096 unknowns
+    tickets = []
+    for i in range(24):
+        d, n, p = small[i % 4]
+        tickets.append(("small", (d, n, p), s.submit(d, n, p, _rhs(d, n, p))))
+    tickets.append(("big", None, s.submit(2, 32, 2, _rhs(2, 32, 2))))    # 9216 unknowns
+    got = []
+    for kind, cls, t in tickets:
+        _, r = s.wait(t)
+        assert r["status"] == lib.OK
+        got.append((kind, cls, r))
+    st = s.stats()
+    assert st["completed"] == 25 and st["builds"] == 5
+    assert st["group_requests"] == 24
+    assert st["group_calls"] >= 4 and st["group_calls"] < 24
+    assert all(r["batch"] <= 6 for kind, _, r in got if kind == "small")
+    # some grouped call served requests of different classes
+    calls = {}
+    for kind, cls, r in got:
+        if kind == "small":
+            calls.setdefault((r["t_start"], r["t_end"]), set()).add(cls)
+    assert max(len(v) for v in calls.values()) > 1
+    # oldest first across classes: grouped calls start in submission order
+    starts = [r["t_start"] for kind, _, r in got if kind == "small"]
+    assert starts == sorted(starts)
+    s.close()
+
+
+def test_group_options_are_checked(lib):
+    with pytest.raises(lib.LdgmgError):
+        lib.Server(workers=1, simulate=True, group_max=70000)
