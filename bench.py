@@ -91,7 +91,7 @@ def parse():
     ap.add_argument("--stokes-tol", type=float, default=1e-9)
     ap.add_argument("--serve-requests", type=int, default=10000, help="0 disables the serving section")
     ap.add_argument("--serve-workers", type=int, default=4)
-    ap.add_argument("--serve-group-dofs", type=int, default=32768,
+    ap.add_argument("--serve-group-dofs", type=int, default=16384,
                     help="scalar classes with at most this many unknowns are solved in grouped calls")
     ap.add_argument("--serve-fp64-prefix", type=int, default=1000,
                     help="requests of the same stream fed to the one-at-a-time FP64 server")

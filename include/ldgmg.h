@@ -260,7 +260,9 @@ void ldgmg_group_free(ldgmg_group* g);
 /* Solve `count` independent single-right-hand-side problems A_i x_i = rhs_i,
  * each on its own hierarchy h[i] (hierarchies may differ in mesh, degree,
  * coefficient field, smoother and V-cycle precision, and may repeat), with
- * one kernel launch per cluster size (at most four launches): every problem
+ * one kernel launch per cluster size (at most four launches, the second to
+ * fourth on side streams the workspace owns, ordered after the work queued
+ * on `stream` and joined back into it): every problem
  * is a whole CG solve (Sec. 2.2, the V-cycle of Algorithm 1 as the
  * preconditioner) run on the device by one thread-block cluster of 1, 2, 4
  * or 8 CTAs (ldgmg_group_cluster), with no host round trip inside it.  The
@@ -285,9 +287,9 @@ ldgmg_status ldgmg_solve_group(ldgmg_group* g, int count, ldgmg_hier* const* h, 
                                double* const* x, const double* tol, int* iters, double* relres,
                                ldgmg_status* status, void* stream);
 
-/* Cluster size (CTAs) a grouped solve gives hierarchy h: 1, 2, 4 or 8 by the
- * entries of its finest operator (about 2^18 per CTA); 0 if h is not
- * eligible for grouped solves. */
+/* Cluster size (CTAs) a grouped solve gives hierarchy h: 1, 2, 4 or 8, about
+ * 1024 finest-level unknowns per CTA; 0 if h is not eligible for grouped
+ * solves. */
 ldgmg_status ldgmg_group_cluster(const ldgmg_hier* h, int* cluster);
 
 /* y = A x with the operator apply of the outer CG (Sec. 2.2: the residual

@@ -28,7 +28,9 @@
  *     ldgmg_solve_group call (one kernel launch per cluster size, each
  *     problem a whole solve on one thread-block cluster) takes up to
  *     group_max of the oldest small requests, whatever their class.  Several
- *     grouped calls may read the same class at once.
+ *     grouped calls may read the same class at once.  With grouped calls on,
+ *     the server runs one more worker (index `workers`) that takes grouped
+ *     calls only, so small requests never wait behind large solves.
  *   - Precision fallback.  When a solve of a class with a reduced-precision
  *     V-cycle ends with LDGMG_ENOTCONV (the V-cycle too inexact for the
  *     class, e.g. a large coefficient contrast in 3D), the class is rebuilt

@@ -1549,6 +1549,10 @@ struct ldgmg_group {
   size_t dev_cap = 0;
   char* host = nullptr;      // pinned mirror of the descriptor and staging regions
   size_t host_cap = 0;
+  // the launches of the second to fourth cluster size run beside the first,
+  // on side streams ordered after the copy-in (ev[0]) and joined back (ev[1..3])
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 static std::string group_ineligible(const ldgmg_hier* h) {
@@ -1559,11 +1563,13 @@ static std::string group_ineligible(const ldgmg_hier* h) {
   return "";
 }
 
-// about 2^18 finest-operator entries per CTA of the cluster
+// A grouped solve is latency bound (each step is a few L2 round trips per
+// thread, then a barrier): about two unknowns per thread, i.e. 1024 per
+// 512-thread CTA of the cluster, up to 8 CTAs.
 static int group_cluster_of(const ldgmg_hier* h) {
-  const double w = double(h->op->A.nnzb) * h->op->A.b * h->op->A.b;
+  const int64_t n0 = h->op->host.N * h->op->host.b;
   int c = 1;
-  while (c < 8 && w > double(c) * double(1 << 18)) c *= 2;
+  while (c < 8 && n0 > int64_t(c) * 1024) c *= 2;
   return c;
 }
 
@@ -1636,6 +1642,10 @@ ldgmg_status ldgmg_group_create(ldgmg_group** out) {
 
 void ldgmg_group_free(ldgmg_group* g) {
   if (!g) return;
+  for (cudaStream_t& x : g->side)
+    if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t& e : g->ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(g->dev);
   cudaFreeHost(g->host);
   delete g;
@@ -1768,12 +1778,28 @@ ldgmg_status ldgmg_solve_group(ldgmg_group* g, int count, ldgmg_hier* const* hs,
   CK(cudaMemcpyAsync(D, H, h2d_end, cudaMemcpyHostToDevice, st));
   const GroupProblem* dprobs = reinterpret_cast<const GroupProblem*>(D + o_probs);
   const GroupItem* ditems = reinterpret_cast<const GroupItem*>(D + o_items);
+  std::vector<std::pair<int, int>> ranges;     // items of one cluster size
   for (int j0 = 0; j0 < count;) {
     int j1 = j0;
     while (j1 < count && item_c[order[j1]] == item_c[order[j0]]) ++j1;
-    CK(group_solve(dprobs, ditems + j0, j1 - j0, item_c[order[j0]], st));
+    ranges.emplace_back(j0, j1);
     j0 = j1;
   }
+  if (ranges.size() > 1) {
+    for (size_t k = 0; k < ranges.size(); ++k) {
+      if (!g->ev[k]) CK(cudaEventCreateWithFlags(&g->ev[k], cudaEventDisableTiming));
+      if (k > 0 && !g->side[k - 1]) CK(cudaStreamCreateWithFlags(&g->side[k - 1], cudaStreamNonBlocking));
+    }
+    CK(cudaEventRecord(g->ev[0], st));
+  }
+  for (size_t k = 0; k < ranges.size(); ++k) {
+    cudaStream_t sk = k == 0 ? st : g->side[k - 1];
+    if (k > 0) CK(cudaStreamWaitEvent(sk, g->ev[0], 0));
+    const int j0 = ranges[k].first, j1 = ranges[k].second;
+    CK(group_solve(dprobs, ditems + j0, j1 - j0, item_c[order[j0]], sk));
+    if (k > 0) CK(cudaEventRecord(g->ev[k], sk));
+  }
+  for (size_t k = 1; k < ranges.size(); ++k) CK(cudaStreamWaitEvent(st, g->ev[k], 0));
   CK(cudaMemcpyAsync(H + o_outs, D + o_outs, d2h_end - o_outs, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const GroupOut* outs = reinterpret_cast<const GroupOut*>(H + o_outs);

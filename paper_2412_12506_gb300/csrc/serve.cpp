@@ -115,6 +115,10 @@ struct ldgmg_server {
   std::deque<Class*> build_q;
   std::deque<Job> work_q;
   int idle_workers = 0;
+  // small lane: with grouped calls on, one more worker takes grouped calls
+  // only, so small requests never wait behind large solves
+  bool has_lane = false, lane_idle = false;
+  std::deque<Job> lane_q;
   size_t reserved = 0;        // estimates of building classes + measured bytes of resident ones
   ldgmg_server_stats st{};
   std::thread builder;
@@ -254,6 +258,32 @@ void plan(ldgmg_server* s) {
   // requests of all ready small classes; any other class runs one call at a
   // time with as many of its own requests as one call takes.
   auto ready = [](const Class* c) { return c->state == Class::READY && !c->rebuild_fp64 && !c->queue.empty(); };
+  auto grouped_job = [&]() {
+    Job j;
+    j.grouped = true;
+    std::vector<Class*> cand;
+    for (auto& kv : s->classes)
+      if (kv.second->small && ready(kv.second.get())) cand.push_back(kv.second.get());
+    while (j.reqs.size() < size_t(s->o.group_max)) {
+      Class* o = nullptr;
+      for (Class* c : cand)
+        if (!c->queue.empty() && (!o || c->queue.front()->res.t_submit < o->queue.front()->res.t_submit)) o = c;
+      if (!o) break;
+      j.reqs.push_back(o->queue.front());
+      j.cls.push_back(o);
+      o->queue.pop_front();
+      o->users++;
+    }
+    return j;
+  };
+  if (s->has_lane && s->lane_idle) {
+    Job j = grouped_job();
+    if (!j.reqs.empty()) {
+      s->lane_idle = false;
+      s->lane_q.push_back(std::move(j));
+      s->cv_work.notify_all();
+    }
+  }
   while (s->idle_workers > 0) {
     Class* best = nullptr;
     for (auto& kv : s->classes) {
@@ -264,20 +294,7 @@ void plan(ldgmg_server* s) {
     if (!best) break;
     Job j;
     if (best->small) {
-      j.grouped = true;
-      std::vector<Class*> cand;
-      for (auto& kv : s->classes)
-        if (kv.second->small && ready(kv.second.get())) cand.push_back(kv.second.get());
-      while (j.reqs.size() < size_t(s->o.group_max)) {
-        Class* o = nullptr;
-        for (Class* c : cand)
-          if (!c->queue.empty() && (!o || c->queue.front()->res.t_submit < o->queue.front()->res.t_submit)) o = c;
-        if (!o) break;
-        j.reqs.push_back(o->queue.front());
-        j.cls.push_back(o);
-        o->queue.pop_front();
-        o->users++;
-      }
+      j = grouped_job();
     } else {
       j.c = best;
       const size_t cap = size_t(best->rmax);
@@ -290,7 +307,7 @@ void plan(ldgmg_server* s) {
     }
     s->idle_workers--;
     s->work_q.push_back(std::move(j));
-    s->cv_work.notify_one();
+    s->cv_work.notify_all();
   }
   s->st.bytes_resident = s->reserved;
   s->st.bytes_peak = std::max(s->st.bytes_peak, s->reserved);
@@ -388,7 +405,7 @@ void run_grouped(ldgmg_server* s, ldgmg_group** grp, const Job& j, cudaStream_t 
     if (v == unset) v = all;     // the call failed before solving
 }
 
-void worker_loop(ldgmg_server* s, int wid) {
+void worker_loop(ldgmg_server* s, int wid, bool lane) {
   cudaStream_t st = nullptr;
   ldgmg_group* grp = nullptr;     // grouped-call work space of this worker
   double *hb = nullptr, *hx = nullptr;   // pinned staging for the stacked right-hand sides
@@ -397,10 +414,11 @@ void worker_loop(ldgmg_server* s, int wid) {
   if (!simulate) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    s->cv_work.wait(lk, [&] { return s->stop || !s->work_q.empty(); });
-    if (s->work_q.empty()) break;
-    Job j = std::move(s->work_q.front());
-    s->work_q.pop_front();
+    std::deque<Job>& q = lane ? s->lane_q : s->work_q;
+    s->cv_work.wait(lk, [&] { return s->stop || !q.empty(); });
+    if (q.empty()) break;
+    Job j = std::move(q.front());
+    q.pop_front();
     Class* c = j.c;
     const double t_start = s->now();
     lk.unlock();
@@ -443,7 +461,8 @@ void worker_loop(ldgmg_server* s, int wid) {
       s->st.group_calls++;
       s->st.group_requests += uint64_t(served);
       s->st.max_batch_seen = std::max(s->st.max_batch_seen, R);
-      s->idle_workers++;
+      if (lane) s->lane_idle = true;
+      else s->idle_workers++;
       plan(s);
       s->cv_done.notify_all();
       continue;
@@ -551,8 +570,10 @@ ldgmg_status ldgmg_server_create(const ldgmg_server_opts* o, ldgmg_server** out)
   }
   s->st.hbm_budget = s->o.hbm_budget;
   s->idle_workers = o->workers;
+  s->has_lane = s->lane_idle = o->group_dofs > 0;
   s->builder = std::thread(builder_loop, s);
-  for (int w = 0; w < o->workers; ++w) s->workers.emplace_back(worker_loop, s, w);
+  for (int w = 0; w < o->workers; ++w) s->workers.emplace_back(worker_loop, s, w, false);
+  if (s->has_lane) s->workers.emplace_back(worker_loop, s, o->workers, true);
   *out = s;
   return LDGMG_OK;
 }

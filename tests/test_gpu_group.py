@@ -48,19 +48,19 @@ def consistent_rhs(d, n, p, seed):
     return ldg.project_out_constant(random_rhs(N, b, seed=seed), d, p, N)
 
 
-# (d, n, p, contrast, smoother, precision); the finest operator's entries set
-# the cluster size: 1, 1, 1, 2, 2, 4, 8, 8
+# (d, n, p, contrast, smoother, precision); the unknowns N b set the cluster
+# size (about 1024 per CTA): 1, 2, 4, 4, 8, 8, 8, 8
 CLASSES = [
-    (2, 16, 1, None, "sai", "fp64"),
-    (2, 16, 2, 1e2, "sai", "fp32"),
-    (3, 8, 1, None, "jacobi", "fp64"),
-    (2, 16, 3, None, "gs", "fp32"),
-    (2, 32, 2, 1e4, "sai", "fp32"),
-    (2, 16, 4, None, "sai", "bf16"),
-    (2, 32, 4, 1e4, "sai", "fp32"),
-    (3, 8, 2, None, "sai", "fp64"),
+    (2, 16, 1, None, "sai", "fp64"),       # 1024 unknowns
+    (2, 8, 4, 1e2, "sai", "fp32"),         # 1600
+    (3, 8, 1, None, "jacobi", "fp64"),     # 4096
+    (2, 16, 3, None, "gs", "fp32"),        # 4096
+    (2, 32, 2, 1e4, "sai", "fp32"),        # 9216
+    (2, 16, 4, None, "sai", "bf16"),       # 6400
+    (2, 32, 4, 1e4, "sai", "fp32"),        # 25600
+    (3, 8, 2, None, "sai", "fp64"),        # 13824
 ]
-CLUSTERS = [1, 1, 1, 2, 2, 4, 8, 8]
+CLUSTERS = [1, 2, 4, 4, 8, 8, 8, 8]
 
 _H = {}
 
@@ -124,7 +124,9 @@ def test_mixed_group_matches_individual_solves(lib):
         y = H.op.apply(x)
         true = float(torch.linalg.norm(b - y) / torch.linalg.norm(b))
         assert r <= 1.05e-10 and true <= 1.05e-10
-        assert abs(true - r) <= 1e-3 * r + 1e-15
+        # the two FP64 residuals differ by their rounding, ~eps |A| |x| / |b|
+        # (up to ~1e-13 at contrast 1e4), not by a relative amount
+        assert abs(true - r) <= 1e-3 * r + 1e-12
         # both iterates meet tol, so A (x - xs) is at most the sum of their
         # residuals; x - xs itself is that times the conditioning (up to ~1e7
         # at contrast 1e4), checked only for gross disagreement
@@ -134,7 +136,7 @@ def test_mixed_group_matches_individual_solves(lib):
 
 
 def test_host_buffers_repeats_and_special_cases(lib):
-    cls = CLASSES[1]
+    cls = (2, 16, 2, 1e2, "sai", "fp32")
     d, n, p = cls[:3]
     H = hier(lib, *cls)
     H2 = hier(lib, *CLASSES[4])
