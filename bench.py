@@ -96,8 +96,10 @@ def parse():
     ap.add_argument("--serve-fp64-prefix", type=int, default=1000,
                     help="requests of the same stream fed to the one-at-a-time FP64 server")
     ap.add_argument("--circle", type=int, default=1, help="0 disables the seeded-circle section")
+    ap.add_argument("--group-copies", type=int, default=16,
+                    help="copies of the grouped-solve section's problems in one call; 0 disables the section")
     ap.add_argument("--circle-max-iter", type=int, default=200)
-    ap.add_argument("--section", default="all", choices=["all", "batched", "stokes", "serve", "tcapply", "circle"],
+    ap.add_argument("--section", default="all", choices=["all", "batched", "stokes", "serve", "tcapply", "circle", "group"],
                     help="batched / stokes / serve: run only that section and print its object (profiling); "
                          "tcapply: only the batched section's dominant-kernel timing")
     ap.add_argument("--oracle-worker", action="store_true", help=argparse.SUPPRESS)
@@ -745,6 +747,65 @@ def run_serve(args, ldgmg, torch, np, dev, stream, barrier):
     return out
 
 
+def run_group(args, ldgmg, torch, np, dev, stream, barrier):
+    """Grouped solves (ldgmg_solve_group): small scalar classes of the serving
+    mix (2D 16^2 / 32^2 / 64^2, 3D 8^3; contrast 1 and 1e4 on the square
+    inclusion; FP32 V-cycles), each problem alone through the grouped kernel
+    against ldgmg_solve, and many problems in one grouped call against one
+    ldgmg_solve at a time."""
+    from paper_2412_12506_gb300.inputs import square_mu, zero_mean_rhs
+    shapes = [(2, 16, 1), (2, 16, 2), (2, 16, 3), (2, 16, 4), (2, 32, 1), (2, 32, 2), (2, 32, 3), (2, 64, 1),
+              (3, 8, 1), (3, 8, 2)]
+    classes, probs = [], []
+    for k, (d, n, p) in enumerate(shapes):
+        for c in (1.0, 1e4):
+            op = ldgmg.Operator(d, n, p, None if c == 1.0 else square_mu(d, n, mu_in=c))
+            H = ldgmg.Hierarchy(op, smoother="sai", precision="fp32", nu1=3, nu2=3)
+            b = torch.tensor(zero_mean_rhs(n ** d, (p + 1) ** d, seed=k), device=dev)
+            classes.append((f"{d}D_n{n}_p{p}_c{c:g}", op, H))
+            probs.append((H, b, torch.zeros_like(b), args.tol))
+    g = ldgmg.Group()
+    alone = []
+    for (name, op, H), pr in zip(classes, probs):
+        Hh, b, x, t = pr
+        Hh.solve(b, t, x=x, check=False)
+        g.solve([pr], check=False)
+        ts, tg = [], []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t1 = time.time()
+            _, ks, _, _ = Hh.solve(b, t, x=x, check=False)
+            torch.cuda.synchronize()
+            ts.append(time.time() - t1)
+            t1 = time.time()
+            it, rr, st = g.solve([pr], check=False)
+            tg.append(time.time() - t1)
+        alone.append({"class": name, "unknowns": op.size, "cluster": ldgmg.Group.cluster(Hh),
+                      "solve_ms": 1e3 * min(ts), "grouped_ms": 1e3 * min(tg), "iterations": [ks, it[0]],
+                      "status": st[0]})
+    copies = args.group_copies
+    many = [(H, b, torch.zeros_like(b), t) for _ in range(copies) for (H, b, x, t) in probs]
+    g.solve(many, check=False)
+    torch.cuda.synchronize()
+    l0 = ldgmg.kernel_launches()
+    t1 = time.time()
+    it, rr, st = g.solve(many, check=False)
+    t_group = time.time() - t1
+    launches_group = ldgmg.kernel_launches() - l0
+    l0 = ldgmg.kernel_launches()
+    t1 = time.time()
+    for H, b, x, t in many:
+        H.solve(b, t, x=x, check=False)
+    torch.cuda.synchronize()
+    t_one = time.time() - t1
+    launches_one = ldgmg.kernel_launches() - l0
+    return {"workload": f"grouped_{len(many)}_small_problems_{len(probs)}classes", "alone": alone,
+            "many": {"problems": len(many), "grouped_ms": 1e3 * t_group, "one_at_a_time_ms": 1e3 * t_one,
+                     "speedup": t_one / t_group, "grouped_launches": int(launches_group),
+                     "one_at_a_time_launches": int(launches_one), "reached_tol": int(sum(
+                         1 for s_, r_ in zip(st, rr) if s_ == ldgmg.OK and r_ <= 1.05 * args.tol))}}
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -796,14 +857,14 @@ def main():
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
         return
 
-    if args.section in ("batched", "stokes", "serve", "tcapply", "circle"):
+    if args.section in ("batched", "stokes", "serve", "tcapply", "circle", "group"):
         import numpy as np
         import torch
         torch.cuda.set_device(local_rank)
         from paper_2412_12506_gb300 import ldgmg
         dev = torch.device("cuda", local_rank)
         fn = {"batched": run_batched, "stokes": run_stokes, "serve": run_serve, "tcapply": run_tcapply,
-              "circle": run_circle}[args.section]
+              "circle": run_circle, "group": run_group}[args.section]
         out = fn(args, ldgmg, torch, np, dev, torch.cuda.current_stream(), lambda: None)
         print(json.dumps(out))
         return
@@ -989,6 +1050,7 @@ def main():
 
     batched = section("batched", args.batched_rhs > 0, run_batched)
     stokes = section("stokes", args.stokes_n > 0, run_stokes)
+    group = section("group", args.group_copies > 0, run_group)
     serve = section("serve", args.serve_requests > 0, run_serve)
     circle = section("circle", bool(args.circle), run_circle)
     if rank != 0:
@@ -1022,7 +1084,7 @@ def main():
         "other_precisions": other_prec,
         "spmv_fp64": {"ms": spmv_ms, "GB_per_s": spmv_bytes / (spmv_ms / 1e3) / 1e9,
                       "frac_of_hbm": spmv_bytes / (spmv_ms / 1e3) / 1e9 / peak},
-        "roofline": roofline, "batched": batched, "stokes": stokes, "serve": serve, "circle": circle, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "roofline": roofline, "batched": batched, "stokes": stokes, "group": group, "serve": serve, "circle": circle, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches, "setup_s": setup_s, "section_s": section_s,
     }
     print(json.dumps(line))
