@@ -89,7 +89,7 @@ constexpr uint32_t kAccCols = 32;       // columns of one accumulator
 constexpr uint32_t kTmemCols = 256;     // kNAcc * kAccCols (two CTAs: the whole TMEM)
 constexpr int kLag = 2;                 // the converter writes row s's slots after row s - kLag completes
 constexpr int kNX = kND;                // x-ready barriers
-constexpr int kNRaw = 3;                // raw x_j stages
+constexpr int kNRaw = 5;                // raw x_j stages (3: 0.2196 ms, 5: 0.2147, 6: 0.2150, 7: 0.2172 at 256^2)
 constexpr int kThreads = 480;
 constexpr int kConvThreads = 128;
 constexpr int kEpiThreads = 128;

@@ -25,7 +25,7 @@ import pytest
 
 from test_tc_pipeline_protocol import Barrier
 
-NS, ND, NACC, LAG, NRAW = 5, 16, 8, 2, 3
+NS, ND, NACC, LAG, NRAW = 5, 16, 8, 2, 5
 NX = ND
 
 
