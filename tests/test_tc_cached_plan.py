@@ -94,10 +94,11 @@ def test_library_schedules_replay_correctly(lib, n, smoother, ell, mu):
 
 
 def test_finest_level_reads_x_about_once(lib):
-    """5-point rows in strips of 8: each x_j is loaded about (8 + 2) / 8 times per
-    apply plus the cold start of each CTA's range (and reloads a 16-slot cache
-    cannot avoid), against 5 reads with one copy per use and a separate split
-    pass."""
+    """5-point rows in strips of 4 (the width the setup tuner picks at 256^2):
+    each x_j is loaded about (4 + 2) / 4 times per apply plus the cold start of
+    each CTA's range, against 5 reads with one copy per use and a separate
+    split pass.  (Wider strips need more slots than the 16 that fit beside
+    five raw x stages: strip 8 reloads 1.8 times per row.)"""
     n = 256
     H = lib.HostHierarchy(2, 16, 3, smoother="jacobi", nu1=1, nu2=1)   # any hierarchy: the pattern below is built here
     N = n * n
@@ -106,7 +107,7 @@ def test_finest_level_reads_x_about_once(lib):
     nb = np.stack([e, (x + 1) % n + n * y, (x - 1) % n + n * y, x + n * ((y + 1) % n), x + n * ((y - 1) % n)], 1)
     nb.sort(axis=1)
     rp = np.arange(0, 5 * N + 1, 5, dtype=np.int64)
-    plan = lib.host_tc_plan(n, rp, nb.reshape(-1).astype(np.int32), rcap=64, ctas=152, strip=8)
+    plan = lib.host_tc_plan(n, rp, nb.reshape(-1).astype(np.int32), rcap=64, ctas=152, strip=4)
     per_row = replay(plan, rp, nb.reshape(-1), n)
     assert plan["slots"] >= 16
     assert per_row < 1.6, per_row
