@@ -1286,6 +1286,18 @@ static ldgmg_status gmres_solve(ldgmg_hier* h, const double* b, double* x, doubl
 // the same outer apply for every R (so each right-hand side is bitwise the
 // same alone and batched): the block-reuse kernels for b = 16 / 64, else the
 // CUDA-core kernel.
+// r = b - A x in FP64 on R right-hand sides ([element][rhs][mode]): the CG's
+// true residual.  Multi-RHS hierarchies with b = 16 / 64 use the FP64
+// block-reuse kernel (A read once for all right-hand sides, and a right-hand
+// side's residual the same alone and batched), the others the CUDA-core kernel.
+static ldgmg_status true_residual(ldgmg_hier* h, const double* x, const double* b, double* r, int R, cudaStream_t s) {
+  const int bsz = h->op->host.b;
+  const bool multi = (h->batched || h->Rmax > 1) && R <= 64 && tc_block_size_supported(bsz);
+  if (multi) CK(bsr_apply_multi64(h->op->A, M_RES, x, b, r, R, s));
+  else CK(bsr_apply_strided(h->op->A, M_RES, x, b, nullptr, r, 1.0, R, int64_t(R) * bsz, bsz, s));
+  return LDGMG_OK;
+}
+
 static ldgmg_status krylov_apply(ldgmg_hier* h, const double* p, double* q, int R, cudaStream_t s) {
   const int bsz = h->op->host.b;
   const bool multi = (h->batched || h->Rmax > 1) && R <= 64 && tc_block_size_supported(bsz);
@@ -1474,7 +1486,7 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
       // miss tol from it (r = b - A x, z = V r, p = z).  Restarting touches
       // r, z, p of every right-hand side, which frozen ones no longer read.
       if (!flexible || nact > 0 || k >= h->o.max_iter || result != LDGMG_OK || round >= 16) break;
-      CK(bsr_apply_strided(h->op->A, M_RES, xg, b, nullptr, h->r, 1.0, R, R * bsz, bsz, st));
+      CKS(true_residual(h, xg, b, h->r, R, st));
       CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_TMP), st));
       CKS(read_slot(h, S_TMP, R, st));
       true_res_fresh = true;
@@ -1515,7 +1527,7 @@ ldgmg_status ldgmg_solve(ldgmg_hier* h, const double* rhs, double tol, double* x
   // true residual of the returned iterates (already in S_TMP when the
   // flexible confirmation just computed it for this x)
   if (!true_res_fresh) {
-    CK(bsr_apply_strided(h->op->A, M_RES, xd, b, nullptr, h->r, 1.0, R, R * bsz, bsz, st));
+    CKS(true_residual(h, xd, b, h->r, R, st));
     CK(dot_batched(N, R, int(bsz), h->r, nullptr, h->partials, slot(S_TMP), st));
     CKS(read_slot(h, S_TMP, R, st));
   }
