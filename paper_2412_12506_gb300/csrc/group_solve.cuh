@@ -35,6 +35,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <mutex>
 
 namespace ldgmg {
 
@@ -51,8 +52,8 @@ static_assert(sizeof(GroupProblem) % 8 == 0, "descriptor copied as 8-byte words"
 struct Smem {
   GroupProblem P;
   double Ps[2][8][8];               // one-dimensional injection matrices P[s][i][j]
-  double red[kGW];
-  double slot[2];                   // ping-pong slots of the CTA's partial inner products
+  double red[2][kGW];
+  double slot[2][2];                // ping-pong slots of the CTA's partial inner products (two sums each)
 };
 
 template <class TA> struct AccT { typedef float T; };
@@ -76,29 +77,59 @@ template <int C> struct Team {
   }
 };
 
-// sum_i a_i b_i over the cluster, the same value in every thread of every CTA
+// (sum_i a_i b_i, sum_i c_i d_i) over the cluster in one pass, the same
+// values in every thread of every CTA: each CTA reduces its part (warp
+// shuffles, then its warps in order), the C partial sums are exchanged
+// through distributed shared memory and added in rank order.  c may be null
+// (one sum).
 template <int C>
-__device__ double team_dot(const Team<C>& tm, Smem& sm, int& pp, const double* a, const double* b, int64_t n) {
-  double s = 0.0;
-  for (int64_t i = tm.t; i < n; i += tm.stride) s += a[i] * b[i];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) sm.red[threadIdx.x >> 5] = s;
+__device__ void team_dot2(const Team<C>& tm, Smem& sm, int& pp, const double* a, const double* b, const double* c,
+                          const double* d, int64_t n, double* out0, double* out1) {
+  double s0 = 0.0, s1 = 0.0;
+  if (c) {
+    for (int64_t i = tm.t; i < n; i += tm.stride) {
+      s0 += a[i] * b[i];
+      s1 += c[i] * d[i];
+    }
+  } else {
+    for (int64_t i = tm.t; i < n; i += tm.stride) s0 += a[i] * b[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sm.red[0][threadIdx.x >> 5] = s0;
+    sm.red[1][threadIdx.x >> 5] = s1;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 2) {
     double v = 0.0;
-    for (int w = 0; w < kGW; ++w) v += sm.red[w];
-    sm.slot[pp] = v;
+    for (int w = 0; w < kGW; ++w) v += sm.red[threadIdx.x][w];
+    sm.slot[pp][threadIdx.x] = v;
   }
   tm.sync();
-  double tot = 0.0;
+  double t0 = 0.0, t1 = 0.0;
   if (C == 1) {
-    tot = sm.slot[pp];
+    t0 = sm.slot[pp][0];
+    t1 = sm.slot[pp][1];
   } else {
     cg::cluster_group cl = cg::this_cluster();
-    for (int r = 0; r < C; ++r) tot += *cl.map_shared_rank(&sm.slot[pp], r);
+    for (int r = 0; r < C; ++r) {
+      t0 += *cl.map_shared_rank(&sm.slot[pp][0], r);
+      t1 += *cl.map_shared_rank(&sm.slot[pp][1], r);
+    }
   }
   pp ^= 1;
-  return tot;
+  *out0 = t0;
+  if (out1) *out1 = t1;
+}
+
+template <int C>
+__device__ double team_dot(const Team<C>& tm, Smem& sm, int& pp, const double* a, const double* b, int64_t n) {
+  double v;
+  team_dot2(tm, sm, pp, a, b, nullptr, nullptr, n, &v, nullptr);
+  return v;
 }
 
 // y = epilogue(M x) on block rows 0..nrows-1 or on the nrows rows listed in
@@ -452,7 +483,9 @@ __device__ void solve_item(const Team<C>& tm, Smem& sm, const GroupItem& I, bool
         x[i] += alpha * p[i];
         r[i] -= alpha * q[i];
       }
-      const double rr = team_dot(tm, sm, pp, r, r, n);
+      // ||r||^2 and, for the flexible beta, r . z_old in one pass
+      double rr = 0.0, rzold = 0.0;
+      team_dot2(tm, sm, pp, r, r, P.flexible ? r : nullptr, z, n, &rr, &rzold);
       ++k;
       if (!isfinite(rr)) {
         status = 2;
@@ -462,7 +495,6 @@ __device__ void solve_item(const Team<C>& tm, Smem& sm, const GroupItem& I, bool
         status = 0;
         break;
       }
-      const double rzold = P.flexible ? team_dot(tm, sm, pp, r, z, n) : 0.0;
       apply_V(tm, sm, lvec, r, z);
       const double rznew = team_dot(tm, sm, pp, r, z, n);
       const double beta = (P.flexible ? rznew - rzold : rznew) / rz;
@@ -516,6 +548,14 @@ __global__ void __launch_bounds__(kGT, 1) group_kernel(const GroupProblem* __res
 
 template <int C>
 cudaError_t launch_group(const GroupProblem* probs, const GroupItem* items, int count, cudaStream_t st) {
+  // the kernel keeps its few kilobytes of shared state and reads everything
+  // else through L1: ask for the largest L1 share (a hint, set once)
+  static std::once_flag once;
+  static cudaError_t cfg_err = cudaSuccess;
+  std::call_once(once, [] {
+    cfg_err = cudaFuncSetAttribute(group_kernel<C>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+  });
+  if (cfg_err != cudaSuccess) return cfg_err;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(count) * C, 1, 1);
   cfg.blockDim = dim3(kGT, 1, 1);
