@@ -17,8 +17,12 @@ with pinned host buffers (host<->device copies inside the timed region).
 bsr_kernel) on the finest level's SAI matrix.  `batched` reports the
 interface workload with 64 right-hand sides per call on the tensor-core path
 (2D 256^2, p = 3, mu 1 / 1e4 on the inclusion (1/4, 3/4)^2, balanced SAI1)
-against one-at-a-time FP64 solves.  `cpu_baseline` / `--impl reference` time
-the CPU oracle on a bounded sample.
+against one-at-a-time FP64 solves.  `stokes` is the stress-form Stokes solve
+(FGMRES, FP32 V-cycle), `group` the grouped solve of many small problems in
+one launch, `serve` the serving engine on a 10,000-request Poisson stream
+(beside the same engine without grouped calls and the one-at-a-time FP64
+solver on the same arrivals), `circle` the seeded-circle interface configs.
+`cpu_baseline` / `--impl reference` time the CPU oracle on a bounded sample.
 
 Multi-GPU (torchrun): every rank runs an independent replica (the solves do
 not shard across GPUs); value = all ranks' solves / max elapsed.
@@ -674,9 +678,19 @@ def run_serve(args, ldgmg, torch, np, dev, stream, barrier):
         span = max(r["t_end"] for r in res) - min(r["t_submit"] for r in res)
         ok = sum(1 for r in res if r["status"] == ldgmg.OK and r["relres"] <= 1.05 * args.tol)
         batches = np.array([r["batch"] for r in res])
+        # latency by request size: unknowns N b of the request's class
+        size = np.array([q["n"] ** q["dim"] * (q["p"] + 1) ** q["dim"] for q in reqs[:len(res)]])
+        by_size = {}
+        for name, lo, hi in (("small_le_16k", 0, 16384), ("medium_le_256k", 16384, 262144),
+                             ("large", 262144, 1 << 62)):
+            sel = (size > lo) & (size <= hi)
+            if sel.any():
+                by_size[name] = dict(requests=int(sel.sum()), latency_ms=pct(lat[sel]), queue_ms=pct(queue[sel]),
+                                     service_ms=pct(service[sel]))
         return {"requests": len(res), "solves_per_s": len(res) / span, "latency_ms": pct(lat), "queue_ms": pct(queue),
                 "service_ms": pct(service), "reached_tol": ok, "mean_batch": float(batches.mean()),
-                "max_batch_seen": int(batches.max()), "gpu_launches_per_request": launches / len(res)}
+                "max_batch_seen": int(batches.max()), "gpu_launches_per_request": launches / len(res),
+                "by_size": by_size}
 
     def pct(v):
         return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))}
