@@ -68,6 +68,9 @@ typedef struct {
   size_t group_dofs;        /* scalar classes with N*b <= group_dofs are solved in grouped calls
                                (ldgmg_solve_group); 0 = none */
   int group_max;            /* requests per grouped call, 1..65536; 0 = 512 */
+  int simulate_notconv_n;   /* simulate = 1 only: solves of classes with mesh size n equal to this value end
+                               with LDGMG_ENOTCONV while their V-cycle runs in reduced precision, which
+                               exercises the precision fallback without a GPU (0: never) */
 } ldgmg_server_opts;
 
 typedef struct {

@@ -100,6 +100,17 @@ struct Job {
 
 size_t esize(int prec) { return prec == LDGMG_FP64 ? 8 : (prec == LDGMG_FP32 ? 4 : 2); }
 
+// V-cycle precision a class is built with
+int class_prec(const ldgmg_server_opts& o, const Class& c) { return c.prec >= 0 ? c.prec : o.setup.vcycle_precision; }
+
+// simulate = 1: the solve outcome of a class (the injected non-convergence of
+// a reduced-precision class, see simulate_notconv_n)
+ldgmg_status simulated_status(const ldgmg_server_opts& o, const Class& c) {
+  return o.simulate_notconv_n > 0 && c.key.n == o.simulate_notconv_n && class_prec(o, c) != LDGMG_FP64
+             ? LDGMG_ENOTCONV
+             : LDGMG_OK;
+}
+
 }  // namespace
 
 struct ldgmg_server {
@@ -381,6 +392,7 @@ void run_grouped(ldgmg_server* s, ldgmg_group** grp, const Job& j, cudaStream_t 
   const int R = int(j.reqs.size());
   if (s->o.simulate) {
     std::this_thread::sleep_for(std::chrono::duration<double>(s->o.simulate_solve_s));
+    for (int r = 0; r < R; ++r) sts[r] = simulated_status(s->o, *j.cls[r]);
     return;
   }
   if (!*grp && ldgmg_group_create(grp) != LDGMG_OK) {
@@ -437,8 +449,7 @@ void worker_loop(ldgmg_server* s, int wid, bool lane) {
       for (int r = R - 1; r >= 0; --r) {
         Class* k = j.cls[size_t(r)];
         auto& q = j.reqs[size_t(r)];
-        if (sts[r] == LDGMG_ENOTCONV && !simulate && k->prec != LDGMG_FP64 &&
-            s->o.setup.vcycle_precision != LDGMG_FP64) {
+        if (sts[r] == LDGMG_ENOTCONV && class_prec(s->o, *k) != LDGMG_FP64) {
           k->queue.push_front(q);
           k->rebuild_fp64 = true;
           continue;
@@ -474,6 +485,7 @@ void worker_loop(ldgmg_server* s, int wid, bool lane) {
     ldgmg_status status = LDGMG_OK;
     if (simulate) {
       std::this_thread::sleep_for(std::chrono::duration<double>(s->o.simulate_solve_s));
+      status = simulated_status(s->o, *c);
     } else {
       if (cap < n * R) {
         if (hb) cudaFreeHost(hb);
@@ -494,8 +506,7 @@ void worker_loop(ldgmg_server* s, int wid, bool lane) {
     }
     lk.lock();
     const double t_end = s->now();
-    if (status == LDGMG_ENOTCONV && !simulate && c->prec != LDGMG_FP64 &&
-        s->o.setup.vcycle_precision != LDGMG_FP64) {
+    if (status == LDGMG_ENOTCONV && class_prec(s->o, *c) != LDGMG_FP64) {
       // A reduced-precision V-cycle too inexact for this class (large
       // coefficient contrast): rebuild the class once with an FP64 V-cycle
       // and solve these requests again, ahead of the class's later ones.

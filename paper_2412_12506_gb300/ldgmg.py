@@ -51,7 +51,7 @@ class SetupOpts(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("workers", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("simulate", ctypes.c_int), ("simulate_solve_s", ctypes.c_double), ("setup", SetupOpts),
-                ("group_dofs", ctypes.c_size_t), ("group_max", ctypes.c_int)]
+                ("group_dofs", ctypes.c_size_t), ("group_max", ctypes.c_int), ("simulate_notconv_n", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -555,11 +555,12 @@ class Server:
     inputs and returns a ticket; wait(ticket) returns (x, result dict)."""
 
     def __init__(self, workers=4, max_batch=32, hbm_budget=0, simulate=False, simulate_solve_s=0.0,
-                 group_dofs=0, group_max=0, **opts):
+                 group_dofs=0, group_max=0, simulate_notconv_n=0, **opts):
         o = ServerOpts()
         o.hbm_budget, o.workers, o.max_batch = int(hbm_budget), workers, max_batch
         o.simulate, o.simulate_solve_s = int(bool(simulate)), simulate_solve_s
         o.group_dofs, o.group_max = int(group_dofs), int(group_max)
+        o.simulate_notconv_n = int(simulate_notconv_n)
         o.setup = make_opts(**opts)
         h = ctypes.c_void_p()
         _check(_lib.ldgmg_server_create(ctypes.byref(o), ctypes.byref(h)))

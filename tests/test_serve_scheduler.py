@@ -169,3 +169,32 @@ def test_small_classes_share_grouped_calls(lib):
 def test_group_options_are_checked(lib):
     with pytest.raises(lib.LdgmgError):
         lib.Server(workers=1, simulate=True, group_max=70000)
+
+
+def test_precision_fallback_grouped_and_per_class(lib):
+    # simulate_notconv_n = 16: classes with n = 16 "do not converge" while their
+    # V-cycle is FP32.  The grouped class (2D 16^2 p = 1, 1,024 unknowns) and the
+    # per-class one (2D 16^2 p = 4, 6,400 unknowns) must each be rebuilt once
+    # with an FP64 V-cycle and their requests served again, in order; the n = 8
+    # class is untouched.
+    s = lib.Server(workers=1, max_batch=4, hbm_budget=1 << 40, simulate=True, simulate_solve_s=0.01,
+                   group_dofs=4096, precision="fp32", simulate_notconv_n=16)
+    order = []
+    for i in range(12):
+        d, n, p = [(2, 16, 1), (2, 16, 4), (2, 8, 1)][i % 3]
+        order.append(((d, n, p), s.submit(d, n, p, _rhs(d, n, p))))
+    got = {}
+    for cls, t in order:
+        _, r = s.wait(t)
+        assert r["status"] == lib.OK, (cls, r)
+        got.setdefault(cls, []).append(r)
+    st = s.stats()
+    assert st["completed"] == 12
+    assert st["precision_fallbacks"] == 2
+    assert st["builds"] == 5                      # 3 classes + 2 FP64 rebuilds
+    assert st["group_requests"] == 8              # the 2D 16^2 p = 1 and 8^2 p = 1 requests
+    # each class's requests start in submission order
+    for rs in got.values():
+        starts = [r["t_start"] for r in rs]
+        assert all(b >= a - 0.005 for a, b in zip(starts, starts[1:]))
+    s.close()
