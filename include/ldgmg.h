@@ -281,8 +281,9 @@ void ldgmg_group_free(ldgmg_group* g);
  *                 iteration count, the true final relative residual and the
  *                 status of problem i (OK; ENOTCONV at max_iter or on a
  *                 non-finite residual, x written; EINVAL for non-finite rhs).
- * Returns OK when every problem converged, else the first failing problem's
- * status (the others are still solved).  Synchronises `stream`. */
+ * Returns OK when every problem converged, else the status of the failing
+ * problem with the lowest index (the others are still solved).  Synchronises
+ * `stream`. */
 ldgmg_status ldgmg_solve_group(ldgmg_group* g, int count, ldgmg_hier* const* h, const double* const* rhs,
                                double* const* x, const double* tol, int* iters, double* relres,
                                ldgmg_status* status, void* stream);

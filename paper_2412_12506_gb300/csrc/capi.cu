@@ -1815,8 +1815,8 @@ ldgmg_status ldgmg_solve_group(ldgmg_group* g, int count, ldgmg_hier* const* hs,
   CK(cudaMemcpyAsync(H + o_outs, D + o_outs, d2h_end - o_outs, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   const GroupOut* outs = reinterpret_cast<const GroupOut*>(H + o_outs);
-  ldgmg_status result = LDGMG_OK;
-  std::string msg;
+  int first_bad = count;          // lowest failing problem index
+  int first_code = 0;
   for (int j = 0; j < count; ++j) {
     const int i = order[j];
     const GroupOut& o = outs[j];
@@ -1825,14 +1825,18 @@ ldgmg_status ldgmg_solve_group(ldgmg_group* g, int count, ldgmg_hier* const* hs,
     if (relres) relres[i] = o.relres;
     if (status) status[i] = si;
     if (hx[i]) std::memcpy(x[i], H + o_x[i], size_t(n0[item_prob[i]]) * 8);
-    if (si != LDGMG_OK && result == LDGMG_OK) {
-      result = si;
-      msg = "problem " + std::to_string(i) +
-            (o.status == 3 ? ": rhs contains NaN or Inf"
-                           : (o.status == 2 ? ": CG breakdown (non-finite residual)" : ": max_iter reached"));
+    if (si != LDGMG_OK && i < first_bad) {
+      first_bad = i;
+      first_code = o.status;
     }
   }
-  if (result != LDGMG_OK) return fail(result, msg);
+  if (first_bad < count) {
+    const ldgmg_status r = first_code == 3 ? LDGMG_EINVAL : LDGMG_ENOTCONV;
+    return fail(r, "problem " + std::to_string(first_bad) +
+                       (first_code == 3 ? ": rhs contains NaN or Inf"
+                                        : (first_code == 2 ? ": CG breakdown (non-finite residual)"
+                                                           : ": max_iter reached")));
+  }
   return LDGMG_OK;
 }
 
